@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Every test here checks ``oracle/ap_dvm_oracle.py`` against something other
+than itself: exact identities of the D2V6 velocity set, the moment system
+derived from the discrete velocity model, closed-form symbols and orders of
+the stencils, textbook WENO limits, a dense linear solve, invariants of the
+scheme (conservation, equilibrium fixed point, mirror symmetry), the stage
+equations of Sec. 3.1 and the incompressible limit (Taylor-Green decay).
+"""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+from oracle import ap_dvm_oracle as O
+from paper_2512_19847_gb300 import workloads as W
+
+warnings.filterwarnings("ignore", category=RuntimeWarning)
+
+SCHEMES = ["LF1_C2", "WENO3_C4", "WENO5_C4"]
+
+
+def _params(n, scheme="WENO5_C4", eps=1e-2, tau=0.05, dt=None, tab="gsa2", **kw):
+    A_ex, _, A_im, _ = O.tableau_gsa2() if tab == "gsa2" else O.tableau_euler()
+    dx = 2 * math.pi / n
+    return O.Params(n, n, eps, tau, 0.25 * dx if dt is None else dt, A_ex, A_im, scheme=scheme, **kw)
+
+
+# ---------------------------------------------------------------- D2V6 algebra (Sec. 2.1)
+
+def test_d2v6_velocity_moments():
+    c = O.d2v6_velocities()
+    assert np.allclose(np.linalg.norm(c, axis=1), 1.0, atol=1e-15)
+    assert np.allclose(c.sum(axis=0), 0.0, atol=1e-15)
+    assert np.allclose(c.T @ c, 3.0 * np.eye(2), atol=1e-14)            # sum c c^T = 3 I
+    c1, c2 = c[:, 0], c[:, 1]
+    assert abs(np.sum(c1 ** 4) - 9 / 4) < 1e-14
+    assert abs(np.sum(c2 ** 4) - 9 / 4) < 1e-14
+    assert abs(np.sum(c1 ** 2 * c2 ** 2) - 3 / 4) < 1e-14
+    assert np.allclose([np.sum(c1 ** 3), np.sum(c1 * c1 * c2), np.sum(c2 ** 3)], 0.0, atol=1e-14)
+    # explicit angles: hexagon, 60 degrees apart
+    assert np.allclose(c[1], [0.5, math.sqrt(3) / 2], atol=1e-15)
+
+
+def test_moment_basis_is_orthogonal_and_invertible():
+    P = O.moment_basis()
+    G = P @ P.T
+    assert np.allclose(G, np.diag([6, 3, 3, 0.75, 0.75, 0.375]), atol=1e-14)
+    # det of the (c1^2 - 1/2 ...) map = product of norms^(1/2) squared: full rank
+    assert abs(np.linalg.det(G) - 6 * 3 * 3 * 0.75 * 0.75 * 0.375) < 1e-12
+
+
+@pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-5])
+def test_population_map_roundtrip(eps):
+    X = W.random_moment_state(8, 8, seed=3)
+    dF = O.populations_from_moments(X, eps, rho0=1.3, amp=2e-3)
+    Y = O.moments_from_populations(dF, eps, rho0=1.3, amp=2e-3)
+    # theta, v ride at eps and q at eps^2 inside f: the round trip's conditioning
+    power = np.array([0, 0, 1, 1, 1, 2])
+    tol = 1e-14 * np.max(np.abs(X)) * 8 / eps ** power
+    err = np.max(np.abs(Y - X), axis=(1, 2))
+    assert np.all(err <= tol), (err, tol)
+
+
+def test_population_moments_by_brute_force():
+    """The rescaled moments of Sec. 2.1 (with the G1 sign of v1) by scalar loops."""
+    rng = np.random.default_rng(1)
+    eps, rho0, amp = 0.03, 1.0, 1.0
+    dF = rng.standard_normal((6, 3, 3)) * 1e-3
+    X = O.moments_from_populations(dF, eps, rho0, amp)
+    for j in range(3):
+        for i in range(3):
+            f = [dF[k, j, i] / (rho0 * amp) for k in range(6)]
+            s0 = s1 = s2 = s3 = s4 = s5 = 0.0
+            for k in range(6):
+                ck1 = math.cos(math.pi * k / 3)
+                ck2 = math.sin(math.pi * k / 3)
+                s0 += f[k]
+                s1 += ck1 * f[k]
+                s2 += ck2 * f[k]
+                s3 += (ck2 * ck2 - 0.5) * f[k]          # G1: v1 uses (c2^2 - 1/2)
+                s4 += ck1 * ck2 * f[k]
+                s5 += ck1 * (ck2 * ck2 - 0.25) * f[k]
+            expect = [s1, s2, s0 / (2 * eps), s3 / eps, s4 / eps, s5 / eps ** 2]
+            got = X[:, j, i]
+            assert np.allclose(got, expect, rtol=1e-12, atol=1e-12)
+
+
+def test_equilibrium_moments():
+    """F^eq of Sec. 2.1 has moments rho, m, and second moments giving F(u)."""
+    rng = np.random.default_rng(2)
+    rho = 1 + 0.1 * rng.standard_normal(5)
+    m1, m2 = 0.1 * rng.standard_normal(5), 0.1 * rng.standard_normal(5)
+    F = O.feq_populations(rho, m1, m2)
+    P = O.moment_basis()
+    M = np.einsum("mi,i...->m...", P, F)
+    assert np.allclose(M[0], rho, atol=1e-14)
+    assert np.allclose(M[1], m1, atol=1e-14)
+    assert np.allclose(M[2], m2, atol=1e-14)
+    # sum (c1^2-1/2) F^eq = (m1^2 - m2^2)/2, i.e. v1^eq = (m2^2 - m1^2)/2 = F(u)_1 under G1
+    assert np.allclose(M[3], 0.5 * (m1 ** 2 - m2 ** 2), atol=1e-14)
+    assert np.allclose(M[4], m1 * m2, atol=1e-14)
+    assert np.allclose(M[5], 0.0, atol=1e-14)
+    f1, f2 = O.F_of_u(m1, m2)
+    assert np.allclose(-M[3], f1, atol=1e-14) and np.allclose(M[4], f2, atol=1e-14)
+
+
+def _spec_d(f, axis, L=2 * math.pi):
+    n = f.shape[axis]
+    k = np.fft.fftfreq(n, d=1.0 / n) * (2 * math.pi / L)
+    shape = [1, 1]
+    shape[axis] = n
+    return np.real(np.fft.ifft(1j * k.reshape(shape) * np.fft.fft(f, axis=axis), axis=axis))
+
+
+def test_moment_system_follows_from_the_dvm():
+    """Pins G1, G2, G3, the moment map (G10) and F(u): the time derivative of
+    the populations under the scaled DVM dF/dt + (1/eps) c.grad F =
+    -(F - F^eq)/(eps^2 tau), mapped to moments, equals the right-hand side of
+    the closed moment system of Sec. 2.1 under those readings."""
+    n, eps, tau = 16, 0.3, 0.7
+    X = W.random_moment_state(n, n, seed=11, modes=3)
+    X = X - 0.05 * 0  # smooth part dominates; white noise is fine for spectral derivatives
+    dF = O.populations_from_moments(X, eps, rho0=1.0, amp=eps)      # physical amplitude A = eps
+    F = 1.0 / 6.0 + dF
+    c = O.d2v6_velocities()
+    rho = F.sum(axis=0)
+    m1 = np.einsum("i,i...->...", c[:, 0], F)
+    m2 = np.einsum("i,i...->...", c[:, 1], F)
+    Feq = O.feq_populations(rho, m1, m2)
+    dFdt = np.stack([-(c[i, 0] * _spec_d(F[i], 1) + c[i, 1] * _spec_d(F[i], 0)) / eps
+                     - (F[i] - Feq[i]) / (eps * eps * tau) for i in range(6)])
+    dXdt = O.moments_from_populations(dFdt, eps, rho0=1.0, amp=eps)
+    u1, u2, th, v1, v2, q = X
+    Dx = lambda f: _spec_d(f, 1)
+    Dy = lambda f: _spec_d(f, 0)
+    r = 1.0 / (eps * eps * tau)
+    rhs = np.stack([
+        Dx(v1) - Dy(v2) - Dx(th),
+        -Dx(v2) - Dy(v1) - Dy(th),
+        -(Dx(u1) + Dy(u2)) / (2 * eps * eps),
+        -(-Dx(u1) + Dy(u2)) / (4 * eps * eps) - Dx(q) - r * (v1 + 0.5 * (u1 ** 2 - u2 ** 2)),
+        -(Dx(u2) + Dy(u1)) / (4 * eps * eps) - Dy(q) - r * (v2 - u1 * u2),
+        -(Dx(v1) + Dy(v2)) / (2 * eps * eps) - r * q,
+    ])
+    scale = np.max(np.abs(rhs), axis=(1, 2))
+    err = np.max(np.abs(dXdt - rhs), axis=(1, 2))
+    assert np.all(err <= 1e-10 * scale), (err, scale)
+    # the printed q equation (d_x v1 + d_x v2) does not hold (G2)
+    printed_q = -(Dx(v1) + Dx(v2)) / (2 * eps * eps) - r * q
+    assert np.max(np.abs(dXdt[5] - printed_q)) > 1e-3 * scale[5]
+
+
+# ---------------------------------------------------------------- tableaux (Sec. 3.1, 4.1)
+
+@pytest.mark.parametrize("name", ["euler", "gsa2"])
+def test_tableau_properties(name):
+    A_ex, w_ex, A_im, w_im = O.tableau_euler() if name == "euler" else O.tableau_gsa2()
+    s = A_ex.shape[0]
+    assert np.allclose(np.triu(A_ex), 0.0)                 # explicit: strictly lower
+    assert np.allclose(np.triu(A_im, 1), 0.0)              # implicit: DIRK
+    assert np.allclose(A_ex[-1], w_ex) and np.allclose(A_im[-1], w_im)   # GSA
+    assert A_im[0, 0] == 0.0 and np.all(np.diag(A_im)[1:] > 0)          # CK / ARS
+    c_ex, c_im = A_ex.sum(axis=1), A_im.sum(axis=1)
+    assert np.allclose(c_ex, c_im)                         # c~ = c: equilibrium is a fixed point
+    assert abs(w_ex.sum() - 1) < 1e-15 and abs(w_im.sum() - 1) < 1e-15
+    if name == "gsa2":
+        assert abs(A_im[2, 2] - 1.4) < 1e-15               # gamma = (c - 1/2)/(c - 1), c = 2.25
+        for w in (w_ex, w_im):
+            for cc in (c_ex, c_im):
+                assert abs(w @ cc - 0.5) < 1e-14           # second-order and coupling conditions
+
+
+# ---------------------------------------------------------------- stencils (Sec. 3.2, G7)
+
+def test_central_difference_orders():
+    errs = {2: [], 4: []}
+    for n in (32, 64):
+        X, Y = W.cell_centres(n, n)
+        f = np.sin(X + 0.3) * np.cos(2 * Y)
+        fx = np.cos(X + 0.3) * np.cos(2 * Y)
+        fyy = -4 * np.sin(X + 0.3) * np.cos(2 * Y)
+        fxy = -2 * np.cos(X + 0.3) * np.sin(2 * Y)
+        for sch, order in (("LF1_C2", 2), ("WENO5_C4", 4)):
+            p = _params(n, sch)
+            e = max(np.abs(O.dx_c(f, p) - fx).max(), np.abs(O.dyy_c(f, p) - fyy).max(),
+                    np.abs(O.dx_c(O.dy_c(f, p), p) - fxy).max())
+            errs[order].append(e)
+    for order, (e1, e2) in errs.items():
+        assert abs(math.log2(e1 / e2) - order) < 0.15
+
+
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO5_C4"])
+def test_laplacian_symbol_matches_stencil(scheme):
+    n = 16
+    p = _params(n, scheme)
+    lam = O.laplacian_symbol(n, p.dx, p)
+    X, Y = W.cell_centres(n, n)
+    for k in range(n):
+        f = np.cos(k * X)
+        assert np.allclose(O.laplacian(f, p), lam[k] * f, atol=1e-10)
+    # closed form of the 4th-order symbol: -(cos phi - 1)(cos phi - 7)/(3 h^2) <= 0
+    if scheme == "WENO5_C4":
+        phi = 2 * math.pi * np.arange(n) / n
+        assert np.allclose(lam, -(np.cos(phi) - 1) * (np.cos(phi) - 7) / (3 * p.dx ** 2))
+    assert np.all(lam[1:] < 0) and lam[0] == 0
+
+
+def test_d0sqB_is_div_div_B():
+    """D_0^2:B(v) of Sec. 3.2 approximates div(div B(v)) = -v1_xx + 2 v2_xy + v1_yy."""
+    errs = []
+    for n in (32, 64):
+        X, Y = W.cell_centres(n, n)
+        v1 = np.sin(X) * np.cos(2 * Y)
+        v2 = np.cos(X + Y)
+        exact = (np.sin(X) * np.cos(2 * Y)) - 2 * np.cos(X + Y) * 1 - 4 * np.sin(X) * np.cos(2 * Y)
+        # -v1_xx = sin x cos 2y ; 2 v2_xy = -2 cos(x+y) ; v1_yy = -4 sin x cos 2y
+        errs.append(np.abs(O.d0sq_B(v1, v2, _params(n, "LF1_C2")) - exact).max())
+    assert abs(math.log2(errs[0] / errs[1]) - 2) < 0.15
+
+
+# ---------------------------------------------------------------- WENO (G7, G8)
+
+def test_weno5_linear_weights_limit_is_upwind5():
+    rng = np.random.default_rng(5)
+    a, b, c, d, e = rng.standard_normal((5, 100))
+    got = O.weno5_reconstruct(a, b, c, d, e, 1e30)
+    assert np.allclose(got, (2 * a - 13 * b + 47 * c + 27 * d - 3 * e) / 60, atol=1e-13)
+    got3 = O.weno3_reconstruct(a, b, c, 1e30)
+    assert np.allclose(got3, (-a + 5 * b + 2 * c) / 6, atol=1e-13)
+
+
+def test_weno_exact_on_linear_data():
+    x = np.arange(-2, 3, dtype=float)
+    f = 0.7 * x + 0.2
+    assert abs(O.weno5_reconstruct(*f, 1e-6) - (0.7 * 0.5 + 0.2)) < 1e-14
+    assert abs(O.weno3_reconstruct(*f[1:4], 1e-6) - (0.7 * 0.5 + 0.2)) < 1e-14
+
+
+def test_weno5_order_and_nonoscillatory():
+    errs = []
+    for n in (32, 64, 128):
+        p = _params(n, "WENO5_C4")
+        X, _ = W.cell_centres(n, 4)
+        g = np.sin(X + 0.4) + 0.5 * np.sin(2 * X)
+        U = 0.3 * np.cos(X)
+        d = O.lf_dx(g, U, p)
+        errs.append(np.abs(d - (np.cos(X + 0.4) + np.cos(2 * X))).max())
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert orders[-1] > 4.3, orders
+    # step: reconstruction stays within the data range (no new extrema beyond eps_W effects)
+    step_f = np.where(np.arange(40) < 20, 0.0, 1.0)[None, :].repeat(2, 0)
+    fh = O.interface_flux(step_f, np.zeros_like(step_f), O.sx, _params(40, "WENO5_C4"))
+    assert fh.min() > -1e-6 and fh.max() < 1 + 1e-6
+
+
+def test_lf1_flux_is_central_plus_dissipation():
+    n = 16
+    p = _params(n, "LF1_C2")
+    rng = np.random.default_rng(8)
+    g, U = rng.standard_normal((2, n, n))
+    d = O.lf_dx(g, U, p)
+    expect = O.dx_c(g, p) - (p.alpha / (2 * p.dx)) * (O.sx(U, 1) - 2 * U + O.sx(U, -1))
+    assert np.allclose(d, expect, atol=1e-12)
+    assert abs(d.sum()) < 1e-10   # telescoping flux differences
+
+
+# ---------------------------------------------------------------- Helmholtz (Algorithm 1, step 2)
+
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO5_C4"])
+@pytest.mark.parametrize("n", [8, 16])
+def test_helmholtz_against_dense_solve(scheme, n):
+    p = _params(n, scheme)
+    kappa = 0.37
+    N2 = n * n
+    M = np.zeros((N2, N2))
+    for col in range(N2):
+        e = np.zeros(N2)
+        e[col] = 1.0
+        M[:, col] = O.laplacian(e.reshape(n, n), p).ravel() - kappa * e
+    rng = np.random.default_rng(n)
+    R = rng.standard_normal((n, n))
+    th_dense = np.linalg.solve(M, R.ravel()).reshape(n, n)
+    th = O.helmholtz_solve(R, kappa, float(np.mean(th_dense)), p)
+    assert np.max(np.abs(th - th_dense)) <= 1e-12 * np.max(np.abs(th_dense))
+    # kappa = 0: zero-mean right-hand side, mean fixed by the G5 rule
+    R0 = R - R.mean()
+    th0 = O.helmholtz_solve(R0, 0.0, 0.25, p)
+    res = O.laplacian(th0, p) - R0
+    assert np.max(np.abs(res)) < 1e-11 * np.max(np.abs(R0))
+    assert abs(th0.mean() - 0.25) < 1e-14
+
+
+# ---------------------------------------------------------------- whole-step invariants
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("eps", [1.0, 1e-3, 0.0])
+@pytest.mark.parametrize("tab", ["euler", "gsa2"])
+def test_uniform_equilibrium_is_fixed_point(scheme, eps, tab):
+    n = 8
+    u1 = np.full((n, n), 0.3)
+    u2 = np.full((n, n), -0.2)
+    X = O.equilibrium_state(u1, u2, np.full((n, n), 0.1))
+    Y = O.step(X, _params(n, scheme, eps=eps, tau=0.05, tab=tab))
+    assert np.max(np.abs(Y - X)) < 1e-13
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_conservation_of_u_and_mean_theta(scheme):
+    n = 16
+    X = W.random_moment_state(n, n, seed=21)
+    Y = O.step(X, _params(n, scheme, eps=0.05, tau=0.1))
+    assert abs(Y[0].sum() - X[0].sum()) < 1e-11 * np.abs(X[0]).sum()
+    assert abs(Y[1].sum() - X[1].sum()) < 1e-11 * np.abs(X[1]).sum()
+    assert abs(Y[2].mean() - X[2].mean()) < 1e-13 * np.abs(X[2]).max()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_mirror_symmetry(scheme):
+    """x -> -x maps (u1,u2,theta,v1,v2,q) -> (-u1,u2,theta,v1,-v2,-q) (odd/even
+    parity of the moment weights in c1); the discrete step commutes with it."""
+    n = 16
+    X = W.random_moment_state(n, n, seed=31)
+    p = _params(n, scheme, eps=0.1, tau=0.2)
+    sgn = np.array([-1, 1, 1, 1, -1, -1])[:, None, None]
+    mirror = lambda Z: sgn * Z[:, :, ::-1]
+    Y1 = O.step(mirror(X), p)
+    Y2 = mirror(O.step(X, p))
+    assert np.max(np.abs(Y1 - Y2)) < 1e-12 * np.max(np.abs(Y2))
+    # y -> -y maps (u1,u2,theta,v1,v2,q) -> (u1,-u2,theta,v1,-v2,q)
+    sgy = np.array([1, -1, 1, 1, -1, 1])[:, None, None]
+    mirror_y = lambda Z: sgy * Z[:, ::-1, :]
+    assert np.max(np.abs(O.step(mirror_y(X), p) - mirror_y(O.step(X, p)))) < 1e-12 * np.max(np.abs(Y2))
+
+
+def test_g4_sign_from_the_stage_equations():
+    """With mutually consistent operators (D_Delta := D_0.D_0, D_0^2:B := D_0.(D_0.B),
+    alpha = 0) Algorithm 1 must satisfy the theta stage equation of Sec. 3.1:
+    theta^(i) = theta^n - dt/(2 eps^2) [sum_{j<i} a_ij D0.u^(j) + a_ii D0.u^(i)].
+    Only the minus sign of the theta-history term (reading G4) does."""
+    n = 16
+    X = W.random_moment_state(n, n, seed=41, amp=0.3)
+    res = {}
+    for sign in (-1.0, +1.0):
+        p = _params(n, "LF1_C2", eps=0.5, tau=0.3, dt=0.05, operators="consistent", alpha=0.0,
+                    theta_hist_sign=sign)
+        _, st = O.step(X, p, return_stages=True)
+        A = p.A_im
+        worst = 0.0
+        for i in (2, 3):
+            acc = np.zeros((n, n))
+            for j in range(1, i + 1):
+                acc += A[i - 1, j - 1] * O.div_c(st[j][0], st[j][1], p)
+            r = st[i][2] - X[2] + p.dt / (2 * p.eps ** 2) * acc
+            worst = max(worst, np.max(np.abs(r)) / np.max(np.abs(st[i][2])))
+        res[sign] = worst
+    assert res[-1.0] < 1e-12, res
+    assert res[+1.0] > 1e-3, res
+
+
+def test_g6_partner_reading_stability():
+    """The explicit-weight dissipation partner stays bounded at CFL 0.5 on
+    Taylor-Green with the second-order tableau; the lagged reading blows up."""
+    n = 32
+    u1, u2, pr = W.taylor_green(n)
+    X0 = O.equilibrium_state(u1, u2, pr) + 1e-6 * np.random.default_rng(0).standard_normal((6, n, n))
+    dx = 2 * math.pi / n
+    out = {}
+    for partner in ("explicit", "lagged"):
+        p = _params(n, "WENO3_C4", eps=1e-2, tau=0.05, dt=0.5 * dx, partner=partner)
+        Y = X0.copy()
+        for _ in range(40):
+            Y = O.step(Y, p)
+        out[partner] = float(np.max(np.abs(Y[:2]))) if np.isfinite(Y).all() else float("inf")
+    assert out["explicit"] < 1.0
+    assert out["lagged"] > 10.0
+
+
+def test_exact_limit_eps_zero_runs():
+    n = 16
+    u1, u2, pr = W.taylor_green(n)
+    X = O.equilibrium_state(u1, u2, pr)
+    Y = O.run(X, _params(n, "WENO5_C4", eps=0.0, tau=0.0), 4)
+    assert np.isfinite(Y).all()
+    assert np.max(np.abs(Y[:2] - X[:2])) < 0.1
+
+
+# ---------------------------------------------------------------- the incompressible limit
+
+def test_taylor_green_limit_decay():
+    """eps -> 0: u follows the INS Taylor-Green solution with nu = tau/4 and the
+    kinetic energy decays like exp(-4 nu t) (Sec. 2.1 INS limit, Theorem 3.5)."""
+    tau, T = 0.4, 0.5
+    nu = tau / 4
+    errs = []
+    for n in (16, 32):
+        u1, u2, pr = W.taylor_green(n)
+        X = O.equilibrium_state(u1, u2, pr)
+        dt, ns = W.fixed_time_dt(T, 0.25 * 2 * math.pi / n)
+        Y = O.run(X, _params(n, "WENO5_C4", eps=1e-6, tau=tau, dt=dt), ns)
+        e1, e2, _ = W.taylor_green(n, t=T, nu=nu)
+        errs.append(max(np.abs(Y[0] - e1).max(), np.abs(Y[1] - e2).max()))
+        ke_ratio = np.mean(Y[0] ** 2 + Y[1] ** 2) / np.mean(X[0] ** 2 + X[1] ** 2)
+        assert abs(ke_ratio / math.exp(-4 * nu * T) - 1) < (0.05 if n == 16 else 0.005)
+    assert errs[1] < errs[0] / 8
+
+
+@pytest.mark.parametrize("tab,order", [("euler", 1.0), ("gsa2", 2.0)])
+def test_temporal_order(tab, order):
+    """Self-convergence under dt halving at fixed N in the limit regime.
+
+    Measured with mutually consistent operators, where Algorithm 1 is exactly
+    the IMEX-RK scheme of Sec. 3.1 applied to the space-discrete system, so
+    the tableau's order shows: 1 (Euler GSA) and 2 (second-order GSA).  With
+    the printed operator mix (compact D_Delta beside D_0 theta) each stage
+    carries the extra term dt^2 a_ii^2/(2 eps^2) (D_Delta - D_0.D_0) theta^(i),
+    which makes dt-self-convergence first order at fixed N (checked below)."""
+    n, T = 16, 0.4
+    u1, u2, pr = W.taylor_green(n)
+    X = O.equilibrium_state(u1, u2, pr)
+
+    def orders(**kw):
+        sols = []
+        for k in range(3):
+            ns = 8 * 2 ** k
+            sols.append(O.run(X, _params(n, eps=1e-6, tau=0.2, dt=T / ns, tab=tab, **kw), ns))
+        e1 = np.max(np.abs(sols[0][:2] - sols[1][:2]))
+        e2 = np.max(np.abs(sols[1][:2] - sols[2][:2]))
+        return math.log2(e1 / e2)
+
+    assert abs(orders(scheme="LF1_C2", alpha=0.0, operators="consistent") - order) < 0.1
+    if tab == "gsa2":
+        assert orders(scheme="LF1_C2", alpha=0.0) < 1.3
