@@ -176,7 +176,8 @@ def laplacian(f, p: Params):
 
 
 def laplacian_symbol(n: int, h: float, p: Params):
-    """Eigenvalue of the 1D second-difference operator on the DFT mode k = 0..n-1."""
+    """Eigenvalue of the 1D second-difference operator on the DFT mode k = 0..n-1
+    (the compact 3-point or the 4th-order 5-point stencil of Sec. 3.2)."""
     phi = 2 * math.pi * np.arange(n) / n
     if p.operators == "consistent":
         # D_0 D_0 with D_0 central: symbol (i sin(phi)/h)^2 (2nd order) or the 4th-order analogue
@@ -185,9 +186,12 @@ def laplacian_symbol(n: int, h: float, p: Params):
         else:
             d = (8 * np.sin(phi) - np.sin(2 * phi)) / (6 * h)
         return -d * d
+    # (2 cos phi - 2) and (-2 cos 2phi + 32 cos phi - 30)/12 written without
+    # cancellation for small phi: -4 sin^2(phi/2) and 2 sin^2(phi/2)(cos phi - 7)/3
+    s2 = np.sin(0.5 * phi) ** 2
     if _order(p) == 2:
-        return (2 * np.cos(phi) - 2) / h ** 2
-    return (-2 * np.cos(2 * phi) + 32 * np.cos(phi) - 30) / (12 * h ** 2)
+        return -4.0 * s2 / h ** 2
+    return 2.0 * s2 * (np.cos(phi) - 7.0) / (3.0 * h ** 2)
 
 
 def div_c(w1, w2, p: Params):
