@@ -1,0 +1,187 @@
+/* ap_dvm.h — C ABI of the GB300 (sm_103a) implementation of the
+ * asymptotic-preserving IMEX Runge-Kutta scheme for the six-velocity (D2V6)
+ * lattice-Boltzmann-type discrete velocity model in the low-Mach /
+ * diffusive scaling (Dimarco, Klar, Koefler, Pareschi: "Asymptotic preserving
+ * methods for the low Mach limit in discrete velocity models approximating
+ * kinetic equations").
+ *
+ * The library advances the closed moment system of Sec. 2.1 (vector form of
+ * Sec. 3) with Algorithm 1 of Sec. 3.1 and the finite-difference operators of
+ * Sec. 3.2 on a periodic nx x ny grid of cell centres.
+ *
+ * Conventions for every call below:
+ *  - All array pointers are DEVICE pointers unless the name starts with h_.
+ *  - A "plane" is nx*ny values, row-major with x fastest: element (i, j) of
+ *    cell centre ((i+1/2) Lx/nx, (j+1/2) Ly/ny) is at j*nx + i.
+ *  - A "moment state" is 6 consecutive double planes in the order
+ *    (u1, u2, theta, v1, v2, q) of Sec. 2.1 (rescaled moments).
+ *  - "Populations" are 6 consecutive planes dF_1..dF_6, the deviations
+ *    F_i - rho0/6 of the D2V6 populations (c_i = (cos(pi(i-1)/3),
+ *    sin(pi(i-1)/3))), scaled so that dF = rho0 * mach * f with
+ *    sum f = 2 eps theta, sum c f = u, sum (c1^2 - 1/2) f = -eps v1,
+ *    sum c1 c2 f = eps v2, sum c1 (c2^2 - 1/4) f = eps^2 q.
+ *  - The caller owns all device memory, including workspaces.  Apart from
+ *    a CUDA graph it may instantiate (ap_dvm_set_graph_steps), the library
+ *    allocates no device memory: it carves the workspaces it is given.
+ *  - Calls that launch work are asynchronous on the handle's stream.
+ *  - Errors: a status code is returned synchronously for argument errors;
+ *    device-side conditions (non-finite state) are latched in a device flag
+ *    read by ap_dvm_sync_status.  Nothing aborts or traps.
+ */
+#ifndef AP_DVM_H
+#define AP_DVM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AP_DVM_OK = 0,
+  AP_DVM_ERR_ARG = 1,          /* invalid argument (message in ap_dvm_last_error) */
+  AP_DVM_ERR_TABLEAU = 2,      /* tableau is not a CK/ARS GSA IMEX tableau with a_ii > 0, i >= 2 */
+  AP_DVM_ERR_WORKSPACE = 3,    /* workspace too small or misaligned */
+  AP_DVM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  AP_DVM_ERR_NONFINITE = 5,    /* a step produced a non-finite value (latched on the device) */
+  AP_DVM_ERR_TIMEOUT = 6,      /* reserved: bounded device waits that expired */
+  AP_DVM_ERR_UNSUPPORTED = 7   /* valid but not implemented configuration */
+} ap_dvm_status;
+
+enum { AP_DVM_D2V6 = 6 };                                        /* velocity set (Sec. 2.1) */
+enum { AP_DVM_LF1_C2 = 0, AP_DVM_WENO3_C4 = 1, AP_DVM_WENO5_C4 = 2 }; /* spatial scheme (Sec. 3.2) */
+enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1 };                   /* precision form */
+#define AP_DVM_MAX_STAGES 4
+
+/* Parameters of one solve.
+ *  nx, ny      cells per direction, powers of two in [8, 4096].
+ *  Lx, Ly      periodic domain [0,Lx) x [0,Ly), > 0 (the paper uses 2 pi).
+ *  velocity_set  AP_DVM_D2V6 (the only set of Sec. 2.1).
+ *  eps         Knudsen / scaling parameter epsilon >= 0 (eps = 0 is the exact
+ *              incompressible limit; the FP32 form needs eps > 0).
+ *  tau         BGK coefficient tau >= 0 (the limit viscosity is tau/4, Sec. 2.1);
+ *              tau < 0 selects tau = 4 eps / mach (from eps = Ma/Re, Re = 4/tau).
+ *  mach        storage amplitude A > 0 of the populations (dF = rho0 A f);
+ *              a pure scale of the population view.
+ *  rho0        reference density > 0.
+ *  dt          time step > 0.
+ *  s           number of stages, 2..AP_DVM_MAX_STAGES.
+ *  A_ex, A_im  explicit (strictly lower) and implicit (lower) tableaux of
+ *              Sec. 3.1, row-major with row stride AP_DVM_MAX_STAGES; the
+ *              implicit tableau must be of type CK/ARS (a_11 = 0, a_ii > 0 for
+ *              i >= 2) and the pair globally stiffly accurate, so that the
+ *              last stage is the new state.
+ *  space_scheme  AP_DVM_LF1_C2, AP_DVM_WENO3_C4 or AP_DVM_WENO5_C4.
+ *  precision   AP_DVM_FP64 (all in FP64) or AP_DVM_FP32_DEV (FP32 deviation
+ *              populations and FP32 transport; FP64 moment sums, division by
+ *              rho0*mach, and closed-form relaxation when eps <= 1e-4).
+ *  weno_eps    epsilon of the WENO weights (> 0; 1e-6 by default).
+ */
+typedef struct {
+  int nx, ny;
+  double Lx, Ly;
+  int velocity_set;
+  double eps, tau, mach, rho0, dt;
+  int s;
+  double A_ex[AP_DVM_MAX_STAGES * AP_DVM_MAX_STAGES];
+  double A_im[AP_DVM_MAX_STAGES * AP_DVM_MAX_STAGES];
+  int space_scheme;
+  int precision;
+  double weno_eps;
+} ap_dvm_params;
+
+typedef struct ap_dvm_handle ap_dvm_handle;
+
+/* ---- single solve --------------------------------------------------------- */
+
+/* Bytes of device workspace ap_dvm_create needs for *p (0 if *p is invalid). */
+size_t ap_dvm_workspace_size(const ap_dvm_params* p);
+
+/* Create a handle for one solve (Algorithm 1 on the grid of *p).
+ *  d_workspace  device buffer of at least ap_dvm_workspace_size(p) bytes,
+ *               256-byte aligned, owned by the caller for the handle's life.
+ *  cuda_stream  cudaStream_t on which all work is enqueued (NULL = legacy default).
+ *  out          receives the handle (host memory owned by the library; free
+ *               with ap_dvm_destroy).
+ * The state is zero until set with ap_dvm_set_state / _equilibrium / _populations. */
+ap_dvm_status ap_dvm_create(const ap_dvm_params* p, void* d_workspace, size_t bytes, void* cuda_stream,
+                            ap_dvm_handle** out);
+
+/* ---- batches of uneven solves (one launch per kernel covers all of them) ---- */
+
+/* Bytes of the batch tables for up to `capacity` instances whose sizes do not
+ * exceed tmpl->nx, tmpl->ny.  tmpl fixes the scheme, precision and tableau. */
+size_t ap_dvm_batch_workspace_size(const ap_dvm_params* tmpl, int capacity);
+/* Bytes of device workspace of one instance attached to a batch. */
+size_t ap_dvm_instance_workspace_size(const ap_dvm_params* p);
+/* Create an empty batch. */
+ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void* d_workspace, size_t bytes,
+                                  void* cuda_stream, ap_dvm_handle** out);
+/* Attach a solve to slot 0 <= slot < capacity with its own workspace of
+ * ap_dvm_instance_workspace_size(p) bytes.  p must share the template's
+ * scheme, precision and tableau; nx <= tmpl->nx, ny <= tmpl->ny.  Must not be
+ * called while the handle's stream is being captured. */
+ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, void* d_workspace, size_t bytes);
+/* Remove a solve from the batch; its workspace may be reused once the stream
+ * has passed this point. */
+ap_dvm_status ap_dvm_detach(ap_dvm_handle* h, int slot);
+
+/* ---- state (slot = 0 for a single solve) ----------------------------------- */
+
+/* Set the moment state from 6 double planes (u1, u2, theta, v1, v2, q). */
+ap_dvm_status ap_dvm_set_state(ap_dvm_handle* h, int slot, const double* d_moments6);
+/* Set the state at equilibrium from a velocity and a pressure (3 double
+ * planes): theta = p + |u|^2/2 (Sec. 3.1), v = F(u) = ((u2^2-u1^2)/2, u1 u2), q = 0. */
+ap_dvm_status ap_dvm_set_equilibrium(ap_dvm_handle* h, int slot, const double* d_u1, const double* d_u2,
+                                     const double* d_p);
+/* Set the state from 6 population planes: double (FP64 form or FP32 form),
+ * or float (is_float = 1, FP32 form only). */
+ap_dvm_status ap_dvm_set_populations(ap_dvm_handle* h, int slot, const void* d_dF6, int is_float);
+/* Read the moment state into 6 double planes. */
+ap_dvm_status ap_dvm_get_state(ap_dvm_handle* h, int slot, double* d_moments6);
+/* Read the populations into 6 planes (double, or float when is_float = 1). */
+ap_dvm_status ap_dvm_get_populations(ap_dvm_handle* h, int slot, void* d_dF6, int is_float);
+/* Macroscopic outputs (4 double planes): density rho = rho0 (1 + 2 mach eps theta),
+ * velocity u1, u2 and pressure p = theta - |u|^2/2 (Sec. 3.1, theta = p + |u|^2/2). */
+ap_dvm_status ap_dvm_moments(ap_dvm_handle* h, int slot, double* d_rho, double* d_u1, double* d_u2, double* d_p);
+
+/* ---- time stepping ------------------------------------------------------------ */
+
+/* Advance every attached solve by nsteps IMEX steps (Algorithm 1; the GSA
+ * property makes the last stage the new state).  Asynchronous.  With
+ * graph steps k > 0 (ap_dvm_set_graph_steps) the steps are replayed from a
+ * CUDA graph of k steps. */
+ap_dvm_status ap_dvm_step(ap_dvm_handle* h, int nsteps);
+/* Use a captured CUDA graph of k steps for ap_dvm_step (k = 0: direct launches). */
+ap_dvm_status ap_dvm_set_graph_steps(ap_dvm_handle* h, int k);
+/* Tile shape of the stencil kernels: 0 = 32x8, 1 = 32x4, 2 = 16x8, 3 = 8x8,
+ * 4 = 64x4, -1 = automatic.  Every attached grid must be at least the tile. */
+ap_dvm_status ap_dvm_set_tile(ap_dvm_handle* h, int tile);
+int ap_dvm_get_tile(const ap_dvm_handle* h);
+/* Kernel launches enqueued by one ap_dvm_step(h, 1). */
+int ap_dvm_launches_per_step(const ap_dvm_handle* h);
+
+/* End-to-end call on HOST buffers: copy 6 moment planes h_in (double) to the
+ * device, set the state of slot, run nsteps, and copy the moment state back
+ * into h_out (6 double planes); synchronous.  Pinned host memory gives
+ * asynchronous copies; d_stage must hold 6 planes of doubles. */
+ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage,
+                              int nsteps);
+
+/* Synchronise the stream and return AP_DVM_ERR_NONFINITE if any step since the
+ * last call produced a non-finite value (the flag is then cleared). */
+ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h);
+/* Message of the last error on this handle (never NULL). */
+const char* ap_dvm_last_error(const ap_dvm_handle* h);
+/* Release the handle (host memory and graphs); device workspaces stay with the caller. */
+void ap_dvm_destroy(ap_dvm_handle* h);
+
+/* Fill *p with defaults: 2 pi periodic square, D2V6, rho0 = 1, mach = 1e-2,
+ * tau = 0.05, the second-order GSA tableau of Sec. 4.1 (c = 2.25), WENO5+C4,
+ * FP64, weno_eps = 1e-6; nx, ny, eps and dt are set from the arguments. */
+void ap_dvm_default_params(ap_dvm_params* p, int nx, int ny, double eps, double dt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AP_DVM_H */

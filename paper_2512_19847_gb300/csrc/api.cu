@@ -1,0 +1,707 @@
+// Host side of the C ABI declared in include/ap_dvm.h.
+//
+// A handle is a batch: a fixed tableau, scheme and precision, and up to
+// `capacity` attached solves, each with its own caller-owned workspace.  The
+// per-instance descriptors and the prefix sums of the work decomposition
+// live in the batch workspace; every kernel of a step is launched once for
+// all attached solves.  One IMEX step (Algorithm 1, CK/ARS tableau, stage 1
+// = X^n) enqueues, for i = 2..s:
+//   k_explicit(i-1)  explicit term of step 1 and reusable operators of stage i-1
+//   k_rhs(i)         step 1 (v^(i)) and the Helmholtz right-hand side of step 2
+//   k_fft_rows_fwd, k_fft_cols(i), k_fft_rows_inv(i)   step 2 (theta^(i))
+//   k_update(i)      steps 3 and 4 (u^(i), q^(i))
+// and finally k_finish (GSA: X^{n+1} = X^(s); FP32 form: repack populations).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ap_dvm.h"
+#include "common.cuh"
+#include "dispatch.h"
+
+using namespace apd;
+
+struct Slot {
+  bool attached = false;
+  ap_dvm_params p{};
+  char* ws = nullptr;
+  size_t bytes = 0;
+  InstDev dev{};
+};
+
+struct ap_dvm_handle {
+  ap_dvm_params tmpl{};
+  int capacity = 0;
+  int f32 = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int tile = 0;
+  bool tile_auto = true;
+  int nmax = 0, lnmax = 0, eblk = 0;
+  // batch workspace
+  BatchDev* d_batch = nullptr;
+  InstDev* d_inst = nullptr;
+  int* d_tile_start = nullptr;
+  int* d_row_start = nullptr;
+  int* d_col_start = nullptr;
+  int* d_counts = nullptr;
+  double2* d_tw = nullptr;
+  unsigned* d_err = nullptr;
+  BatchDev hb{};
+  std::vector<Slot> slots;
+  bool dirty = true;
+  int n_active = 0;
+  // upload staging (kept alive across async copies)
+  std::vector<InstDev> up_inst;
+  std::vector<int> up_tiles, up_rows, up_cols;
+  int up_counts[4] = {0, 0, 0, 0};
+  // kernels
+  StencilSet ks{};
+  MiscSet km{};
+  int grid_explicit = 0, grid_rhs = 0, grid_update = 0, grid_fft = 0, grid_finish = 0;
+  bool kernels_ready = false;
+  // graph
+  int graph_steps = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool graph_valid = false;
+  char err[512] = "";
+};
+
+namespace {
+
+ap_dvm_status fail(ap_dvm_handle* h, ap_dvm_status st, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+#define CUDA_TRY(h, call)                                                                                 \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
+    if (e_ != cudaSuccess) return fail(h, AP_DVM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+double tau_of(const ap_dvm_params& p) { return p.tau < 0 ? 4.0 * p.eps / p.mach : p.tau; }
+
+// Validates one solve's parameters; writes a message into buf.
+ap_dvm_status validate(const ap_dvm_params* p, char* buf, size_t n) {
+  if (!p) { snprintf(buf, n, "null parameters"); return AP_DVM_ERR_ARG; }
+  if (!is_pow2(p->nx) || !is_pow2(p->ny) || p->nx < 8 || p->ny < 8 || p->nx > 4096 || p->ny > 4096) {
+    snprintf(buf, n, "nx, ny must be powers of two in [8, 4096] (got %d, %d)", p->nx, p->ny);
+    return AP_DVM_ERR_ARG;
+  }
+  if (!(p->Lx > 0) || !(p->Ly > 0)) { snprintf(buf, n, "Lx, Ly must be > 0"); return AP_DVM_ERR_ARG; }
+  if (p->velocity_set != AP_DVM_D2V6) { snprintf(buf, n, "only the D2V6 velocity set exists (Sec. 2.1)"); return AP_DVM_ERR_ARG; }
+  if (!(p->eps >= 0) || !std::isfinite(p->eps)) { snprintf(buf, n, "eps must be >= 0"); return AP_DVM_ERR_ARG; }
+  if (!(p->mach > 0)) { snprintf(buf, n, "mach must be > 0"); return AP_DVM_ERR_ARG; }
+  if (!(p->rho0 > 0)) { snprintf(buf, n, "rho0 must be > 0"); return AP_DVM_ERR_ARG; }
+  if (!(p->dt > 0) || !std::isfinite(p->dt)) { snprintf(buf, n, "dt must be > 0"); return AP_DVM_ERR_ARG; }
+  if (!std::isfinite(p->tau)) { snprintf(buf, n, "tau must be finite"); return AP_DVM_ERR_ARG; }
+  if (p->space_scheme < AP_DVM_LF1_C2 || p->space_scheme > AP_DVM_WENO5_C4) { snprintf(buf, n, "unknown space_scheme"); return AP_DVM_ERR_ARG; }
+  if (p->precision != AP_DVM_FP64 && p->precision != AP_DVM_FP32_DEV) { snprintf(buf, n, "unknown precision"); return AP_DVM_ERR_ARG; }
+  if (p->precision == AP_DVM_FP32_DEV && !(p->eps > 0)) { snprintf(buf, n, "the FP32 deviation form needs eps > 0 (population view)"); return AP_DVM_ERR_ARG; }
+  if (!(p->weno_eps > 0)) { snprintf(buf, n, "weno_eps must be > 0"); return AP_DVM_ERR_ARG; }
+  const int s = p->s;
+  if (s < 2 || s > AP_DVM_MAX_STAGES) { snprintf(buf, n, "s must be in [2, %d]", AP_DVM_MAX_STAGES); return AP_DVM_ERR_TABLEAU; }
+  auto ae = [&](int i, int j) { return p->A_ex[i * AP_DVM_MAX_STAGES + j]; };
+  auto ai = [&](int i, int j) { return p->A_im[i * AP_DVM_MAX_STAGES + j]; };
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      if (!std::isfinite(ae(i, j)) || !std::isfinite(ai(i, j))) { snprintf(buf, n, "non-finite tableau entry"); return AP_DVM_ERR_TABLEAU; }
+      if (j >= i && ae(i, j) != 0.0) { snprintf(buf, n, "explicit tableau must be strictly lower triangular"); return AP_DVM_ERR_TABLEAU; }
+      if (j > i && ai(i, j) != 0.0) { snprintf(buf, n, "implicit tableau must be lower triangular (DIRK)"); return AP_DVM_ERR_TABLEAU; }
+    }
+  if (ai(0, 0) != 0.0) { snprintf(buf, n, "type-A tableaux (a_11 != 0) are not supported; use a CK/ARS tableau"); return AP_DVM_ERR_UNSUPPORTED; }
+  for (int i = 1; i < s; ++i)
+    if (!(ai(i, i) > 0)) { snprintf(buf, n, "a_ii must be > 0 for i >= 2"); return AP_DVM_ERR_TABLEAU; }
+  return AP_DVM_OK;
+}
+
+bool same_method(const ap_dvm_params& a, const ap_dvm_params& b) {
+  if (a.s != b.s || a.space_scheme != b.space_scheme || a.precision != b.precision) return false;
+  for (int k = 0; k < AP_DVM_MAX_STAGES * AP_DVM_MAX_STAGES; ++k)
+    if (a.A_ex[k] != b.A_ex[k] || a.A_im[k] != b.A_im[k]) return false;
+  return true;
+}
+
+// Carves one instance's workspace (base == nullptr: size only).
+size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
+  const size_t es = p.precision == AP_DVM_FP64 ? 8 : 4;
+  const size_t cells = (size_t)p.nx * p.ny;
+  const size_t plane = cells * es;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    off = align_up(off, 256);
+    void* r = base ? base + off : nullptr;
+    off += bytes;
+    return r;
+  };
+  const int s = p.s;
+  InstDev tmp{};
+  InstDev& I = d ? *d : tmp;
+  I.X = take(6 * plane);
+  for (int j = 2; j <= s; ++j) I.Xs[j] = take(6 * plane);
+  for (int j = 1; j <= s; ++j) {
+    I.E[j] = take(2 * plane);
+    I.Du[j] = take(plane);
+    I.Lth[j] = take(plane);
+    I.Gth[j] = take(2 * plane);
+    I.DLFB[j] = take(2 * plane);
+    I.Dv[j] = take(plane);
+    I.DB[j] = take(plane);
+  }
+  I.R = take(plane);
+  I.sstride = p.nx / 2 + 1;
+  I.S = take((size_t)p.ny * I.sstride * 2 * es);
+  I.lamx = reinterpret_cast<double*>(take((size_t)(p.nx / 2 + 1) * sizeof(double)));
+  I.lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
+  I.th_part = reinterpret_cast<double*>(take(cells / 32 * sizeof(double)));
+  I.dF = p.precision == AP_DVM_FP32_DEV ? reinterpret_cast<float*>(take(6 * cells * sizeof(float))) : nullptr;
+  return align_up(off, 256);
+}
+
+// 1D symbol of the Laplacian stencil on DFT mode k (compact 3-point or 4th-order
+// 5-point second difference, Sec. 3.2), without cancellation for small k.
+void laplacian_symbol(int n, double h, int scheme, double* out, int count) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < count; ++k) {
+    const long double phi = 2.0L * pi * (long double)k / (long double)n;
+    const long double s = std::sin(0.5L * phi);
+    const long double s2 = s * s;
+    long double v;
+    if (scheme == AP_DVM_LF1_C2) v = -4.0L * s2 / ((long double)h * h);
+    else v = 2.0L * s2 * (std::cos(phi) - 7.0L) / (3.0L * (long double)h * h);
+    out[k] = (double)v;
+  }
+}
+
+size_t batch_bytes(int capacity, int nmax) {
+  size_t off = 0;
+  auto take = [&](size_t b) { off = align_up(off, 256); off += b; };
+  take(sizeof(BatchDev));
+  take(sizeof(InstDev) * capacity);
+  take(sizeof(int) * (capacity + 1));
+  take(sizeof(int) * (capacity + 1));
+  take(sizeof(int) * (capacity + 1));
+  take(sizeof(int) * 4);
+  take(sizeof(double2) * (nmax / 2));
+  take(sizeof(unsigned) * 4);
+  return align_up(off, 256);
+}
+
+int auto_tile(const ap_dvm_handle* h) {
+  int minx = 1 << 30, miny = 1 << 30;
+  for (const Slot& s : h->slots)
+    if (s.attached) { minx = std::min(minx, s.p.nx); miny = std::min(miny, s.p.ny); }
+  if (minx == (1 << 30)) { minx = h->tmpl.nx; miny = h->tmpl.ny; }
+  for (int t : {0, 1, 2, 3})
+    if (kTileX[t] <= minx && kTileY[t] <= miny) return t;
+  return 3;
+}
+
+StencilSet stencil_for(int f32, int scheme, int tile) {
+  if (!f32) {
+    if (scheme == AP_DVM_LF1_C2) return stencil_f64_lf1(tile);
+    if (scheme == AP_DVM_WENO3_C4) return stencil_f64_w3(tile);
+    return stencil_f64_w5(tile);
+  }
+  if (scheme == AP_DVM_LF1_C2) return stencil_f32_lf1(tile);
+  if (scheme == AP_DVM_WENO3_C4) return stencil_f32_w3(tile);
+  return stencil_f32_w5(tile);
+}
+
+ap_dvm_status occupancy_grid(ap_dvm_handle* h, const void* fn, int threads, size_t smem, int* grid) {
+  if (smem > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+  if (per_sm < 1) return fail(h, AP_DVM_ERR_UNSUPPORTED, "kernel does not fit on an SM (smem %zu)", smem);
+  *grid = per_sm * h->num_sms;
+  return AP_DVM_OK;
+}
+
+size_t fft_smem(const ap_dvm_handle* h) { return (size_t)h->eblk * 2 * (h->f32 ? 4 : 8); }
+
+ap_dvm_status prepare_kernels(ap_dvm_handle* h) {
+  if (h->kernels_ready) return AP_DVM_OK;
+  if (h->tile_auto) h->tile = auto_tile(h);
+  h->ks = stencil_for(h->f32, h->tmpl.space_scheme, h->tile);
+  h->km = misc_set(h->f32, h->tile);
+  const int thr = h->ks.tx * h->ks.ty;
+  ap_dvm_status st;
+  if ((st = occupancy_grid(h, h->ks.k_explicit, thr, h->ks.smem_explicit, &h->grid_explicit))) return st;
+  if ((st = occupancy_grid(h, h->ks.k_rhs, thr, h->ks.smem_rhs, &h->grid_rhs))) return st;
+  if ((st = occupancy_grid(h, h->ks.k_update, thr, h->ks.smem_update, &h->grid_update))) return st;
+  if ((st = occupancy_grid(h, h->km.k_finish, thr, 0, &h->grid_finish))) return st;
+  int g1 = 0, g2 = 0, g3 = 0;
+  if ((st = occupancy_grid(h, h->km.k_rows_fwd, 256, fft_smem(h), &g1))) return st;
+  if ((st = occupancy_grid(h, h->km.k_cols, 256, fft_smem(h), &g2))) return st;
+  if ((st = occupancy_grid(h, h->km.k_rows_inv, 256, fft_smem(h), &g3))) return st;
+  h->grid_fft = std::min(g1, std::min(g2, g3));
+  h->kernels_ready = true;
+  h->graph_valid = false;
+  return AP_DVM_OK;
+}
+
+// Rebuild and upload the compacted instance table and work decomposition.
+ap_dvm_status flush(ap_dvm_handle* h) {
+  ap_dvm_status st = prepare_kernels(h);
+  if (st) return st;
+  if (!h->dirty) return AP_DVM_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CUDA_TRY(h, cudaStreamIsCapturing(h->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(h, AP_DVM_ERR_ARG, "the set of solves changed while the stream is being captured");
+  const int TX = h->ks.tx, TY = h->ks.ty;
+  h->up_inst.clear();
+  h->up_tiles.assign(1, 0);
+  h->up_rows.assign(1, 0);
+  h->up_cols.assign(1, 0);
+  for (Slot& s : h->slots) {
+    if (!s.attached) continue;
+    if (s.p.nx < TX || s.p.ny < TY) return fail(h, AP_DVM_ERR_ARG, "grid %dx%d smaller than the tile %dx%d", s.p.nx, s.p.ny, TX, TY);
+    InstDev d = s.dev;
+    d.tiles_x = s.p.nx / TX;
+    d.tiles_y = s.p.ny / TY;
+    d.row_pairs = std::max(1, std::min(h->eblk / s.p.nx, s.p.ny / 2));
+    d.col_group = std::max(1, h->eblk / s.p.ny);
+    h->up_inst.push_back(d);
+    h->up_tiles.push_back(h->up_tiles.back() + d.tiles_x * d.tiles_y);
+    h->up_rows.push_back(h->up_rows.back() + (s.p.ny / 2 + d.row_pairs - 1) / d.row_pairs);
+    h->up_cols.push_back(h->up_cols.back() + (s.p.nx / 2 + 1 + d.col_group - 1) / d.col_group);
+  }
+  const int n = (int)h->up_inst.size();
+  h->n_active = n;
+  h->up_counts[0] = h->up_tiles.back();
+  h->up_counts[1] = h->up_rows.back();
+  h->up_counts[2] = h->up_cols.back();
+  h->up_counts[3] = n;
+  if (n > 0) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_inst, h->up_inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_tile_start, h->up_tiles.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_row_start, h->up_rows.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_col_start, h->up_cols.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_counts, h->up_counts, sizeof(int) * 4, cudaMemcpyHostToDevice, h->stream));
+  h->dirty = false;
+  return AP_DVM_OK;
+}
+
+ap_dvm_status launch(ap_dvm_handle* h, cudaStream_t stream, const void* fn, int grid, dim3 block, size_t smem, void** args) {
+  CUDA_TRY(h, cudaLaunchKernel(fn, dim3(grid), block, args, smem, stream));
+  return AP_DVM_OK;
+}
+
+// Kernels of one IMEX step for all attached solves (see the file header).
+ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream) {
+  const ap_dvm_params& t = h->tmpl;
+  const int s = t.s;
+  BatchDev* bp = h->d_batch;
+  const dim3 blk(h->ks.tx, h->ks.ty);
+  double weno_eps = t.weno_eps;
+  int f32 = h->f32;
+  ap_dvm_status st;
+  auto AEX = [&](int i, int j) { return t.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
+  auto AIM = [&](int i, int j) { return t.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
+  if (f32) {
+    void* a[] = {&bp};
+    if ((st = launch(h, stream, h->km.k_unpack, h->grid_finish, blk, 0, a))) return st;
+  }
+  for (int i = 2; i <= s; ++i) {
+    int j = i - 1;
+    unsigned need = 0;
+    for (int k = j + 1; k <= s; ++k) {
+      if (AEX(k, j) != 0.0) need |= 1u;                        // E^(j)
+      if (AIM(k, j) != 0.0) need |= 2u | 4u | 8u | 16u;        // D0.u, D_Delta theta, D0 theta, D_LF.B(v) of stage j
+    }
+    if (j == 1) need |= 2u;                                    // D0 . u^n enters every right-hand side
+    if (need) {
+      void* a[] = {&bp, &j, &need, &weno_eps};
+      if ((st = launch(h, stream, h->ks.k_explicit, h->grid_explicit, blk, h->ks.smem_explicit, a))) return st;
+    }
+    double sign = -1.0;                                        // reading G4
+    int first = (i == 2) ? 1 : 0;
+    {
+      void* a[] = {&bp, &i, &sign, &first};
+      if ((st = launch(h, stream, h->ks.k_rhs, h->grid_rhs, blk, h->ks.smem_rhs, a))) return st;
+    }
+    {
+      void* a[] = {&bp};
+      if ((st = launch(h, stream, h->km.k_rows_fwd, h->grid_fft, dim3(256), fft_smem(h), a))) return st;
+      void* b[] = {&bp, &i};
+      if ((st = launch(h, stream, h->km.k_cols, h->grid_fft, dim3(256), fft_smem(h), b))) return st;
+      if ((st = launch(h, stream, h->km.k_rows_inv, h->grid_fft, dim3(256), fft_smem(h), b))) return st;
+    }
+    {
+      void* a[] = {&bp, &i, &weno_eps};
+      if ((st = launch(h, stream, h->ks.k_update, h->grid_update, blk, h->ks.smem_update, a))) return st;
+    }
+  }
+  void* a[] = {&bp, &f32};
+  return launch(h, stream, h->km.k_finish, h->grid_finish, blk, 0, a);
+}
+
+ap_dvm_status build_graph(ap_dvm_handle* h) {
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  ap_dvm_status st = AP_DVM_OK;
+  for (int k = 0; k < h->graph_steps && st == AP_DVM_OK; ++k) st = enqueue_step(h, h->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (st) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) return fail(h, AP_DVM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, AP_DVM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  h->graph_valid = true;
+  return AP_DVM_OK;
+}
+
+Slot* slot_of(ap_dvm_handle* h, int slot) {
+  if (!h || slot < 0 || slot >= h->capacity || !h->slots[slot].attached) return nullptr;
+  return &h->slots[slot];
+}
+
+int grid_for_cells(size_t cells) { return (int)std::min<size_t>((cells + 255) / 256, 4096); }
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+void ap_dvm_default_params(ap_dvm_params* p, int nx, int ny, double eps, double dt) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->Lx = p->Ly = 2.0 * 3.14159265358979323846;
+  p->velocity_set = AP_DVM_D2V6;
+  p->eps = eps;
+  p->tau = 0.05;
+  p->mach = 1e-2;
+  p->rho0 = 1.0;
+  p->dt = dt;
+  p->s = 3;
+  const double c = 2.25, g = (c - 0.5) / (c - 1.0);
+  const int M = AP_DVM_MAX_STAGES;
+  p->A_ex[1 * M + 0] = c;
+  p->A_ex[2 * M + 0] = 1.0 - 1.0 / (2.0 * c);
+  p->A_ex[2 * M + 1] = 1.0 / (2.0 * c);
+  p->A_im[1 * M + 1] = c;
+  p->A_im[2 * M + 1] = 1.0 - g;
+  p->A_im[2 * M + 2] = g;
+  p->space_scheme = AP_DVM_WENO5_C4;
+  p->precision = AP_DVM_FP64;
+  p->weno_eps = 1e-6;
+}
+
+size_t ap_dvm_instance_workspace_size(const ap_dvm_params* p) {
+  char buf[256];
+  if (validate(p, buf, sizeof(buf)) != AP_DVM_OK) return 0;
+  return carve_instance(*p, nullptr, nullptr);
+}
+
+size_t ap_dvm_batch_workspace_size(const ap_dvm_params* tmpl, int capacity) {
+  char buf[256];
+  if (capacity < 1 || validate(tmpl, buf, sizeof(buf)) != AP_DVM_OK) return 0;
+  return batch_bytes(capacity, std::max(tmpl->nx, tmpl->ny));
+}
+
+size_t ap_dvm_workspace_size(const ap_dvm_params* p) {
+  const size_t a = ap_dvm_batch_workspace_size(p, 1), b = ap_dvm_instance_workspace_size(p);
+  return (a && b) ? a + b : 0;
+}
+
+ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void* d_workspace, size_t bytes,
+                                  void* cuda_stream, ap_dvm_handle** out) {
+  if (!out) return AP_DVM_ERR_ARG;
+  *out = nullptr;
+  ap_dvm_handle* h = new (std::nothrow) ap_dvm_handle();
+  if (!h) return AP_DVM_ERR_ARG;
+  *out = h;
+  ap_dvm_status st = validate(tmpl, h->err, sizeof(h->err));
+  if (st) return st;
+  if (capacity < 1) return fail(h, AP_DVM_ERR_ARG, "capacity must be >= 1");
+  h->tmpl = *tmpl;
+  h->capacity = capacity;
+  h->f32 = tmpl->precision == AP_DVM_FP32_DEV;
+  h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->nmax = std::max(tmpl->nx, tmpl->ny);
+  h->lnmax = ilog2(h->nmax);
+  h->eblk = std::max(2048, h->nmax);
+  const size_t need = batch_bytes(capacity, h->nmax);
+  if (!d_workspace || bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+    return fail(h, AP_DVM_ERR_WORKSPACE, "batch workspace needs %zu bytes, 256-byte aligned (got %zu)", need, bytes);
+  CUDA_TRY(h, cudaGetDevice(&h->device));
+  CUDA_TRY(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  char* base = reinterpret_cast<char*>(d_workspace);
+  size_t off = 0;
+  auto take = [&](size_t b) { off = align_up(off, 256); char* r = base + off; off += b; return r; };
+  h->d_batch = reinterpret_cast<BatchDev*>(take(sizeof(BatchDev)));
+  h->d_inst = reinterpret_cast<InstDev*>(take(sizeof(InstDev) * capacity));
+  h->d_tile_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
+  h->d_row_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
+  h->d_col_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
+  h->d_counts = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  h->d_tw = reinterpret_cast<double2*>(take(sizeof(double2) * (h->nmax / 2)));
+  h->d_err = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * 4));
+  // twiddles exp(-2 pi i k / nmax) from long double
+  std::vector<double2> tw(h->nmax / 2);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < h->nmax / 2; ++k) {
+    const long double a = -2.0L * pi * (long double)k / (long double)h->nmax;
+    tw[k].x = (double)std::cos(a);
+    tw[k].y = (double)std::sin(a);
+  }
+  BatchDev& hb = h->hb;
+  hb.inst = h->d_inst;
+  hb.tile_start = h->d_tile_start;
+  hb.row_start = h->d_row_start;
+  hb.col_start = h->d_col_start;
+  hb.counts = h->d_counts;
+  hb.tw = h->d_tw;
+  hb.lnmax = h->lnmax;
+  hb.s = tmpl->s;
+  for (int k = 0; k < APD_MAXS * APD_MAXS; ++k) { hb.A_ex[k] = tmpl->A_ex[k]; hb.A_im[k] = tmpl->A_im[k]; }
+  hb.err = h->d_err;
+  // synchronous uploads: the host vectors go out of scope
+  CUDA_TRY(h, cudaMemcpy(h->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_batch, &hb, sizeof(BatchDev), cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned) * 4));
+  int zeros[4] = {0, 0, 0, 0};
+  CUDA_TRY(h, cudaMemcpy(h->d_counts, zeros, sizeof(zeros), cudaMemcpyHostToDevice));
+  h->slots.resize(capacity);
+  h->dirty = true;
+  return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, void* d_workspace, size_t bytes) {
+  if (!h) return AP_DVM_ERR_ARG;
+  if (slot < 0 || slot >= h->capacity) return fail(h, AP_DVM_ERR_ARG, "slot %d out of range [0, %d)", slot, h->capacity);
+  if (h->slots[slot].attached) return fail(h, AP_DVM_ERR_ARG, "slot %d is in use", slot);
+  ap_dvm_status st = validate(p, h->err, sizeof(h->err));
+  if (st) return st;
+  if (!same_method(*p, h->tmpl)) return fail(h, AP_DVM_ERR_ARG, "scheme, precision and tableau must match the batch");
+  if (p->nx > h->tmpl.nx || p->ny > h->tmpl.ny) return fail(h, AP_DVM_ERR_ARG, "grid larger than the batch template");
+  const size_t need = carve_instance(*p, nullptr, nullptr);
+  if (!d_workspace || bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+    return fail(h, AP_DVM_ERR_WORKSPACE, "instance workspace needs %zu bytes, 256-byte aligned (got %zu)", need, bytes);
+  Slot& s = h->slots[slot];
+  s = Slot();
+  s.p = *p;
+  s.ws = reinterpret_cast<char*>(d_workspace);
+  s.bytes = bytes;
+  InstDev& d = s.dev;
+  carve_instance(*p, s.ws, &d);
+  d.nx = p->nx; d.ny = p->ny; d.lnx = ilog2(p->nx); d.lny = ilog2(p->ny);
+  d.dx = p->Lx / p->nx; d.dy = p->Ly / p->ny;
+  d.dt = p->dt; d.eps = p->eps; d.tau = tau_of(*p);
+  d.te2 = d.tau * p->eps * p->eps;
+  d.rho0 = p->rho0; d.amp = p->mach;
+  d.relax64 = (p->precision == AP_DVM_FP32_DEV && p->eps <= 1e-4) ? 1 : 0;
+  for (int i = 2; i <= p->s; ++i) {
+    const double a = p->A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+    d.kappa[i] = 2.0 * p->eps * p->eps / (p->dt * p->dt * a * a);
+    d.den[i] = d.te2 + p->dt * a;
+  }
+  std::vector<double> lx(p->nx / 2 + 1), ly(p->ny);
+  laplacian_symbol(p->nx, d.dx, p->space_scheme, lx.data(), (int)lx.size());
+  laplacian_symbol(p->ny, d.dy, p->space_scheme, ly.data(), (int)ly.size());
+  CUDA_TRY(h, cudaMemcpyAsync(d.lamx, lx.data(), sizeof(double) * lx.size(), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(d.lamy, ly.data(), sizeof(double) * ly.size(), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));   // the symbol vectors are about to go out of scope
+  CUDA_TRY(h, cudaMemsetAsync(d.X, 0, (size_t)6 * p->nx * p->ny * (h->f32 ? 4 : 8), h->stream));
+  if (d.dF) CUDA_TRY(h, cudaMemsetAsync(d.dF, 0, (size_t)6 * p->nx * p->ny * sizeof(float), h->stream));
+  s.attached = true;
+  h->dirty = true;
+  if (h->tile_auto) {
+    const int t = auto_tile(h);
+    if (t != h->tile || !h->kernels_ready) { h->tile = t; h->kernels_ready = false; }
+  }
+  return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_detach(ap_dvm_handle* h, int slot) {
+  if (!slot_of(h, slot)) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
+  h->slots[slot].attached = false;
+  h->dirty = true;
+  return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_create(const ap_dvm_params* p, void* d_workspace, size_t bytes, void* cuda_stream, ap_dvm_handle** out) {
+  if (!out) return AP_DVM_ERR_ARG;
+  const size_t a = ap_dvm_batch_workspace_size(p, 1), b = ap_dvm_instance_workspace_size(p);
+  ap_dvm_status st = ap_dvm_batch_create(p, 1, d_workspace, bytes, cuda_stream, out);
+  if (st) return st;
+  if (bytes < a + b) return fail(*out, AP_DVM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", a + b, bytes);
+  return ap_dvm_attach(*out, 0, p, reinterpret_cast<char*>(d_workspace) + a, bytes - a);
+}
+
+static ap_dvm_status set_state_impl(ap_dvm_handle* h, int slot, const double* a, const double* b, const double* c,
+                                    const float* f, int mode) {
+  Slot* s = slot_of(h, slot);
+  if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
+  ap_dvm_status st = prepare_kernels(h);
+  if (st) return st;
+  InstDev d = s->dev;
+  int f32 = h->f32;
+  void* args[] = {&d, &a, &b, &c, &f, &mode, &f32};
+  return launch(h, h->stream, h->km.k_set_state, grid_for_cells((size_t)s->p.nx * s->p.ny), dim3(256), 0, args);
+}
+
+static ap_dvm_status get_state_impl(ap_dvm_handle* h, int slot, double* out, float* out32, int what,
+                                    double* o1 = nullptr, double* o2 = nullptr, double* o3 = nullptr) {
+  Slot* s = slot_of(h, slot);
+  if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
+  ap_dvm_status st = prepare_kernels(h);
+  if (st) return st;
+  InstDev d = s->dev;
+  int f32 = h->f32;
+  void* args[] = {&d, &out, &o1, &o2, &o3, &out32, &what, &f32};
+  return launch(h, h->stream, h->km.k_get_state, grid_for_cells((size_t)s->p.nx * s->p.ny), dim3(256), 0, args);
+}
+
+ap_dvm_status ap_dvm_set_state(ap_dvm_handle* h, int slot, const double* d_moments6) {
+  if (!d_moments6) return h ? fail(h, AP_DVM_ERR_ARG, "null state pointer") : AP_DVM_ERR_ARG;
+  return set_state_impl(h, slot, d_moments6, nullptr, nullptr, nullptr, 0);
+}
+
+ap_dvm_status ap_dvm_set_equilibrium(ap_dvm_handle* h, int slot, const double* d_u1, const double* d_u2, const double* d_p) {
+  if (!d_u1 || !d_u2 || !d_p) return h ? fail(h, AP_DVM_ERR_ARG, "null pointer") : AP_DVM_ERR_ARG;
+  return set_state_impl(h, slot, d_u1, d_u2, d_p, nullptr, 1);
+}
+
+ap_dvm_status ap_dvm_set_populations(ap_dvm_handle* h, int slot, const void* d_dF6, int is_float) {
+  if (!d_dF6) return h ? fail(h, AP_DVM_ERR_ARG, "null pointer") : AP_DVM_ERR_ARG;
+  if (is_float && h && !h->f32) return fail(h, AP_DVM_ERR_ARG, "float populations need the FP32 form");
+  if (is_float) return set_state_impl(h, slot, nullptr, nullptr, nullptr, reinterpret_cast<const float*>(d_dF6), 3);
+  return set_state_impl(h, slot, reinterpret_cast<const double*>(d_dF6), nullptr, nullptr, nullptr, 2);
+}
+
+ap_dvm_status ap_dvm_get_state(ap_dvm_handle* h, int slot, double* d_moments6) {
+  if (!d_moments6) return h ? fail(h, AP_DVM_ERR_ARG, "null pointer") : AP_DVM_ERR_ARG;
+  return get_state_impl(h, slot, d_moments6, nullptr, 0);
+}
+
+ap_dvm_status ap_dvm_get_populations(ap_dvm_handle* h, int slot, void* d_dF6, int is_float) {
+  if (!d_dF6) return h ? fail(h, AP_DVM_ERR_ARG, "null pointer") : AP_DVM_ERR_ARG;
+  if (is_float) return get_state_impl(h, slot, nullptr, reinterpret_cast<float*>(d_dF6), 3);
+  return get_state_impl(h, slot, reinterpret_cast<double*>(d_dF6), nullptr, 2);
+}
+
+ap_dvm_status ap_dvm_moments(ap_dvm_handle* h, int slot, double* d_rho, double* d_u1, double* d_u2, double* d_p) {
+  Slot* s = slot_of(h, slot);
+  if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
+  if (!d_rho || !d_u1 || !d_u2 || !d_p) return fail(h, AP_DVM_ERR_ARG, "null pointer");
+  return get_state_impl(h, slot, d_rho, nullptr, 1, d_u1, d_u2, d_p);
+}
+
+ap_dvm_status ap_dvm_step(ap_dvm_handle* h, int nsteps) {
+  if (!h) return AP_DVM_ERR_ARG;
+  if (nsteps < 0) return fail(h, AP_DVM_ERR_ARG, "nsteps must be >= 0");
+  ap_dvm_status st = flush(h);
+  if (st) return st;
+  if (h->n_active == 0 || nsteps == 0) return AP_DVM_OK;
+  int done = 0;
+  if (h->graph_steps > 0) {
+    if (!h->graph_valid && (st = build_graph(h))) return st;
+    while (nsteps - done >= h->graph_steps) {
+      CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+      done += h->graph_steps;
+    }
+  }
+  for (; done < nsteps; ++done)
+    if ((st = enqueue_step(h, h->stream))) return st;
+  return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_set_graph_steps(ap_dvm_handle* h, int k) {
+  if (!h) return AP_DVM_ERR_ARG;
+  if (k < 0) return fail(h, AP_DVM_ERR_ARG, "k must be >= 0");
+  if (k != h->graph_steps) { h->graph_steps = k; h->graph_valid = false; }
+  return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_set_tile(ap_dvm_handle* h, int tile) {
+  if (!h) return AP_DVM_ERR_ARG;
+  if (tile < -1 || tile >= kNumTiles) return fail(h, AP_DVM_ERR_ARG, "tile index out of range");
+  const bool aut = tile < 0;
+  const int t = aut ? auto_tile(h) : tile;
+  for (const Slot& s : h->slots)
+    if (s.attached && (s.p.nx < kTileX[t] || s.p.ny < kTileY[t])) return fail(h, AP_DVM_ERR_ARG, "an attached grid is smaller than the tile");
+  h->tile_auto = aut;
+  if (t != h->tile || !h->kernels_ready) { h->tile = t; h->kernels_ready = false; h->dirty = true; }
+  return AP_DVM_OK;
+}
+
+int ap_dvm_get_tile(const ap_dvm_handle* h) { return h ? h->tile : -1; }
+
+int ap_dvm_launches_per_step(const ap_dvm_handle* h) {
+  if (!h) return 0;
+  const ap_dvm_params& t = h->tmpl;
+  int n = h->f32 ? 1 : 0;
+  for (int i = 2; i <= t.s; ++i) {
+    const int j = i - 1;
+    bool need = (j == 1);
+    for (int k = j + 1; k <= t.s; ++k)
+      need |= t.A_ex[(k - 1) * AP_DVM_MAX_STAGES + (j - 1)] != 0.0 || t.A_im[(k - 1) * AP_DVM_MAX_STAGES + (j - 1)] != 0.0;
+    n += (need ? 1 : 0) + 5;
+  }
+  return n + 1;
+}
+
+ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage, int nsteps) {
+  Slot* s = slot_of(h, slot);
+  if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
+  if (!h_in || !h_out || !d_stage) return fail(h, AP_DVM_ERR_ARG, "null pointer");
+  const size_t bytes = (size_t)6 * s->p.nx * s->p.ny * sizeof(double);
+  CUDA_TRY(h, cudaMemcpyAsync(d_stage, h_in, bytes, cudaMemcpyHostToDevice, h->stream));
+  ap_dvm_status st;
+  if ((st = ap_dvm_set_state(h, slot, d_stage))) return st;
+  if ((st = ap_dvm_step(h, nsteps))) return st;
+  if ((st = ap_dvm_get_state(h, slot, d_stage))) return st;
+  CUDA_TRY(h, cudaMemcpyAsync(h_out, d_stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h) {
+  if (!h) return AP_DVM_ERR_ARG;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaGetLastError());
+  unsigned flags = 0;
+  CUDA_TRY(h, cudaMemcpy(&flags, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (flags & 1u) {
+    CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
+    return fail(h, AP_DVM_ERR_NONFINITE, "a step produced a non-finite value");
+  }
+  return AP_DVM_OK;
+}
+
+const char* ap_dvm_last_error(const ap_dvm_handle* h) { return h ? h->err : "null handle"; }
+
+void ap_dvm_destroy(ap_dvm_handle* h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Shared device-side definitions of the AP IMEX-RK D2V6 library.
+//
+// Layout in HBM: every field is a "plane" of nx*ny values, row-major with x
+// fastest (index j*nx + i, cell centre ((i+1/2)dx, (j+1/2)dy)), structure of
+// arrays.  A moment state is 6 consecutive planes (u1, u2, theta, v1, v2, q).
+// All kernels are persistent grid-stride loops over a device-resident work
+// list, so one launch covers every instance of a batch whatever their sizes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#define APD_MAXS 4          // maximum number of IMEX stages
+#define APD_NPLANES_STATE 6
+
+namespace apd {
+
+enum Scheme { LF1_C2 = 0, WENO3_C4 = 1, WENO5_C4 = 2 };
+
+// Halo width of the per-cell operators of each spatial scheme (Sec. 3.2):
+// LF1 fluxes and 2nd-order central differences reach 1 cell, WENO3 fluxes
+// and 4th-order central differences 2, WENO5 fluxes 3.
+__host__ __device__ constexpr int halo_of(int scheme) { return scheme == LF1_C2 ? 1 : (scheme == WENO3_C4 ? 2 : 3); }
+__host__ __device__ constexpr int central_halo(int scheme) { return scheme == LF1_C2 ? 1 : 2; }
+
+// Per-instance description, resident in device memory.  Plane pointers are
+// untyped: the scalar type is the batch's transport type T (double for the
+// FP64 form, float for the FP32-deviation form).
+struct InstDev {
+  int nx, ny, lnx, lny;         // sizes and their log2
+  int tiles_x, tiles_y;         // tile grid for the batch's tile shape
+  int row_pairs;                // row pairs per row-FFT work item
+  int col_group;                // spectral columns per column-FFT work item
+  int relax64;                  // FP32 form: closed-form relaxation in FP64
+  int sstride;                  // complex elements per spectral row (>= nx/2 + 1)
+  double dx, dy, dt, eps, tau, te2, rho0, amp;
+  double kappa[APD_MAXS + 1];   // kappa_i = 2 eps^2/(dt^2 a_ii^2), by stage i (1-based)
+  double den[APD_MAXS + 1];     // tau eps^2 + dt a_ii
+  void* X;                      // 6 planes: state at t^n (moments)
+  void* Xs[APD_MAXS + 1];       // stage values X^(j), j = 2..s (6 planes); Xs[s] = next state
+  void* E[APD_MAXS + 1];        // explicit term of step 1 for stage j (2 planes)
+  void* Du[APD_MAXS + 1];       // D_0 . u^(j)
+  void* Lth[APD_MAXS + 1];      // D_Delta theta^(j)
+  void* Gth[APD_MAXS + 1];      // D_0 theta^(j) (2 planes)
+  void* DLFB[APD_MAXS + 1];     // D_LF . B(v^(j)) with partner u^(j) (2 planes)
+  void* Dv[APD_MAXS + 1];       // D0_LF . v^(j)
+  void* DB[APD_MAXS + 1];       // D_0^2 : B(v^(j))
+  void* R;                      // Helmholtz right-hand side
+  void* S;                      // half spectrum, complex T, ny rows x sstride
+  double* lamx;                 // 1D Laplacian symbol in x, kx = 0..nx/2
+  double* lamy;                 // 1D Laplacian symbol in y, ky = 0..ny-1
+  double* th_part;              // per-tile partial sums of theta^n
+  float* dF;                    // FP32 form: deviation populations (6 planes)
+};
+
+// Work decomposition of the active instances: item ranges per instance are
+// prefix sums (start[k] .. start[k+1]); an item is decoded by binary search.
+struct BatchDev {
+  InstDev* inst;         // active instances, compacted
+  int* tile_start;       // [n+1]
+  int* row_start;        // [n+1]
+  int* col_start;        // [n+1]
+  int* counts;           // [0] tiles, [1] row items, [2] column items, [3] instances
+  double2* tw;           // twiddles exp(-2 pi i k / nmax), k < nmax/2
+  int lnmax;             // log2 of the largest transform length
+  int s;                 // stages
+  double A_ex[APD_MAXS * APD_MAXS];
+  double A_im[APD_MAXS * APD_MAXS];
+  unsigned* err;         // device error flags (bit 0: non-finite state)
+};
+
+// Instance owning work item `item`: the last k with start[k] <= item.
+__device__ __forceinline__ int find_inst(const int* __restrict__ start, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Row-major tableau access, 1-based stage indices as in the paper.
+__device__ __forceinline__ double aex(const BatchDev& b, int i, int j) { return b.A_ex[(i - 1) * APD_MAXS + (j - 1)]; }
+__device__ __forceinline__ double aim(const BatchDev& b, int i, int j) { return b.A_im[(i - 1) * APD_MAXS + (j - 1)]; }
+
+// ---------------------------------------------------------------------------
+// Jiang-Shu WENO reconstructions at x_{i+1/2} from the left-biased stencil.
+// The nonlinear weights alpha_k = d_k/(eps_W + beta_k)^2 are normalised with
+// a single division: multiplying every alpha_k by prod_m (eps_W + beta_m)^2
+// gives alpha'_k = d_k prod_{m != k} (eps_W + beta_m)^2, the same weights.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T ew) {
+  const T p0 = (T(2) * a - T(7) * b + T(11) * c) * T(1.0 / 6.0);
+  const T p1 = (-b + T(5) * c + T(2) * d) * T(1.0 / 6.0);
+  const T p2 = (T(2) * c + T(5) * d - e) * T(1.0 / 6.0);
+  const T c0 = a - T(2) * b + c, l0 = a - T(4) * b + T(3) * c;
+  const T c1 = b - T(2) * c + d, l1 = b - d;
+  const T c2 = c - T(2) * d + e, l2 = T(3) * c - T(4) * d + e;
+  const T b0 = T(13.0 / 12.0) * c0 * c0 + T(0.25) * l0 * l0;
+  const T b1 = T(13.0 / 12.0) * c1 * c1 + T(0.25) * l1 * l1;
+  const T b2 = T(13.0 / 12.0) * c2 * c2 + T(0.25) * l2 * l2;
+  T s0 = ew + b0; s0 *= s0;
+  T s1 = ew + b1; s1 *= s1;
+  T s2 = ew + b2; s2 *= s2;
+  const T w0 = T(0.1) * (s1 * s2);
+  const T w1 = T(0.6) * (s0 * s2);
+  const T w2 = T(0.3) * (s0 * s1);
+  return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
+}
+
+template <typename T>
+__device__ __forceinline__ T weno3(T a, T b, T c, T ew) {
+  const T p0 = (T(3) * b - a) * T(0.5);
+  const T p1 = (b + c) * T(0.5);
+  T s0 = ew + (b - a) * (b - a); s0 *= s0;
+  T s1 = ew + (c - b) * (c - b); s1 *= s1;
+  const T w0 = T(1.0 / 3.0) * s1;
+  const T w1 = T(2.0 / 3.0) * s0;
+  return (w0 * p0 + w1 * p1) / (w0 + w1);
+}
+
+// Central first difference (Sec. 3.2 D_0; fourth order under the WENO schemes)
+// along a line with stride st, times 1/h.
+template <typename T, int SCHEME>
+__device__ __forceinline__ T cdiff(const T* f, int st, T inv_h) {
+  if (SCHEME == LF1_C2) return (f[st] - f[-st]) * (T(0.5) * inv_h);
+  return (-f[2 * st] + T(8) * f[st] - T(8) * f[-st] + f[-2 * st]) * (inv_h * T(1.0 / 12.0));
+}
+
+// Central second difference along a line, times 1/h^2 (compact 3-point or 5-point).
+template <typename T, int SCHEME>
+__device__ __forceinline__ T cdiff2(const T* f, int st, T inv_h2) {
+  if (SCHEME == LF1_C2) return (f[st] - T(2) * f[0] + f[-st]) * inv_h2;
+  return (-f[2 * st] + T(16) * f[st] - T(30) * f[0] + T(16) * f[-st] - f[-2 * st]) * (inv_h2 * T(1.0 / 12.0));
+}
+
+template <typename T> __device__ __forceinline__ T* P(void* p, size_t k, size_t plane) { return reinterpret_cast<T*>(p) + k * plane; }
+
+}  // namespace apd

@@ -1,0 +1,38 @@
+// Kernel tables shared between the instantiation units and the host API.
+#pragma once
+#include <cstddef>
+
+namespace apd {
+
+// Tile shapes of the stencil kernels (index = ap_dvm_set_tile argument).
+constexpr int kNumTiles = 5;
+constexpr int kTileX[kNumTiles] = {32, 32, 16, 8, 64};
+constexpr int kTileY[kNumTiles] = {8, 4, 8, 8, 4};
+
+struct StencilSet {
+  const void* k_explicit;
+  const void* k_rhs;
+  const void* k_update;
+  size_t smem_explicit, smem_rhs, smem_update;
+  int tx, ty;
+};
+
+struct MiscSet {
+  const void* k_finish;    // per tile shape
+  const void* k_unpack;    // FP32 form only
+  const void* k_rows_fwd;
+  const void* k_cols;
+  const void* k_rows_inv;
+  const void* k_set_state;
+  const void* k_get_state;
+};
+
+StencilSet stencil_f64_lf1(int tile);
+StencilSet stencil_f64_w3(int tile);
+StencilSet stencil_f64_w5(int tile);
+StencilSet stencil_f32_lf1(int tile);
+StencilSet stencil_f32_w3(int tile);
+StencilSet stencil_f32_w5(int tile);
+MiscSet misc_set(int f32form, int tile);
+
+}  // namespace apd

@@ -1,0 +1,210 @@
+// Periodic Helmholtz solve of Algorithm 1, step 2:
+//     (D_Delta - kappa_i) theta^(i) = R_i
+// by diagonalisation in the discrete Fourier basis (the operator is periodic
+// with constant coefficients, so every DFT mode is an eigenvector with
+// eigenvalue lam_x(kx) + lam_y(ky) - kappa_i).  Three passes:
+//   k_fft_rows_fwd : real row DFTs of R (two rows packed as one complex row),
+//                    written as the half spectrum S[y][0..nx/2];
+//   k_fft_cols     : per spectral column, DFT along y, division by the
+//                    symbol (mode k = 0 set to mean(theta^n), reading G5),
+//                    inverse DFT along y, scaled by 1/(nx ny);
+//   k_fft_rows_inv : inverse real row DFTs into theta^(i).
+// Radix-2 in shared memory: decimation in time from bit-reversed order for
+// the forward transforms, decimation in frequency (natural in, bit-reversed
+// out) for the inverse ones, so no permutation pass is needed.
+#pragma once
+#include "common.cuh"
+
+namespace apd {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+
+__device__ __forceinline__ int brev(int k, int ln) { return (int)(__brev((unsigned)k) >> (32 - ln)); }
+
+// ntr transforms of length n = 2^ln held back to back in x[], input in
+// bit-reversed order, output natural.  Twiddle W_m^p = tw[p * nmax/m].
+template <typename T>
+__device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int ntr, const double2* __restrict__ tw, int lnmax,
+                                        bool inv, int tid, int nthr) {
+  const int n = 1 << ln, nb = ntr * (n >> 1);
+  for (int s = 1; s <= ln; ++s) {
+    const int half = 1 << (s - 1), sh = lnmax - s;
+    for (int k = tid; k < nb; k += nthr) {
+      const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
+      const int pos = bi & (half - 1), grp = bi >> (s - 1);
+      const int i0 = t * n + grp * 2 * half + pos, i1 = i0 + half;
+      const double2 w = tw[pos << sh];
+      const T wr = T(w.x), wi = inv ? T(-w.y) : T(w.y);
+      const auto a = x[i0], bb = x[i1];
+      const T tr = wr * bb.x - wi * bb.y, ti = wr * bb.y + wi * bb.x;
+      x[i1].x = a.x - tr; x[i1].y = a.y - ti;
+      x[i0].x = a.x + tr; x[i0].y = a.y + ti;
+    }
+    __syncthreads();
+  }
+}
+
+// Natural-order input, bit-reversed output.
+template <typename T>
+__device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int ntr, const double2* __restrict__ tw, int lnmax,
+                                        bool inv, int tid, int nthr) {
+  const int n = 1 << ln, nb = ntr * (n >> 1);
+  for (int s = ln; s >= 1; --s) {
+    const int half = 1 << (s - 1), sh = lnmax - s;
+    for (int k = tid; k < nb; k += nthr) {
+      const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
+      const int pos = bi & (half - 1), grp = bi >> (s - 1);
+      const int i0 = t * n + grp * 2 * half + pos, i1 = i0 + half;
+      const double2 w = tw[pos << sh];
+      const T wr = T(w.x), wi = inv ? T(-w.y) : T(w.y);
+      const auto a = x[i0], bb = x[i1];
+      const T dr = a.x - bb.x, di = a.y - bb.y;
+      x[i0].x = a.x + bb.x; x[i0].y = a.y + bb.y;
+      x[i1].x = wr * dr - wi * di; x[i1].y = wr * di + wi * dr;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const BatchDev& b = *bp;
+  const int nitems = b.counts[1], tid = threadIdx.x, nthr = blockDim.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k_inst = find_inst(b.row_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const int n = I.nx, ln = I.lnx, ss = I.sstride;
+    const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
+    const int ntr = min(I.row_pairs, (I.ny >> 1) - pair0);
+    const T* R = reinterpret_cast<const T*>(I.R);
+    for (int e = tid; e < ntr * n; e += nthr) {
+      const int p = e >> ln, k = e & (n - 1);
+      const size_t row = (size_t)(2 * (pair0 + p));
+      C z; z.x = R[row * n + k]; z.y = R[(row + 1) * n + k];
+      x[p * n + brev(k, ln)] = z;
+    }
+    __syncthreads();
+    fft_dit<T>(x, ln, ntr, b.tw, b.lnmax, false, tid, nthr);
+    C* S = reinterpret_cast<C*>(I.S);
+    const int nh = (n >> 1) + 1;
+    for (int e = tid; e < ntr * nh; e += nthr) {
+      const int p = e / nh, k = e - p * nh;
+      const C zk = x[p * n + k], zm = x[p * n + ((n - k) & (n - 1))];
+      const size_t row = (size_t)(2 * (pair0 + p));
+      C A, B;
+      A.x = T(0.5) * (zk.x + zm.x); A.y = T(0.5) * (zk.y - zm.y);
+      B.x = T(0.5) * (zk.y + zm.y); B.y = T(-0.5) * (zk.x - zm.x);
+      S[row * ss + k] = A;
+      S[(row + 1) * ss + k] = B;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[8];
+  __shared__ double s_mean;
+  const BatchDev& b = *bp;
+  const int nitems = b.counts[2], tid = threadIdx.x, nthr = blockDim.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k_inst = find_inst(b.col_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const int n = I.ny, ln = I.lny, ss = I.sstride, nh = (I.nx >> 1) + 1;
+    const int col0 = (it - b.col_start[k_inst]) * I.col_group;
+    const int ntr = min(I.col_group, nh - col0);
+    if (col0 == 0) {
+      // mean(theta^n) from the per-tile partial sums, in a fixed order
+      const int nt = I.tiles_x * I.tiles_y;
+      double acc = 0.0;
+      for (int k = tid; k < nt; k += nthr) acc += I.th_part[k];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if ((tid & 31) == 0) red[tid >> 5] = acc;
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < (nthr + 31) / 32; ++w) sum += red[w];
+        s_mean = sum / ((double)I.nx * (double)I.ny);
+      }
+      __syncthreads();
+    }
+    C* S = reinterpret_cast<C*>(I.S);
+    for (int e = tid; e < ntr * n; e += nthr) {
+      const int g = e >> ln, y = e & (n - 1);
+      x[g * n + brev(y, ln)] = S[(size_t)y * ss + col0 + g];
+    }
+    __syncthreads();
+    fft_dit<T>(x, ln, ntr, b.tw, b.lnmax, false, tid, nthr);
+    const double kap = I.kappa[i];
+    const double scale = 1.0 / ((double)I.nx * (double)I.ny);
+    for (int e = tid; e < ntr * n; e += nthr) {
+      const int g = e >> ln, ky = e & (n - 1), kx = col0 + g;
+      C v = x[e];
+      if (kx == 0 && ky == 0) {
+        v.x = T(s_mean); v.y = T(0);
+      } else {
+        const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
+        v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
+      }
+      x[e] = v;
+    }
+    __syncthreads();
+    fft_dif<T>(x, ln, ntr, b.tw, b.lnmax, true, tid, nthr);
+    for (int e = tid; e < ntr * n; e += nthr) {
+      const int g = e >> ln, y = e & (n - 1);
+      S[(size_t)y * ss + col0 + g] = x[g * n + brev(y, ln)];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const BatchDev& b = *bp;
+  const int nitems = b.counts[1], tid = threadIdx.x, nthr = blockDim.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k_inst = find_inst(b.row_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const int n = I.nx, ln = I.lnx, ss = I.sstride;
+    const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
+    const int ntr = min(I.row_pairs, (I.ny >> 1) - pair0);
+    const C* S = reinterpret_cast<const C*>(I.S);
+    for (int e = tid; e < ntr * n; e += nthr) {
+      const int p = e >> ln, k = e & (n - 1);
+      const size_t row = (size_t)(2 * (pair0 + p));
+      C A, B;
+      if (k <= (n >> 1)) {
+        A = S[row * ss + k]; B = S[(row + 1) * ss + k];
+      } else {
+        A = S[row * ss + (n - k)]; B = S[(row + 1) * ss + (n - k)];
+        A.y = -A.y; B.y = -B.y;
+      }
+      C z; z.x = A.x - B.y; z.y = A.y + B.x;
+      x[e] = z;
+    }
+    __syncthreads();
+    fft_dif<T>(x, ln, ntr, b.tw, b.lnmax, true, tid, nthr);
+    T* th = reinterpret_cast<T*>(I.Xs[i]) + 2 * (size_t)I.nx * I.ny;
+    for (int e = tid; e < ntr * n; e += nthr) {
+      const int p = e >> ln, m = e & (n - 1);
+      const size_t row = (size_t)(2 * (pair0 + p));
+      const C z = x[p * n + brev(m, ln)];
+      th[row * n + m] = z.x;
+      th[(row + 1) * n + m] = z.y;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace apd

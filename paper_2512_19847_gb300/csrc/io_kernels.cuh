@@ -1,0 +1,187 @@
+// State input/output and the population view (Sec. 2.1).
+//
+// Population view (D2V6, c_i = (cos(pi(i-1)/3), sin(pi(i-1)/3))): the
+// deviation populations dF_i = F_i - rho0/6 relate to the moments through
+// f = dF/(rho0 A) and the six rescaled moments of Sec. 2.1,
+//   sum f = 2 eps theta, sum c f = u, sum (c1^2 - 1/2) f = -eps v1,
+//   sum c1 c2 f = eps v2, sum c1 (c2^2 - 1/4) f = eps^2 q,
+// (sign of v1: reading G1).  Opposite velocities c_{k+3} = -c_k make even
+// and odd pair sums s_k = f_k + f_{k+3}, d_k = f_k - f_{k+3} the natural
+// variables; both directions of the map are evaluated in FP64.
+#pragma once
+#include "common.cuh"
+
+namespace apd {
+
+constexpr double SQ3 = 1.7320508075688772935;
+
+// dF (six values) -> moments (u1, u2, theta, v1, v2, q)
+__device__ __forceinline__ void pop_to_mom(const double* dF, double eps, double rho0, double amp, double* m) {
+  const double s1 = dF[0] + dF[3], s2 = dF[1] + dF[4], s3 = dF[2] + dF[5];
+  const double d1 = dF[0] - dF[3], d2 = dF[1] - dF[4], d3 = dF[2] - dF[5];
+  const double M0 = s1 + s2 + s3;
+  const double M1 = d1 + 0.5 * (d2 - d3);
+  const double M2 = 0.5 * SQ3 * (d2 + d3);
+  const double M3 = 0.5 * s1 - 0.25 * (s2 + s3);
+  const double M4 = 0.25 * SQ3 * (s2 - s3);
+  const double M5 = 0.25 * (d2 - d1 - d3);
+  const double inv = 1.0 / (rho0 * amp);
+  m[0] = M1 * inv;
+  m[1] = M2 * inv;
+  m[2] = M0 * inv / (2.0 * eps);
+  m[3] = -M3 * inv / eps;
+  m[4] = M4 * inv / eps;
+  m[5] = M5 * inv / (eps * eps);
+}
+
+// moments -> dF
+__device__ __forceinline__ void mom_to_pop(const double* m, double eps, double rho0, double amp, double* dF) {
+  const double M0 = 2.0 * eps * m[2], M1 = m[0], M2 = m[1];
+  const double M3 = -eps * m[3], M4 = eps * m[4], M5 = eps * eps * m[5];
+  const double S1 = M0 / 6.0 + (2.0 / 3.0) * M3;
+  const double S2 = M0 / 6.0 - M3 / 3.0 + (SQ3 / 3.0) * M4;
+  const double S3 = M0 / 6.0 - M3 / 3.0 - (SQ3 / 3.0) * M4;
+  const double D1 = M1 / 3.0 - (2.0 / 3.0) * M5;
+  const double D2 = M1 / 6.0 + (SQ3 / 6.0) * M2 + (2.0 / 3.0) * M5;
+  const double D3 = -M1 / 6.0 + (SQ3 / 6.0) * M2 - (2.0 / 3.0) * M5;
+  const double a = rho0 * amp;
+  dF[0] = a * (S1 + D1); dF[3] = a * (S1 - D1);
+  dF[1] = a * (S2 + D2); dF[4] = a * (S2 - D2);
+  dF[2] = a * (S3 + D3); dF[5] = a * (S3 - D3);
+}
+
+// ---- per-instance conversions (one instance, grid-stride over cells)
+
+// mode 0: moments (double) -> state;  mode 1: equilibrium from (u1, u2, p);
+// mode 2: populations dF (double) -> state;  mode 3: populations (float) -> state (FP32 form copy)
+template <typename T>
+__global__ void k_set_state(InstDev I, const double* __restrict__ a, const double* __restrict__ b2,
+                            const double* __restrict__ c3, const float* __restrict__ f32, int mode, int f32form) {
+  const size_t pl = (size_t)I.nx * I.ny;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < pl; o += (size_t)gridDim.x * blockDim.x) {
+    double m[6];
+    if (mode == 0) {
+      for (int k = 0; k < 6; ++k) m[k] = a[o + k * pl];
+    } else if (mode == 1) {
+      const double u1 = a[o], u2 = b2[o], p = c3[o];
+      m[0] = u1; m[1] = u2;
+      m[2] = p + 0.5 * (u1 * u1 + u2 * u2);     // theta = p + |u|^2/2
+      m[3] = 0.5 * (u2 * u2 - u1 * u1);         // v = F(u)
+      m[4] = u1 * u2;
+      m[5] = 0.0;
+    } else if (mode == 2) {
+      double d[6];
+      for (int k = 0; k < 6; ++k) d[k] = a[o + k * pl];
+      if (f32form) {
+        for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = float(d[k]);
+        continue;
+      }
+      pop_to_mom(d, I.eps, I.rho0, I.amp, m);
+    } else {
+      for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = f32[o + k * pl];
+      continue;
+    }
+    if (f32form) {
+      double d[6];
+      mom_to_pop(m, I.eps, I.rho0, I.amp, d);
+      for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = float(d[k]);
+    } else {
+      T* X = reinterpret_cast<T*>(I.X);
+      for (int k = 0; k < 6; ++k) X[o + k * pl] = T(m[k]);
+    }
+  }
+}
+
+// what 0: moments (double, 6 planes at out) ; 1: outputs rho, u1, u2, p (planes out, o1, o2, o3);
+// 2: populations (double, 6 planes at out) ; 3: populations (float, 6 planes at out32)
+template <typename T>
+__global__ void k_get_state(InstDev I, double* __restrict__ out, double* __restrict__ o1, double* __restrict__ o2,
+                            double* __restrict__ o3, float* __restrict__ out32, int what, int f32form) {
+  const size_t pl = (size_t)I.nx * I.ny;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < pl; o += (size_t)gridDim.x * blockDim.x) {
+    double m[6], d[6];
+    if (f32form) {
+      for (int k = 0; k < 6; ++k) d[k] = double(I.dF[o + k * pl]);
+      if (what == 3) { for (int k = 0; k < 6; ++k) out32[o + k * pl] = I.dF[o + k * pl]; continue; }
+      if (what == 2) { for (int k = 0; k < 6; ++k) out[o + k * pl] = d[k]; continue; }
+      pop_to_mom(d, I.eps, I.rho0, I.amp, m);
+    } else {
+      const T* X = reinterpret_cast<const T*>(I.X);
+      for (int k = 0; k < 6; ++k) m[k] = double(X[o + k * pl]);
+    }
+    if (what == 0) {
+      for (int k = 0; k < 6; ++k) out[o + k * pl] = m[k];
+    } else if (what == 1) {
+      out[o] = I.rho0 * (1.0 + 2.0 * I.amp * I.eps * m[2]);
+      o1[o] = m[0];
+      o2[o] = m[1];
+      o3[o] = m[2] - 0.5 * (m[0] * m[0] + m[1] * m[1]);
+    } else {
+      mom_to_pop(m, I.eps, I.rho0, I.amp, d);
+      if (what == 2) for (int k = 0; k < 6; ++k) out[o + k * pl] = d[k];
+      else for (int k = 0; k < 6; ++k) out32[o + k * pl] = float(d[k]);
+    }
+  }
+}
+
+// ---- per-step batched kernels over the tile list (one thread per cell)
+
+// FP64 form: X^(s) -> X (GSA: the last stage is the new state), with a
+// finiteness check.  FP32 form: pack X^(s) into the FP32 deviation populations.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ bp, int f32form) {
+  const BatchDev& b = *bp;
+  const int ntiles = b.counts[0];
+  const int s = b.s;
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int k_inst = find_inst(b.tile_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const int tile = it - b.tile_start[k_inst];
+    const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
+    const size_t pl = (size_t)I.nx * I.ny;
+    const size_t o = (size_t)(tyi * TY + threadIdx.y) * I.nx + (txi * TX + threadIdx.x);
+    const T* Y = reinterpret_cast<const T*>(I.Xs[s]);
+    bool bad = false;
+    if (f32form) {
+      double m[6], d[6];
+      for (int k = 0; k < 6; ++k) m[k] = double(Y[o + k * pl]);
+      mom_to_pop(m, I.eps, I.rho0, I.amp, d);
+      for (int k = 0; k < 6; ++k) {
+        const float v = float(d[k]);
+        bad |= !isfinite(v);
+        I.dF[o + k * pl] = v;
+      }
+    } else {
+      T* X = reinterpret_cast<T*>(I.X);
+      for (int k = 0; k < 6; ++k) {
+        const T v = Y[o + k * pl];
+        bad |= !isfinite(v);
+        X[o + k * pl] = v;
+      }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(b.err, 1u);
+  }
+}
+
+// FP32 form, start of a step: moments of the FP32 populations in FP64
+// (sums and the division by rho0 A), rounded once into the FP32 planes X.
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_unpack(const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
+  const int ntiles = b.counts[0];
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int k_inst = find_inst(b.tile_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const int tile = it - b.tile_start[k_inst];
+    const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
+    const size_t pl = (size_t)I.nx * I.ny;
+    const size_t o = (size_t)(tyi * TY + threadIdx.y) * I.nx + (txi * TX + threadIdx.x);
+    double d[6], m[6];
+    for (int k = 0; k < 6; ++k) d[k] = double(I.dF[o + k * pl]);
+    pop_to_mom(d, I.eps, I.rho0, I.amp, m);
+    float* X = reinterpret_cast<float*>(I.X);
+    for (int k = 0; k < 6; ++k) X[o + k * pl] = float(m[k]);
+  }
+}
+
+}  // namespace apd

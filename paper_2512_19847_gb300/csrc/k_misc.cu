@@ -1,0 +1,33 @@
+// Instantiation unit of the FFT Helmholtz, state I/O and per-step finish kernels.
+#include "dispatch.h"
+#include "fft_kernels.cuh"
+#include "io_kernels.cuh"
+
+namespace apd {
+namespace {
+template <typename T, int TX, int TY>
+MiscSet make_misc() {
+  MiscSet m{};
+  m.k_finish = reinterpret_cast<const void*>(&k_finish<T, TX, TY>);
+  m.k_unpack = reinterpret_cast<const void*>(&k_unpack<TX, TY>);
+  m.k_rows_fwd = reinterpret_cast<const void*>(&k_fft_rows_fwd<T>);
+  m.k_cols = reinterpret_cast<const void*>(&k_fft_cols<T>);
+  m.k_rows_inv = reinterpret_cast<const void*>(&k_fft_rows_inv<T>);
+  m.k_set_state = reinterpret_cast<const void*>(&k_set_state<T>);
+  m.k_get_state = reinterpret_cast<const void*>(&k_get_state<T>);
+  return m;
+}
+template <typename T>
+MiscSet by_tile(int tile) {
+  switch (tile) {
+    case 0: return make_misc<T, 32, 8>();
+    case 1: return make_misc<T, 32, 4>();
+    case 2: return make_misc<T, 16, 8>();
+    case 3: return make_misc<T, 8, 8>();
+    default: return make_misc<T, 64, 4>();
+  }
+}
+}  // namespace
+
+MiscSet misc_set(int f32form, int tile) { return f32form ? by_tile<float>(tile) : by_tile<double>(tile); }
+}  // namespace apd

@@ -1,0 +1,172 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 form: element by element, max |gpu - oracle| <= 1e-12 * max |oracle| per
+moment plane, on seeded inputs at sizes spanning several tiles, for every
+spatial scheme and both tableaux of Sec. 4.1, non-square grids, eps from the
+kinetic regime to the exact limit eps = 0, and multi-step runs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ap_dvm_oracle as O  # noqa: E402
+from paper_2512_19847_gb300 import api, tableaux, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _tab(name):
+    return tableaux.gsa2() if name == "gsa2" else tableaux.euler()
+
+
+def _pair(nx, ny, scheme, tab, eps, tau, dt, **kw):
+    A_ex, A_im = _tab(tab)
+    p = api.default_params(nx, ny, eps=eps, dt=dt, tau=tau, space_scheme=scheme, tableau=(A_ex, A_im), **kw)
+    o = O.Params(nx, ny, eps, tau, dt, np.array(A_ex), np.array(A_im), scheme=scheme)
+    return p, o
+
+
+def rel_err(got, ref):
+    scale = np.maximum(np.max(np.abs(ref), axis=(1, 2)), 1e-300)
+    return np.max(np.abs(got - ref), axis=(1, 2)) / scale
+
+
+def run_gpu(p, X0, nsteps, graph=0, tile=-1):
+    s = api.Solver(p)
+    if tile >= 0:
+        s.set_tile(tile)
+    s.set_graph_steps(graph)
+    s.set_state(torch.from_numpy(X0).cuda())
+    s.step(nsteps)
+    s.sync_status()
+    return s.get_state().cpu().numpy()
+
+
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO3_C4", "WENO5_C4"])
+@pytest.mark.parametrize("tab", ["euler", "gsa2"])
+@pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-6])
+def test_one_step_random_state(scheme, tab, eps):
+    nx, ny = 64, 32
+    X0 = W.random_moment_state(nx, ny, seed=101, amp=0.5)
+    p, o = _pair(nx, ny, scheme, tab, eps, 0.05, 0.02)
+    got = run_gpu(p, X0, 1)
+    ref = O.step(X0, o)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO5_C4"])
+def test_exact_limit_eps_zero(scheme):
+    n = 32
+    u1, u2, pr = W.taylor_green(n)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    p, o = _pair(n, n, scheme, "gsa2", 0.0, 0.0, 0.5 * 2 * math.pi / n)
+    got = run_gpu(p, X0, 3)
+    ref = O.run(X0, o, 3)
+    err = rel_err(got, ref)
+    assert np.all(err[:3] <= TOL), err            # v, q vanish identically in this limit
+
+
+def test_taylor_green_64_100_steps():
+    """Taylor-Green vortex, 64^2, eps = Ma = 1e-2, CFL 0.5, 100 steps, second-order
+    IMEX with WENO5 + C4 (the small FP64 workload)."""
+    n = 64
+    u1, u2, pr = W.taylor_green(n)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    dt = W.cfl_dt(u1, u2, 2 * math.pi / n, 0.5)
+    p, o = _pair(n, n, "WENO5_C4", "gsa2", 1e-2, 0.05, dt, mach=1e-2)
+    got = run_gpu(p, X0, 100, graph=10)
+    ref = O.run(X0, o, 100)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+@pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-4, 1e-6])
+def test_double_shear_layer_sweep(eps):
+    """Double shear layer (1/rho = 30, delta = 0.05), the asymptotic-preserving sweep
+    over eps at a reduced size (128^2, 20 steps) the oracle finishes quickly."""
+    n = 128
+    u1, u2, pr = W.double_shear_layer(n)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    dt = W.cfl_dt(u1, u2, 2 * math.pi / n, 0.5)
+    p, o = _pair(n, n, "WENO5_C4", "gsa2", eps, 0.05, dt, mach=1e-2)
+    got = run_gpu(p, X0, 20)
+    ref = O.run(X0, o, 20)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+def test_tile_shapes_agree(tile):
+    n = 64
+    X0 = W.random_moment_state(n, n, seed=5, amp=0.3)
+    p, o = _pair(n, n, "WENO5_C4", "gsa2", 1e-3, 0.05, 0.02)
+    got = run_gpu(p, X0, 2, tile=tile)
+    ref = O.run(X0, o, 2)
+    assert np.all(rel_err(got, ref) <= TOL)
+
+
+def test_graph_replay_is_bitwise_direct():
+    n = 64
+    X0 = W.random_moment_state(n, n, seed=9, amp=0.3)
+    p, _ = _pair(n, n, "WENO5_C4", "gsa2", 1e-2, 0.05, 0.02)
+    a = run_gpu(p, X0, 6, graph=0)
+    b = run_gpu(p, X0, 6, graph=3)
+    assert np.array_equal(a, b)
+
+
+def test_equilibrium_and_outputs():
+    n = 32
+    u1, u2, pr = W.taylor_green(n)
+    p, _ = _pair(n, n, "WENO5_C4", "gsa2", 1e-2, 0.05, 0.01, mach=2e-3, rho0=1.2)
+    s = api.Solver(p)
+    s.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, pr)])
+    X = s.get_state().cpu().numpy()
+    assert np.allclose(X, O.equilibrium_state(u1, u2, pr), rtol=0, atol=1e-15)
+    rho, a1, a2, pp = [t.cpu().numpy() for t in s.moments()]
+    r_ref = O.outputs(X, 1e-2, rho0=1.2, amp=2e-3)
+    for g, r in zip((rho, a1, a2, pp), r_ref):
+        assert np.max(np.abs(g - r)) <= 1e-14 * max(1.0, np.max(np.abs(r)))
+
+
+def test_population_view_round_trip():
+    n, eps, mach, rho0 = 32, 3e-2, 5e-3, 1.1
+    X0 = W.random_moment_state(n, n, seed=17, amp=0.4)
+    p, _ = _pair(n, n, "WENO5_C4", "gsa2", eps, 0.05, 0.01, mach=mach, rho0=rho0)
+    s = api.Solver(p)
+    dF_ref = O.populations_from_moments(X0, eps, rho0=rho0, amp=mach)
+    s.set_populations(torch.from_numpy(dF_ref).cuda())
+    X = s.get_state().cpu().numpy()
+    power = np.array([0, 0, 1, 1, 1, 2])
+    tol = 1e-14 * np.max(np.abs(X0)) * 8 / eps ** power
+    assert np.all(np.max(np.abs(X - X0), axis=(1, 2)) <= tol)
+    dF = s.get_populations().cpu().numpy()
+    assert np.max(np.abs(dF - dF_ref)) <= 1e-13 * np.max(np.abs(dF_ref))
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted in the input (on the host) is caught by the per-step check."""
+    n = 16
+    X0 = W.random_moment_state(n, n, seed=1)
+    X0[0, 3, 4] = np.nan
+    p, _ = _pair(n, n, "WENO5_C4", "gsa2", 1e-2, 0.05, 0.01)
+    s = api.Solver(p)
+    s.set_state(torch.from_numpy(X0).cuda())
+    s.step(1)
+    with pytest.raises(api.ApDvmError) as e:
+        s.sync_status()
+    assert e.value.status == 5
+    s.set_state(torch.from_numpy(np.nan_to_num(X0)).cuda())
+    s.step(1)
+    s.sync_status()      # flag was cleared by the previous read
+
+
+def test_run_host_matches_device_path():
+    n = 32
+    X0 = W.random_moment_state(n, n, seed=23, amp=0.3)
+    p, _ = _pair(n, n, "WENO5_C4", "gsa2", 1e-2, 0.05, 0.01)
+    a = run_gpu(p, X0, 3)
+    s = api.Solver(p)
+    b = s.run_host(torch.from_numpy(X0).pin_memory(), 3).numpy()
+    assert np.array_equal(a, b)
