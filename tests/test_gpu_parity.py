@@ -86,14 +86,17 @@ def test_taylor_green_64_100_steps():
 @pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-4, 1e-6])
 def test_double_shear_layer_sweep(eps):
     """Double shear layer (1/rho = 30, delta = 0.05), the asymptotic-preserving sweep
-    over eps at a reduced size (128^2, 20 steps) the oracle finishes quickly."""
+    over eps at a reduced size (128^2).  The thin layer is Kelvin-Helmholtz
+    unstable: a 1e-14 perturbation of the oracle's own input grows ~2.5x per
+    step (rate ~ U/delta = 30), so round-off differences between any two
+    implementations are compared over a short horizon, 5 steps."""
     n = 128
     u1, u2, pr = W.double_shear_layer(n)
     X0 = O.equilibrium_state(u1, u2, pr)
     dt = W.cfl_dt(u1, u2, 2 * math.pi / n, 0.5)
     p, o = _pair(n, n, "WENO5_C4", "gsa2", eps, 0.05, dt, mach=1e-2)
-    got = run_gpu(p, X0, 20)
-    ref = O.run(X0, o, 20)
+    got = run_gpu(p, X0, 5)
+    ref = O.run(X0, o, 5)
     assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
 
 
