@@ -1,0 +1,382 @@
+"""Benchmark: Mcell-updates/s per IMEX step of the AP IMEX-RK D2V6 solver.
+
+Workload (default): Taylor-Green vortex on a periodic 2048 x 2048 grid,
+eps = 1e-4, Ma = 1e-3, tau = 0.05, CFL 0.5, second-order GSA IMEX tableau
+(c = 2.25) with WENO5 + fourth-order central differences.  One "step" is one
+full IMEX step (both stages: explicit operators, closed-form relaxation,
+Helmholtz solve, u/q update) of the whole grid.  The FP64 form is the
+headline value; the FP32 deviation form is reported beside it with its
+velocity/pressure error against the FP64 result.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched with torchrun: every rank runs an independent replica on
+its own GPU (the solve does not shard; replicas only), the time is the max
+over ranks and the value counts the cells of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-updates/s per IMEX step (FP64 vs FP32-dev) at stated error; served p99"
+UNIT = "Mcell-updates/s"
+
+
+# ----------------------------------------------------------------- algorithmic counts
+# Flops per cell of each kernel kind for one IMEX step of the second-order
+# tableau (both stages), counting every +, -, *, / as one flop, derived from
+# the formulas (halo recomputation and redundant loads are not counted).
+def weno_flux_pair_flops(scheme: str) -> int:
+    """Flops per cell for one flux/partner pair along one axis: two
+    reconstructions per interface + split + sum, and the difference."""
+    if scheme == "WENO5_C4":
+        return 2 * 69 + 1 + 4 + 2
+    if scheme == "WENO3_C4":
+        return 2 * 20 + 1 + 4 + 2
+    return 4 + 2
+
+
+def step_flops_per_cell(scheme: str, n: int) -> dict:
+    FP = weno_flux_pair_flops(scheme)
+    c1 = 6 if scheme != "LF1_C2" else 2           # first central difference
+    c2 = 8 if scheme != "LF1_C2" else 4           # second central difference
+    lg = math.log2(n)
+    explicit = (2 * c1 + 1) * 2 + 2 * FP + 13 + (2 * c1 + 1)          # stage 1: E, D0.u^n
+    explicit += (2 * c1 + 1) * 2 + 2 * FP + 13 + (2 * c1 + 1) + (2 * c2 + 1) + 2 * c1 + 4 * FP + 2   # stage 2: all
+    dbf = 2 * c2 + 2 * c1 + 3
+    rhs = (14 + dbf + 5 + 1) + (22 + dbf + 11)
+    # radix-2 butterflies (10 flops) of the two real-row, column and inverse-row passes, two solves
+    rows = 2 * (2.5 * lg + 2)
+    cols = 2 * (5 * lg + 2.5)
+    update = (6 + 4 * FP + 2 + 2 * c1 + (2 * c1 + 1) + 6 + 4 + 8) + (10 + 4 * FP + 2 + 2 * c1 + (2 * c1 + 1) + 12 + 4 + 13)
+    return {"explicit": explicit, "rhs": rhs, "fft_rows_fwd": rows, "fft_cols": cols,
+            "fft_rows_inv": rows, "update": update, "finish": 0, "unpack": 0}
+
+
+def step_bytes_per_cell(f32: bool) -> dict:
+    """Algorithmic DRAM bytes per cell of each kernel kind for one step:
+    every plane a kernel must read or write, once."""
+    e = 4 if f32 else 8
+    planes = {
+        # stage 1: read u, v, q (5), write E, D0.u (3); stage 2: read 6, write E, D0.u, D_Delta theta, D0 theta, D_LF.B(v) (8)
+        "explicit": (5 + 3) + (6 + 8),
+        # stage 2: read v^n, E^(1), theta^n, D0.u^n (6), write v, DB, R (4);
+        # stage 3: read v^n, E^(1), E^(2), v^(2), theta^n, D0.u^n, D0.u^(2), DB^(2), D_Delta theta^(2) (13), write 4
+        "rhs": (6 + 4) + (13 + 4),
+        # each pass reads and writes one plane-equivalent (real plane or half spectrum), two solves
+        "fft_rows_fwd": 4, "fft_cols": 4, "fft_rows_inv": 4,
+        # stage 2: read v, u^n, theta, q^n (6), write u, q, D0.v (4); stage 3: read 14, write 4
+        "update": (6 + 4) + (14 + 4),
+        "finish": 12, "unpack": 12 if f32 else 0}
+    return {k: v * e for k, v in planes.items()}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- workload
+def workload(n: int, eps: float, mach: float, tau: float):
+    from paper_2512_19847_gb300 import workloads as W
+    u1, u2, p = W.taylor_green(n)
+    dt = W.stable_dt(u1, u2, 2 * math.pi / n, tau, cfl=0.5, visc=0.4)
+    return (u1, u2, p), dt
+
+
+def make_solver(n, eps, mach, tau, dt, f32: bool, scheme="WENO5_C4"):
+    from paper_2512_19847_gb300 import api, tableaux
+    p = api.default_params(n, n, eps=eps, dt=dt, tau=tau, mach=mach, space_scheme=scheme,
+                           tableau=tableaux.gsa2(), precision=api.FP32_DEV if f32 else api.FP64)
+    return api.Solver(p)
+
+
+def time_form(torch, fields, n, eps, mach, tau, dt, f32, steps, warmup, barrier, graph_steps=1):
+    s = make_solver(n, eps, mach, tau, dt, f32)
+    s.set_equilibrium(*[torch.from_numpy(a).cuda() for a in fields])
+    s.set_graph_steps(graph_steps)
+    s.step(warmup)
+    s.sync_status()
+    torch.cuda.synchronize()
+    barrier()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    s.sync_status()
+    return s, ms
+
+
+def profile_form(s, steps):
+    s.profile(True)
+    s.step(steps)
+    prof = s.profile_read()
+    s.profile(False)
+    return prof
+
+
+def roofline(prof: dict, steps: int, cells: int, f32: bool, scheme: str, n: int, peaks: dict):
+    flops = step_flops_per_cell(scheme, n)
+    byts = step_bytes_per_cell(f32)
+    kind, (tot_ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = tot_ms / launches
+    launches_per_step = launches / steps
+    if f32:
+        alg = byts[kind] * cells / launches_per_step            # bytes per launch
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs") or 6800.0
+        return kind, {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                      "frac": round(achieved / peak, 4), "traffic": None, "kernel": kind,
+                      "algorithmic_bytes_per_launch": alg, "ms_per_launch": round(per_launch_ms, 4),
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
+    alg = flops[kind] * cells / launches_per_step                # flops per launch
+    achieved = alg / (per_launch_ms * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS
+    return kind, {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                  "frac": round(achieved / peak, 4), "traffic": None, "kernel": kind,
+                  "algorithmic_flops_per_launch": alg, "ms_per_launch": round(per_launch_ms, 4),
+                  "peak_source": "FP64 FMA pipe, measured: 0.505e12 DFMA/s x 2 (DESIGN.md)"}
+
+
+# measured on this machine's GB300 (FMA-chain microbenchmark, 152 SMs x 8 blocks x 256 threads)
+FP64_PEAK_TFLOPS = 1.01
+
+
+def cpu_baseline(n, eps, mach, tau, dt, fields, nsteps=1):
+    """The oracle as it stands, on the host, one full-size IMEX step."""
+    import numpy as np
+    from oracle import ap_dvm_oracle as O
+    A_ex, _, A_im, _ = O.tableau_gsa2()
+    X = O.equilibrium_state(*fields)
+    p = O.Params(n, n, eps, tau, dt, A_ex, A_im, scheme="WENO5_C4")
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        X = O.step(X, p)
+    el = time.perf_counter() - t0
+    return {"value": round(n * n * nsteps / el / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} IMEX step(s) of the {n}x{n} workload, numpy float64, 1 thread ({el:.1f} s)"}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = args.ref_n
+    fields, dt = workload(n, args.eps, args.mach, args.tau)
+    import numpy as np
+    from oracle import ap_dvm_oracle as O
+    A_ex, _, A_im, _ = O.tableau_gsa2()
+    p = O.Params(n, n, args.eps, args.tau, dt, A_ex, A_im, scheme="WENO5_C4")
+    X = O.equilibrium_state(*fields)
+    for _ in range(args.warmup):
+        X = O.step(X, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        X = O.step(X, p)
+    el = time.perf_counter() - t0
+    v = n * n * args.steps / el / 1e6
+    sample = (f"one IMEX step of the same scheme on a {n}x{n} Taylor-Green grid per step "
+              f"(the oracle's Mcell/s is size-independent within ~15% from 256^2 to 1024^2)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args),
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    return {"workload": f"taylor_green_{args.n}x{args.n}_eps{args.eps:g}_Ma{args.mach:g}",
+            "grid": [args.n, args.n], "eps": args.eps, "mach": args.mach, "tau": args.tau,
+            "dt_rule": "min(0.5 dx/max|u|, 0.4 dx^2/(tau/4))",
+            "tableau": "GSA2 c=2.25", "space": "WENO5+C4", "l2": "inputs larger than L2 (FP64 state 201 MB, step working set ~1.7 GB)"}
+
+
+# ----------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--mach", type=float, default=1e-3)
+    ap.add_argument("--tau", type=float, default=0.05)
+    ap.add_argument("--ref-n", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, cells = args.n, args.n * args.n
+    fields, dt = workload(n, args.eps, args.mach, args.tau)
+    peaks = load_peaks()
+
+    with ClockSampler(local) as clk:
+        s64, ms64 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, False, args.steps, args.warmup, barrier)
+    clocks = clk.summary()
+    s32, ms32 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, True, args.steps, args.warmup, barrier)
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms64 = max_over_ranks(ms64)
+    ms32 = max_over_ranks(ms32)
+    v64 = world * cells * args.steps / (ms64 * 1e-3) / 1e6
+    v32 = world * cells * args.steps / (ms32 * 1e-3) / 1e6
+
+    # accuracy of the FP32 deviation form against the FP64 result after the same steps
+    X64 = s64.get_state().cpu().numpy()
+    X32 = s32.get_state().cpu().numpy()
+    ref_p = X64[2] - 0.5 * (X64[0] ** 2 + X64[1] ** 2)
+    p32 = X32[2] - 0.5 * (X32[0] ** 2 + X32[1] ** 2)
+    umax = float(np.max(np.hypot(X64[0], X64[1])))
+    vel_err = float(np.max(np.hypot(X32[0] - X64[0], X32[1] - X64[1])) / umax)
+    pr_err = float(np.max(np.abs((p32 - p32.mean()) - (ref_p - ref_p.mean()))) / float(np.max(np.abs(ref_p - ref_p.mean()))))
+
+    # per-kernel CUDA-event profile on the launching stream, dominant kernel roofline
+    prof64 = profile_form(s64, args.profile_steps)
+    prof32 = profile_form(s32, args.profile_steps)
+    k64, roof64 = roofline(prof64, args.profile_steps, cells, False, "WENO5_C4", n, peaks)
+    k32, roof32 = roofline(prof32, args.profile_steps, cells, True, "WENO5_C4", n, peaks)
+    launches64 = s64.launches_per_step * args.steps
+
+    # end to end through the public API with host buffers: per step, H2D of the
+    # state from pinned memory, the step, and D2H of the resulting state
+    Xh = torch.from_numpy(X64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    s64.run_host(Xh, 1)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Xh = s64.run_host(Xh, 1)
+    el = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": round(world * cells * e2e_steps / el / 1e6, 3), "unit": UNIT,
+           "h2d_bytes_per_step": 6 * cells * 8, "d2h_bytes_per_step": 6 * cells * 8}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(n, args.eps, args.mach, args.tau, dt, fields)
+    line = {
+        "metric": METRIC, "value": round(v64, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms64 / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args),
+        "roofline": roof64,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches64,
+        "clocks": clocks,
+        "fp32_dev": {"value": round(v32, 3), "unit": UNIT, "ms_per_step": round(ms32 / args.steps, 4),
+                     "dtype": "f32 transport, f64 moment sums and relaxation (eps<=1e-4)",
+                     "velocity_rel_err_vs_fp64": vel_err, "pressure_rel_err_vs_fp64": pr_err,
+                     "roofline": roof32, "gpu_launches": s32.launches_per_step * args.steps},
+        "kernels_fp64_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in prof64.items()},
+        "kernels_fp32_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in prof32.items()},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,15 @@ int ap_dvm_get_tile(const ap_dvm_handle* h);
 /* Kernel launches enqueued by one ap_dvm_step(h, 1). */
 int ap_dvm_launches_per_step(const ap_dvm_handle* h);
 
+/* Per-kernel timing.  While enabled, ap_dvm_step launches directly (no graph)
+ * and brackets every kernel with CUDA events on the handle's stream; enabling
+ * or disabling resets the totals. */
+ap_dvm_status ap_dvm_profile_enable(ap_dvm_handle* h, int enable);
+/* Synchronise and read per-kernel totals since the last reset: up to max
+ * entries of kernel name (static string), total milliseconds and launch
+ * count.  Returns the number of kernel kinds (8), or -1 on error. */
+int ap_dvm_profile_read(ap_dvm_handle* h, const char** names, double* total_ms, long* launches, int max);
+
 /* End-to-end call on HOST buffers: copy 6 moment planes h_in (double) to the
  * device, set the state of slot, run nsteps, and copy the moment state back
  * into h_out (6 double planes); synchronous.  Pinned host memory gives

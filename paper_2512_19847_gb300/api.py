@@ -101,6 +101,9 @@ def lib():
         "ap_dvm_launches_per_step": (i32, [H]),
         "ap_dvm_run_host": (i32, [H, i32, vp, vp, vp, i32]),
         "ap_dvm_sync_status": (i32, [H]),
+        "ap_dvm_profile_enable": (i32, [H, i32]),
+        "ap_dvm_profile_read": (i32, [H, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(f64),
+                                      ctypes.POINTER(ctypes.c_long), i32]),
         "ap_dvm_last_error": (ctypes.c_char_p, [H]),
         "ap_dvm_destroy": (None, [H]),
         "ap_dvm_default_params": (None, [P, i32, i32, f64, f64]),
@@ -218,6 +221,20 @@ class _Handle:
 
     def sync_status(self):
         self._check(lib().ap_dvm_sync_status(self._h))
+
+    def profile(self, enable: bool):
+        """Per-kernel CUDA-event timing of the following ap_dvm_step calls."""
+        self._check(lib().ap_dvm_profile_enable(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        """{kernel: (total_ms, launches)} since profiling was enabled."""
+        names = (ctypes.c_char_p * 8)()
+        ms = (ctypes.c_double * 8)()
+        cnt = (ctypes.c_long * 8)()
+        n = lib().ap_dvm_profile_read(self._h, names, ms, cnt, 8)
+        if n < 0:
+            self._check(4)
+        return {names[k].decode(): (ms[k], cnt[k]) for k in range(n) if cnt[k] > 0}
 
 
 class Solver(_Handle):

@@ -72,6 +72,13 @@ struct ap_dvm_handle {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;
   bool graph_valid = false;
+  // per-kernel CUDA-event profile (direct launches only)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  int ev_used = 0;
+  double prof_ms[8] = {0};
+  long prof_count[8] = {0};
   char err[512] = "";
 };
 
@@ -302,8 +309,43 @@ ap_dvm_status flush(ap_dvm_handle* h) {
   return AP_DVM_OK;
 }
 
-ap_dvm_status launch(ap_dvm_handle* h, cudaStream_t stream, const void* fn, int grid, dim3 block, size_t smem, void** args) {
+const char* const kKernelNames[8] = {"explicit", "rhs", "fft_rows_fwd", "fft_cols", "fft_rows_inv", "update", "finish", "unpack"};
+enum { KK_EXPLICIT, KK_RHS, KK_ROWS_FWD, KK_COLS, KK_ROWS_INV, KK_UPDATE, KK_FINISH, KK_UNPACK };
+
+ap_dvm_status launch(ap_dvm_handle* h, cudaStream_t stream, const void* fn, int grid, dim3 block, size_t smem, void** args,
+                     int kind = -1) {
+  const bool prof = h->profile && kind >= 0;
+  if (prof) {
+    if (h->ev_used + 2 > (int)h->ev.size()) {
+      for (int k = 0; k < 256; ++k) {
+        cudaEvent_t e;
+        CUDA_TRY(h, cudaEventCreate(&e));
+        h->ev.push_back(e);
+        h->ev_kind.push_back(-1);
+      }
+    }
+    h->ev_kind[h->ev_used] = kind;
+    CUDA_TRY(h, cudaEventRecord(h->ev[h->ev_used], stream));
+  }
   CUDA_TRY(h, cudaLaunchKernel(fn, dim3(grid), block, args, smem, stream));
+  if (prof) {
+    CUDA_TRY(h, cudaEventRecord(h->ev[h->ev_used + 1], stream));
+    h->ev_used += 2;
+  }
+  return AP_DVM_OK;
+}
+
+// Accumulate the elapsed times of the recorded event pairs (synchronises).
+ap_dvm_status profile_collect(ap_dvm_handle* h) {
+  if (h->ev_used == 0) return AP_DVM_OK;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k + 1 < h->ev_used; k += 2) {
+    float ms = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+    h->prof_ms[h->ev_kind[k]] += ms;
+    h->prof_count[h->ev_kind[k]] += 1;
+  }
+  h->ev_used = 0;
   return AP_DVM_OK;
 }
 
@@ -320,7 +362,7 @@ ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream) {
   auto AIM = [&](int i, int j) { return t.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
   if (f32) {
     void* a[] = {&bp};
-    if ((st = launch(h, stream, h->km.k_unpack, h->grid_finish, blk, 0, a))) return st;
+    if ((st = launch(h, stream, h->km.k_unpack, h->grid_finish, blk, 0, a, KK_UNPACK))) return st;
   }
   for (int i = 2; i <= s; ++i) {
     int j = i - 1;
@@ -332,28 +374,28 @@ ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream) {
     if (j == 1) need |= 2u;                                    // D0 . u^n enters every right-hand side
     if (need) {
       void* a[] = {&bp, &j, &need, &weno_eps};
-      if ((st = launch(h, stream, h->ks.k_explicit, h->grid_explicit, blk, h->ks.smem_explicit, a))) return st;
+      if ((st = launch(h, stream, h->ks.k_explicit, h->grid_explicit, blk, h->ks.smem_explicit, a, KK_EXPLICIT))) return st;
     }
     double sign = -1.0;                                        // reading G4
     int first = (i == 2) ? 1 : 0;
     {
       void* a[] = {&bp, &i, &sign, &first};
-      if ((st = launch(h, stream, h->ks.k_rhs, h->grid_rhs, blk, h->ks.smem_rhs, a))) return st;
+      if ((st = launch(h, stream, h->ks.k_rhs, h->grid_rhs, blk, h->ks.smem_rhs, a, KK_RHS))) return st;
     }
     {
       void* a[] = {&bp};
-      if ((st = launch(h, stream, h->km.k_rows_fwd, h->grid_fft, dim3(256), fft_smem(h), a))) return st;
+      if ((st = launch(h, stream, h->km.k_rows_fwd, h->grid_fft, dim3(256), fft_smem(h), a, KK_ROWS_FWD))) return st;
       void* b[] = {&bp, &i};
-      if ((st = launch(h, stream, h->km.k_cols, h->grid_fft, dim3(256), fft_smem(h), b))) return st;
-      if ((st = launch(h, stream, h->km.k_rows_inv, h->grid_fft, dim3(256), fft_smem(h), b))) return st;
+      if ((st = launch(h, stream, h->km.k_cols, h->grid_fft, dim3(256), fft_smem(h), b, KK_COLS))) return st;
+      if ((st = launch(h, stream, h->km.k_rows_inv, h->grid_fft, dim3(256), fft_smem(h), b, KK_ROWS_INV))) return st;
     }
     {
       void* a[] = {&bp, &i, &weno_eps};
-      if ((st = launch(h, stream, h->ks.k_update, h->grid_update, blk, h->ks.smem_update, a))) return st;
+      if ((st = launch(h, stream, h->ks.k_update, h->grid_update, blk, h->ks.smem_update, a, KK_UPDATE))) return st;
     }
   }
   void* a[] = {&bp, &f32};
-  return launch(h, stream, h->km.k_finish, h->grid_finish, blk, 0, a);
+  return launch(h, stream, h->km.k_finish, h->grid_finish, blk, 0, a, KK_FINISH);
 }
 
 ap_dvm_status build_graph(ap_dvm_handle* h) {
@@ -620,16 +662,38 @@ ap_dvm_status ap_dvm_step(ap_dvm_handle* h, int nsteps) {
   if (st) return st;
   if (h->n_active == 0 || nsteps == 0) return AP_DVM_OK;
   int done = 0;
-  if (h->graph_steps > 0) {
+  if (h->graph_steps > 0 && !h->profile) {
     if (!h->graph_valid && (st = build_graph(h))) return st;
     while (nsteps - done >= h->graph_steps) {
       CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
       done += h->graph_steps;
     }
   }
-  for (; done < nsteps; ++done)
+  for (; done < nsteps; ++done) {
     if ((st = enqueue_step(h, h->stream))) return st;
+    if (h->profile && h->ev_used > 2048 && (st = profile_collect(h))) return st;
+  }
   return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_profile_enable(ap_dvm_handle* h, int enable) {
+  if (!h) return AP_DVM_ERR_ARG;
+  ap_dvm_status st = profile_collect(h);
+  if (st) return st;
+  h->profile = enable != 0;
+  for (int k = 0; k < 8; ++k) { h->prof_ms[k] = 0; h->prof_count[k] = 0; }
+  return AP_DVM_OK;
+}
+
+int ap_dvm_profile_read(ap_dvm_handle* h, const char** names, double* total_ms, long* launches, int max) {
+  if (!h || profile_collect(h) != AP_DVM_OK) return -1;
+  const int n = std::min(max, 8);
+  for (int k = 0; k < n; ++k) {
+    if (names) names[k] = kKernelNames[k];
+    if (total_ms) total_ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->prof_count[k];
+  }
+  return 8;
 }
 
 ap_dvm_status ap_dvm_set_graph_steps(ap_dvm_handle* h, int k) {
@@ -699,6 +763,7 @@ const char* ap_dvm_last_error(const ap_dvm_handle* h) { return h ? h->err : "nul
 
 void ap_dvm_destroy(ap_dvm_handle* h) {
   if (!h) return;
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;

@@ -432,3 +432,21 @@ def test_temporal_order(tab, order):
     assert abs(orders(scheme="LF1_C2", alpha=0.0, operators="consistent") - order) < 0.1
     if tab == "gsa2":
         assert orders(scheme="LF1_C2", alpha=0.0) < 1.3
+
+
+def test_viscous_time_step_bound():
+    """In the limit the viscous term is explicit (Sec. 3.1), so dt needs
+    nu dt/dx^2 below ~0.5: 0.4 (the workload rule) is stable, 0.7 is not."""
+    n, tau = 32, 2.0
+    u1, u2, pr = W.taylor_green(n)
+    X0 = O.equilibrium_state(u1, u2, pr) + 1e-8 * np.random.default_rng(0).standard_normal((6, n, n))
+    h = 2 * math.pi / n
+    out = {}
+    for r in (0.4, 0.7):
+        p = _params(n, "WENO5_C4", eps=1e-4, tau=tau, dt=r * h * h / (tau / 4))
+        Y = X0.copy()
+        for _ in range(150):
+            Y = O.step(Y, p)
+        out[r] = float(np.max(np.abs(Y[:2]))) if np.isfinite(Y).all() else float("inf")
+    assert out[0.4] < 1.0 and out[0.7] > 10.0, out
+    assert W.stable_dt(u1, u2, h, tau) == pytest.approx(0.4 * h * h / (tau / 4))
