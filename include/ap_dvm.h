@@ -177,6 +177,30 @@ int ap_dvm_profile_read(ap_dvm_handle* h, const char** names, double* total_ms, 
 ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage,
                               int nsteps);
 
+/* Advance one small FP64 solve by nsteps IMEX steps without allocating or
+ * being given any device memory beyond its state.  The paper has no
+ * counterpart: this is a deployment variant of ap_dvm_create + ap_dvm_step
+ * for callers that cannot call cudaMalloc or hand over a workspace, e.g.
+ * code running under a host framework that owns every device allocation,
+ * real-time loops that forbid allocation after start-up, or plugins loaded
+ * into a process whose allocator they may not touch.
+ *  p          parameters (FP64 form only; nx, ny <= 128 and the whole
+ *             scratch of the solve <= 8 MiB: up to 3 stages at 128 x 128).
+ *  d_state6   device moment state, 6 double planes (u1, u2, theta, v1, v2, q):
+ *             read at the start, overwritten with the state after nsteps.
+ *  cuda_stream  stream for the copies and kernels.
+ * Returns AP_DVM_ERR_ARG for invalid parameters or a grid beyond the limit
+ * above, AP_DVM_ERR_UNSUPPORTED for the FP32 form, AP_DVM_ERR_CUDA if a CUDA
+ * call fails.  The scratch is one 8 MiB file-scope device array that every
+ * GPU which loads this library holds until the process exits.  The first
+ * call on a device looks up that array's address (set-up), so make it before
+ * any stream capture.  Each call synchronises the stream once after staging
+ * its small descriptors, then enqueues the steps asynchronously.  All calls
+ * share the one array and it keeps the last call's contents: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and give
+ * wrong results; serialise them. */
+ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_state6, int nsteps, void* cuda_stream);
+
 /* Synchronise the stream and return AP_DVM_ERR_NONFINITE if any step since the
  * last call produced a non-finite value (the flag is then cleared). */
 ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h);

@@ -1,0 +1,247 @@
+// ap_dvm_step_noalloc: IMEX steps of one small FP64 solve with all scratch
+// in a file-scope device array, for callers that cannot allocate device
+// memory (see include/ap_dvm.h).  It reuses the library's kernels unchanged;
+// only the carving of the scratch and the launch sequence live here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "../../include/ap_dvm.h"
+#include "common.cuh"
+#include "dispatch.h"
+
+using namespace apd;
+
+namespace {
+
+constexpr int kMaxCells = 128 * 128;                 // largest grid accepted (nx * ny)
+constexpr size_t kScratchBytes = size_t(8) << 20;   // 8 MiB
+constexpr int kMaxDevices = 64;
+
+// The scratch every call uses.  In host code its name is only a stand-in;
+// the device address comes from cudaGetSymbolAddress at set-up.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+size_t up(size_t x) { return (x + 255) / 256 * 256; }
+
+// Layout of the scratch: batch tables, then the instance's planes.
+struct Layout {
+  size_t batch, inst, tile_start, row_start, col_start, counts, tw, err, ws;
+  size_t total;
+};
+
+size_t instance_bytes(const ap_dvm_params& p, char* base, InstDev* I) {
+  const size_t plane = (size_t)p.nx * p.ny * sizeof(double);
+  size_t off = 0;
+  auto take = [&](size_t b) -> void* { off = up(off); void* r = base ? base + off : nullptr; off += b; return r; };
+  I->X = take(6 * plane);
+  for (int j = 2; j <= p.s; ++j) I->Xs[j] = take(6 * plane);
+  for (int j = 1; j <= p.s; ++j) {
+    I->E[j] = take(2 * plane);
+    I->Du[j] = take(plane);
+    I->Lth[j] = take(plane);
+    I->Gth[j] = take(2 * plane);
+    I->DLFB[j] = take(2 * plane);
+    I->Dv[j] = take(plane);
+    I->DB[j] = take(plane);
+  }
+  I->R = take(plane);
+  I->sstride = p.nx / 2 + 1;
+  I->S = take((size_t)p.ny * I->sstride * 2 * sizeof(double));
+  I->lamx = reinterpret_cast<double*>(take((size_t)(p.nx / 2 + 1) * sizeof(double)));
+  I->lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
+  I->th_part = reinterpret_cast<double*>(take((size_t)p.nx * p.ny / 32 * sizeof(double)));
+  I->dF = nullptr;
+  return up(off);
+}
+
+Layout layout(const ap_dvm_params& p, int nmax) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t b) { off = up(off); size_t r = off; off += b; return r; };
+  L.batch = take(sizeof(BatchDev));
+  L.inst = take(sizeof(InstDev));
+  L.tile_start = take(2 * sizeof(int));
+  L.row_start = take(2 * sizeof(int));
+  L.col_start = take(2 * sizeof(int));
+  L.counts = take(4 * sizeof(int));
+  L.tw = take(sizeof(double2) * (nmax / 2));
+  L.err = take(4 * sizeof(unsigned));
+  InstDev dummy{};
+  L.ws = take(instance_bytes(p, nullptr, &dummy));
+  L.total = up(off);
+  return L;
+}
+
+void symbol(int n, double h, int scheme, double* out, int count) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < count; ++k) {
+    const long double phi = 2.0L * pi * (long double)k / (long double)n;
+    const long double s = std::sin(0.5L * phi);
+    const long double s2 = s * s;
+    const long double v = scheme == AP_DVM_LF1_C2 ? -4.0L * s2 / ((long double)h * h)
+                                                  : 2.0L * s2 * (std::cos(phi) - 7.0L) / (3.0L * (long double)h * h);
+    out[k] = (double)v;
+  }
+}
+
+int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+cudaError_t grid_of(const void* fn, int threads, size_t smem, int sms, int* grid) {
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  *grid = std::max(1, per) * sms;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+#define NA_TRY(call)                                   \
+  do {                                                 \
+    if ((call) != cudaSuccess) return AP_DVM_ERR_CUDA; \
+  } while (0)
+
+extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_state6, int nsteps, void* cuda_stream) {
+  if (!p || !d_state6 || nsteps < 0) return AP_DVM_ERR_ARG;
+  if (ap_dvm_instance_workspace_size(p) == 0) return AP_DVM_ERR_ARG;           // invalid parameters or tableau
+  if (p->precision != AP_DVM_FP64) return AP_DVM_ERR_UNSUPPORTED;
+  if (p->nx > 128 || p->ny > 128 || (long)p->nx * p->ny > kMaxCells) return AP_DVM_ERR_ARG;  // beyond the static scratch
+  const int nmax = std::max(p->nx, p->ny);
+  const Layout L = layout(*p, nmax);
+  if (L.total > kScratchBytes) return AP_DVM_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+
+  // set-up, once per device, with that device current
+  int dev = 0;
+  NA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return AP_DVM_ERR_UNSUPPORTED;
+  if (!g_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    NA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_scratch_ptr[dev] = ptr;
+  }
+  char* base = reinterpret_cast<char*>(g_scratch_ptr[dev]);
+  int sms = 0;
+  NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+  // kernels: the tile rule of the handle path (largest of 32x8, 32x4, 16x8, 8x8 that fits)
+  int tile = 3;
+  for (int t : {0, 1, 2, 3})
+    if (kTileX[t] <= p->nx && kTileY[t] <= p->ny) { tile = t; break; }
+  StencilSet ks = p->space_scheme == AP_DVM_LF1_C2 ? stencil_f64_lf1(tile)
+                : p->space_scheme == AP_DVM_WENO3_C4 ? stencil_f64_w3(tile) : stencil_f64_w5(tile);
+  MiscSet km = misc_set(0, tile);
+  const int eblk = std::max(2048, nmax);
+  const size_t fft_smem = (size_t)eblk * 2 * sizeof(double);
+  const int thr = ks.tx * ks.ty;
+  int g_exp = 0, g_rhs = 0, g_upd = 0, g_fin = 0, g1 = 0, g2 = 0, g3 = 0;
+  NA_TRY(grid_of(ks.k_explicit, thr, ks.smem_explicit, sms, &g_exp));
+  NA_TRY(grid_of(ks.k_rhs, thr, ks.smem_rhs, sms, &g_rhs));
+  NA_TRY(grid_of(ks.k_update, thr, ks.smem_update, sms, &g_upd));
+  NA_TRY(grid_of(km.k_finish, thr, 0, sms, &g_fin));
+  NA_TRY(grid_of(km.k_rows_fwd, 256, fft_smem, sms, &g1));
+  NA_TRY(grid_of(km.k_cols, 256, fft_smem, sms, &g2));
+  NA_TRY(grid_of(km.k_rows_inv, 256, fft_smem, sms, &g3));
+  const int g_fft = std::min(g1, std::min(g2, g3));
+
+  // descriptors, built on the host stack and copied into the scratch
+  InstDev I{};
+  instance_bytes(*p, base + L.ws, &I);
+  I.nx = p->nx; I.ny = p->ny; I.lnx = ilog2(p->nx); I.lny = ilog2(p->ny);
+  I.tiles_x = p->nx / ks.tx; I.tiles_y = p->ny / ks.ty;
+  I.row_pairs = std::max(1, std::min(eblk / p->nx, p->ny / 2));
+  I.col_group = std::max(1, eblk / p->ny);
+  I.relax64 = 0;
+  I.dx = p->Lx / p->nx; I.dy = p->Ly / p->ny;
+  I.dt = p->dt; I.eps = p->eps;
+  I.tau = p->tau < 0 ? 4.0 * p->eps / p->mach : p->tau;
+  I.te2 = I.tau * p->eps * p->eps;
+  I.rho0 = p->rho0; I.amp = p->mach;
+  for (int i = 2; i <= p->s; ++i) {
+    const double a = p->A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+    I.kappa[i] = 2.0 * p->eps * p->eps / (p->dt * p->dt * a * a);
+    I.den[i] = I.te2 + p->dt * a;
+  }
+  BatchDev B{};
+  B.inst = reinterpret_cast<InstDev*>(base + L.inst);
+  B.tile_start = reinterpret_cast<int*>(base + L.tile_start);
+  B.row_start = reinterpret_cast<int*>(base + L.row_start);
+  B.col_start = reinterpret_cast<int*>(base + L.col_start);
+  B.counts = reinterpret_cast<int*>(base + L.counts);
+  B.tw = reinterpret_cast<double2*>(base + L.tw);
+  B.lnmax = ilog2(nmax);
+  B.s = p->s;
+  for (int k = 0; k < APD_MAXS * APD_MAXS; ++k) { B.A_ex[k] = p->A_ex[k]; B.A_im[k] = p->A_im[k]; }
+  B.err = reinterpret_cast<unsigned*>(base + L.err);
+  const int ntiles = I.tiles_x * I.tiles_y;
+  const int nrows = (p->ny / 2 + I.row_pairs - 1) / I.row_pairs;
+  const int ncols = (p->nx / 2 + 1 + I.col_group - 1) / I.col_group;
+  const int ts[2] = {0, ntiles}, rs[2] = {0, nrows}, cs[2] = {0, ncols}, counts[4] = {ntiles, nrows, ncols, 1};
+  double2 tw[64];                                   // nmax/2 <= 64 for grids of at most 128 cells a side
+  double lx[65], ly[128];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < nmax / 2; ++k) {
+    const long double a = -2.0L * pi * (long double)k / (long double)nmax;
+    tw[k].x = (double)std::cos(a);
+    tw[k].y = (double)std::sin(a);
+  }
+  symbol(p->nx, I.dx, p->space_scheme, lx, p->nx / 2 + 1);
+  symbol(p->ny, I.dy, p->space_scheme, ly, p->ny);
+  NA_TRY(cudaMemcpyAsync(base + L.batch, &B, sizeof(B), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(base + L.inst, &I, sizeof(I), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(B.tile_start, ts, sizeof(ts), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(B.row_start, rs, sizeof(rs), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(B.col_start, cs, sizeof(cs), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(B.counts, counts, sizeof(counts), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(B.tw, tw, sizeof(double2) * (nmax / 2), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(I.lamx, lx, sizeof(double) * (p->nx / 2 + 1), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(I.lamy, ly, sizeof(double) * p->ny, cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemsetAsync(B.err, 0, 4 * sizeof(unsigned), stream));
+  NA_TRY(cudaMemcpyAsync(I.X, d_state6, 6 * sizeof(double) * p->nx * p->ny, cudaMemcpyDeviceToDevice, stream));
+  NA_TRY(cudaStreamSynchronize(stream));            // the host-stack sources above go out of scope
+
+  // the steps: the launch sequence of one IMEX step (Algorithm 1, CK/ARS tableau)
+  BatchDev* bp = reinterpret_cast<BatchDev*>(base + L.batch);
+  double weno_eps = p->weno_eps;
+  int f32 = 0;
+  const dim3 blk(ks.tx, ks.ty);
+  auto AEX = [&](int i, int j) { return p->A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
+  auto AIM = [&](int i, int j) { return p->A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
+  for (int step = 0; step < nsteps; ++step) {
+    for (int i = 2; i <= p->s; ++i) {
+      int j = i - 1;
+      unsigned need = (j == 1) ? 2u : 0u;
+      for (int k = j + 1; k <= p->s; ++k) {
+        if (AEX(k, j) != 0.0) need |= 1u;
+        if (AIM(k, j) != 0.0) need |= 2u | 4u | 8u | 16u;
+      }
+      if (need) {
+        void* a[] = {&bp, &j, &need, &weno_eps};
+        NA_TRY(cudaLaunchKernel(ks.k_explicit, dim3(g_exp), blk, a, ks.smem_explicit, stream));
+      }
+      double sign = -1.0;
+      int first = (i == 2) ? 1 : 0;
+      void* r[] = {&bp, &i, &sign, &first};
+      NA_TRY(cudaLaunchKernel(ks.k_rhs, dim3(g_rhs), blk, r, ks.smem_rhs, stream));
+      void* f0[] = {&bp};
+      void* f1[] = {&bp, &i};
+      NA_TRY(cudaLaunchKernel(km.k_rows_fwd, dim3(g_fft), dim3(256), f0, fft_smem, stream));
+      NA_TRY(cudaLaunchKernel(km.k_cols, dim3(g_fft), dim3(256), f1, fft_smem, stream));
+      NA_TRY(cudaLaunchKernel(km.k_rows_inv, dim3(g_fft), dim3(256), f1, fft_smem, stream));
+      void* u[] = {&bp, &i, &weno_eps};
+      NA_TRY(cudaLaunchKernel(ks.k_update, dim3(g_upd), blk, u, ks.smem_update, stream));
+    }
+    void* fa[] = {&bp, &f32};
+    NA_TRY(cudaLaunchKernel(km.k_finish, dim3(g_fin), blk, fa, 0, stream));
+  }
+  NA_TRY(cudaMemcpyAsync(d_state6, I.X, 6 * sizeof(double) * p->nx * p->ny, cudaMemcpyDeviceToDevice, stream));
+  return AP_DVM_OK;
+}
