@@ -24,6 +24,7 @@
 #include "../../include/ap_dvm.h"
 #include "common.cuh"
 #include "dispatch.h"
+#include "step_plan.h"
 
 using namespace apd;
 
@@ -103,8 +104,6 @@ ap_dvm_status fail(ap_dvm_handle* h, ap_dvm_status st, const char* fmt, ...) {
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-double tau_of(const ap_dvm_params& p) { return p.tau < 0 ? 4.0 * p.eps / p.mach : p.tau; }
 
 // Validates one solve's parameters; writes a message into buf.
 ap_dvm_status validate(const ap_dvm_params* p, char* buf, size_t n) {
@@ -310,7 +309,6 @@ ap_dvm_status flush(ap_dvm_handle* h) {
 }
 
 const char* const kKernelNames[8] = {"explicit", "rhs", "fft_rows_fwd", "fft_cols", "fft_rows_inv", "update", "finish", "unpack"};
-enum { KK_EXPLICIT, KK_RHS, KK_ROWS_FWD, KK_COLS, KK_ROWS_INV, KK_UPDATE, KK_FINISH, KK_UNPACK };
 
 ap_dvm_status launch(ap_dvm_handle* h, cudaStream_t stream, const void* fn, int grid, dim3 block, size_t smem, void** args,
                      int kind = -1) {
@@ -351,51 +349,11 @@ ap_dvm_status profile_collect(ap_dvm_handle* h) {
 
 // Kernels of one IMEX step for all attached solves (see the file header).
 ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream) {
-  const ap_dvm_params& t = h->tmpl;
-  const int s = t.s;
-  BatchDev* bp = h->d_batch;
-  const dim3 blk(h->ks.tx, h->ks.ty);
-  double weno_eps = t.weno_eps;
-  int f32 = h->f32;
-  ap_dvm_status st;
-  auto AEX = [&](int i, int j) { return t.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
-  auto AIM = [&](int i, int j) { return t.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
-  if (f32) {
-    void* a[] = {&bp};
-    if ((st = launch(h, stream, h->km.k_unpack, h->grid_finish, blk, 0, a, KK_UNPACK))) return st;
-  }
-  for (int i = 2; i <= s; ++i) {
-    int j = i - 1;
-    unsigned need = 0;
-    for (int k = j + 1; k <= s; ++k) {
-      if (AEX(k, j) != 0.0) need |= 1u;                        // E^(j)
-      if (AIM(k, j) != 0.0) need |= 2u | 4u | 8u | 16u;        // D0.u, D_Delta theta, D0 theta, D_LF.B(v) of stage j
-    }
-    if (j == 1) need |= 2u;                                    // D0 . u^n enters every right-hand side
-    if (need) {
-      void* a[] = {&bp, &j, &need, &weno_eps};
-      if ((st = launch(h, stream, h->ks.k_explicit, h->grid_explicit, blk, h->ks.smem_explicit, a, KK_EXPLICIT))) return st;
-    }
-    double sign = -1.0;                                        // reading G4
-    int first = (i == 2) ? 1 : 0;
-    {
-      void* a[] = {&bp, &i, &sign, &first};
-      if ((st = launch(h, stream, h->ks.k_rhs, h->grid_rhs, blk, h->ks.smem_rhs, a, KK_RHS))) return st;
-    }
-    {
-      void* a[] = {&bp};
-      if ((st = launch(h, stream, h->km.k_rows_fwd, h->grid_fft, dim3(256), fft_smem(h), a, KK_ROWS_FWD))) return st;
-      void* b[] = {&bp, &i};
-      if ((st = launch(h, stream, h->km.k_cols, h->grid_fft, dim3(256), fft_smem(h), b, KK_COLS))) return st;
-      if ((st = launch(h, stream, h->km.k_rows_inv, h->grid_fft, dim3(256), fft_smem(h), b, KK_ROWS_INV))) return st;
-    }
-    {
-      void* a[] = {&bp, &i, &weno_eps};
-      if ((st = launch(h, stream, h->ks.k_update, h->grid_update, blk, h->ks.smem_update, a, KK_UPDATE))) return st;
-    }
-  }
-  void* a[] = {&bp, &f32};
-  return launch(h, stream, h->km.k_finish, h->grid_finish, blk, 0, a, KK_FINISH);
+  StepKernels K{h->ks, h->km, h->grid_explicit, h->grid_rhs, h->grid_update, h->grid_finish, h->grid_fft, fft_smem(h)};
+  auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int kind) -> int {
+    return (int)launch(h, stream, fn, grid, block, smem, args, kind);
+  };
+  return (ap_dvm_status)enqueue_imex_step(h->tmpl, K, h->d_batch, h->f32, ln);
 }
 
 ap_dvm_status build_graph(ap_dvm_handle* h) {
@@ -553,16 +511,8 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   InstDev& d = s.dev;
   carve_instance(*p, s.ws, &d);
   d.nx = p->nx; d.ny = p->ny; d.lnx = ilog2(p->nx); d.lny = ilog2(p->ny);
-  d.dx = p->Lx / p->nx; d.dy = p->Ly / p->ny;
-  d.dt = p->dt; d.eps = p->eps; d.tau = tau_of(*p);
-  d.te2 = d.tau * p->eps * p->eps;
-  d.rho0 = p->rho0; d.amp = p->mach;
+  fill_constants(*p, d);
   d.relax64 = (p->precision == AP_DVM_FP32_DEV && p->eps <= 1e-4) ? 1 : 0;
-  for (int i = 2; i <= p->s; ++i) {
-    const double a = p->A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
-    d.kappa[i] = 2.0 * p->eps * p->eps / (p->dt * p->dt * a * a);
-    d.den[i] = d.te2 + p->dt * a;
-  }
   std::vector<double> lx(p->nx / 2 + 1), ly(p->ny);
   laplacian_symbol(p->nx, d.dx, p->space_scheme, lx.data(), (int)lx.size());
   laplacian_symbol(p->ny, d.dy, p->space_scheme, ly.data(), (int)ly.size());
@@ -720,15 +670,7 @@ int ap_dvm_get_tile(const ap_dvm_handle* h) { return h ? h->tile : -1; }
 int ap_dvm_launches_per_step(const ap_dvm_handle* h) {
   if (!h) return 0;
   const ap_dvm_params& t = h->tmpl;
-  int n = h->f32 ? 1 : 0;
-  for (int i = 2; i <= t.s; ++i) {
-    const int j = i - 1;
-    bool need = (j == 1);
-    for (int k = j + 1; k <= t.s; ++k)
-      need |= t.A_ex[(k - 1) * AP_DVM_MAX_STAGES + (j - 1)] != 0.0 || t.A_im[(k - 1) * AP_DVM_MAX_STAGES + (j - 1)] != 0.0;
-    n += (need ? 1 : 0) + 5;
-  }
-  return n + 1;
+  return (h->f32 ? 1 : 0) + 6 * (t.s - 1) + 1;
 }
 
 ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage, int nsteps) {

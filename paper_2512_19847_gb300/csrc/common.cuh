@@ -36,6 +36,15 @@ struct InstDev {
   double dx, dy, dt, eps, tau, te2, rho0, amp;
   double kappa[APD_MAXS + 1];   // kappa_i = 2 eps^2/(dt^2 a_ii^2), by stage i (1-based)
   double den[APD_MAXS + 1];     // tau eps^2 + dt a_ii
+  double inv_den[APD_MAXS + 1]; // 1 / (tau eps^2 + dt a_ii)
+  double sc_u, sc_th, sc_v, sc_q;  // population view: 1/(rho0 A), 1/(2 eps rho0 A), 1/(eps rho0 A), 1/(eps^2 rho0 A)
+  double inv_dx, inv_dy;
+  // coefficients of the Helmholtz right-hand side of stage i (Algorithm 1, step 2), by [i][j]:
+  double c_du[APD_MAXS + 1][APD_MAXS + 1];   // a_ij / (dt a_ii^2), j < i
+  double c_dun[APD_MAXS + 1];                // 1 / (dt a_ii)
+  double c_db[APD_MAXS + 1][APD_MAXS + 1];   // a_ij / a_ii, j <= i
+  double c_lth[APD_MAXS + 1][APD_MAXS + 1];  // -a_ij / a_ii, j < i (reading G4)
+  double inv_aii[APD_MAXS + 1];              // 1 / a_ii
   void* X;                      // 6 planes: state at t^n (moments)
   void* Xs[APD_MAXS + 1];       // stage values X^(j), j = 2..s (6 planes); Xs[s] = next state
   void* E[APD_MAXS + 1];        // explicit term of step 1 for stage j (2 planes)

@@ -5,9 +5,9 @@
 namespace apd {
 
 // Tile shapes of the stencil kernels (index = ap_dvm_set_tile argument).
-constexpr int kNumTiles = 5;
-constexpr int kTileX[kNumTiles] = {32, 32, 16, 8, 64};
-constexpr int kTileY[kNumTiles] = {8, 4, 8, 8, 4};
+constexpr int kNumTiles = 6;
+constexpr int kTileX[kNumTiles] = {32, 32, 16, 8, 64, 32};
+constexpr int kTileY[kNumTiles] = {8, 4, 8, 8, 4, 16};
 
 struct StencilSet {
   const void* k_explicit;

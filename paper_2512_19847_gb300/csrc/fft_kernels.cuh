@@ -150,9 +150,12 @@ __global__ void __launch_bounds__(256) k_fft_cols(const BatchDev* __restrict__ b
       C v = x[e];
       if (kx == 0 && ky == 0) {
         v.x = T(s_mean); v.y = T(0);
-      } else {
+      } else if (sizeof(T) == 8) {
         const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
         v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
+      } else {
+        const T f = T(scale) / T(I.lamx[kx] + I.lamy[ky] - kap);
+        v.x *= f; v.y *= f;
       }
       x[e] = v;
     }

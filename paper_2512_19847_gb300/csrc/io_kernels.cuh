@@ -15,8 +15,9 @@ namespace apd {
 
 constexpr double SQ3 = 1.7320508075688772935;
 
-// dF (six values) -> moments (u1, u2, theta, v1, v2, q)
-__device__ __forceinline__ void pop_to_mom(const double* dF, double eps, double rho0, double amp, double* m) {
+// dF (six values) -> moments (u1, u2, theta, v1, v2, q); the scalings
+// 1/(rho0 A), 1/(2 eps rho0 A), 1/(eps rho0 A), 1/(eps^2 rho0 A) come precomputed.
+__device__ __forceinline__ void pop_to_mom(const double* dF, const InstDev& I, double* m) {
   const double s1 = dF[0] + dF[3], s2 = dF[1] + dF[4], s3 = dF[2] + dF[5];
   const double d1 = dF[0] - dF[3], d2 = dF[1] - dF[4], d3 = dF[2] - dF[5];
   const double M0 = s1 + s2 + s3;
@@ -25,26 +26,29 @@ __device__ __forceinline__ void pop_to_mom(const double* dF, double eps, double 
   const double M3 = 0.5 * s1 - 0.25 * (s2 + s3);
   const double M4 = 0.25 * SQ3 * (s2 - s3);
   const double M5 = 0.25 * (d2 - d1 - d3);
-  const double inv = 1.0 / (rho0 * amp);
-  m[0] = M1 * inv;
-  m[1] = M2 * inv;
-  m[2] = M0 * inv / (2.0 * eps);
-  m[3] = -M3 * inv / eps;
-  m[4] = M4 * inv / eps;
-  m[5] = M5 * inv / (eps * eps);
+  m[0] = M1 * I.sc_u;
+  m[1] = M2 * I.sc_u;
+  m[2] = M0 * I.sc_th;
+  m[3] = -M3 * I.sc_v;
+  m[4] = M4 * I.sc_v;
+  m[5] = M5 * I.sc_q;
 }
 
-// moments -> dF
-__device__ __forceinline__ void mom_to_pop(const double* m, double eps, double rho0, double amp, double* dF) {
-  const double M0 = 2.0 * eps * m[2], M1 = m[0], M2 = m[1];
-  const double M3 = -eps * m[3], M4 = eps * m[4], M5 = eps * eps * m[5];
-  const double S1 = M0 / 6.0 + (2.0 / 3.0) * M3;
-  const double S2 = M0 / 6.0 - M3 / 3.0 + (SQ3 / 3.0) * M4;
-  const double S3 = M0 / 6.0 - M3 / 3.0 - (SQ3 / 3.0) * M4;
-  const double D1 = M1 / 3.0 - (2.0 / 3.0) * M5;
-  const double D2 = M1 / 6.0 + (SQ3 / 6.0) * M2 + (2.0 / 3.0) * M5;
-  const double D3 = -M1 / 6.0 + (SQ3 / 6.0) * M2 - (2.0 / 3.0) * M5;
-  const double a = rho0 * amp;
+// moments -> dF, in the arithmetic type R (FP64 in the FP64 form and for
+// state input; FP32 when the FP32 form repacks its FP32 stage values, whose
+// result is stored in FP32 anyway)
+template <typename R>
+__device__ __forceinline__ void mom_to_pop(const R* m, R eps, R rho0, R amp, R* dF) {
+  const R M0 = R(2) * eps * m[2], M1 = m[0], M2 = m[1];
+  const R M3 = -eps * m[3], M4 = eps * m[4], M5 = eps * eps * m[5];
+  const R r6 = R(1.0 / 6.0), r3 = R(1.0 / 3.0), t3 = R(2.0 / 3.0);
+  const R S1 = M0 * r6 + t3 * M3;
+  const R S2 = M0 * r6 - M3 * r3 + R(SQ3 / 3.0) * M4;
+  const R S3 = M0 * r6 - M3 * r3 - R(SQ3 / 3.0) * M4;
+  const R D1 = M1 * r3 - t3 * M5;
+  const R D2 = M1 * r6 + R(SQ3 / 6.0) * M2 + t3 * M5;
+  const R D3 = -M1 * r6 + R(SQ3 / 6.0) * M2 - t3 * M5;
+  const R a = rho0 * amp;
   dF[0] = a * (S1 + D1); dF[3] = a * (S1 - D1);
   dF[1] = a * (S2 + D2); dF[4] = a * (S2 - D2);
   dF[2] = a * (S3 + D3); dF[5] = a * (S3 - D3);
@@ -76,14 +80,14 @@ __global__ void k_set_state(InstDev I, const double* __restrict__ a, const doubl
         for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = float(d[k]);
         continue;
       }
-      pop_to_mom(d, I.eps, I.rho0, I.amp, m);
+      pop_to_mom(d, I, m);
     } else {
       for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = f32[o + k * pl];
       continue;
     }
     if (f32form) {
       double d[6];
-      mom_to_pop(m, I.eps, I.rho0, I.amp, d);
+      mom_to_pop<double>(m, I.eps, I.rho0, I.amp, d);
       for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = float(d[k]);
     } else {
       T* X = reinterpret_cast<T*>(I.X);
@@ -104,7 +108,7 @@ __global__ void k_get_state(InstDev I, double* __restrict__ out, double* __restr
       for (int k = 0; k < 6; ++k) d[k] = double(I.dF[o + k * pl]);
       if (what == 3) { for (int k = 0; k < 6; ++k) out32[o + k * pl] = I.dF[o + k * pl]; continue; }
       if (what == 2) { for (int k = 0; k < 6; ++k) out[o + k * pl] = d[k]; continue; }
-      pop_to_mom(d, I.eps, I.rho0, I.amp, m);
+      pop_to_mom(d, I, m);
     } else {
       const T* X = reinterpret_cast<const T*>(I.X);
       for (int k = 0; k < 6; ++k) m[k] = double(X[o + k * pl]);
@@ -117,7 +121,7 @@ __global__ void k_get_state(InstDev I, double* __restrict__ out, double* __restr
       o2[o] = m[1];
       o3[o] = m[2] - 0.5 * (m[0] * m[0] + m[1] * m[1]);
     } else {
-      mom_to_pop(m, I.eps, I.rho0, I.amp, d);
+      mom_to_pop<double>(m, I.eps, I.rho0, I.amp, d);
       if (what == 2) for (int k = 0; k < 6; ++k) out[o + k * pl] = d[k];
       else for (int k = 0; k < 6; ++k) out32[o + k * pl] = float(d[k]);
     }
@@ -143,11 +147,11 @@ __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ 
     const T* Y = reinterpret_cast<const T*>(I.Xs[s]);
     bool bad = false;
     if (f32form) {
-      double m[6], d[6];
-      for (int k = 0; k < 6; ++k) m[k] = double(Y[o + k * pl]);
-      mom_to_pop(m, I.eps, I.rho0, I.amp, d);
+      float m[6], d[6];
+      for (int k = 0; k < 6; ++k) m[k] = float(Y[o + k * pl]);
+      mom_to_pop<float>(m, float(I.eps), float(I.rho0), float(I.amp), d);
       for (int k = 0; k < 6; ++k) {
-        const float v = float(d[k]);
+        const float v = d[k];
         bad |= !isfinite(v);
         I.dF[o + k * pl] = v;
       }
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(TX* TY) k_unpack(const BatchDev* __restrict__ 
     const size_t o = (size_t)(tyi * TY + threadIdx.y) * I.nx + (txi * TX + threadIdx.x);
     double d[6], m[6];
     for (int k = 0; k < 6; ++k) d[k] = double(I.dF[o + k * pl]);
-    pop_to_mom(d, I.eps, I.rho0, I.amp, m);
+    pop_to_mom(d, I, m);
     float* X = reinterpret_cast<float*>(I.X);
     for (int k = 0; k < 6; ++k) X[o + k * pl] = float(m[k]);
   }

@@ -24,7 +24,8 @@ MiscSet by_tile(int tile) {
     case 1: return make_misc<T, 32, 4>();
     case 2: return make_misc<T, 16, 8>();
     case 3: return make_misc<T, 8, 8>();
-    default: return make_misc<T, 64, 4>();
+    case 4: return make_misc<T, 64, 4>();
+    default: return make_misc<T, 32, 16>();
   }
 }
 }  // namespace

@@ -11,6 +11,7 @@
 #include "../../include/ap_dvm.h"
 #include "common.cuh"
 #include "dispatch.h"
+#include "step_plan.h"
 
 using namespace apd;
 
@@ -160,16 +161,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   I.row_pairs = std::max(1, std::min(eblk / p->nx, p->ny / 2));
   I.col_group = std::max(1, eblk / p->ny);
   I.relax64 = 0;
-  I.dx = p->Lx / p->nx; I.dy = p->Ly / p->ny;
-  I.dt = p->dt; I.eps = p->eps;
-  I.tau = p->tau < 0 ? 4.0 * p->eps / p->mach : p->tau;
-  I.te2 = I.tau * p->eps * p->eps;
-  I.rho0 = p->rho0; I.amp = p->mach;
-  for (int i = 2; i <= p->s; ++i) {
-    const double a = p->A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
-    I.kappa[i] = 2.0 * p->eps * p->eps / (p->dt * p->dt * a * a);
-    I.den[i] = I.te2 + p->dt * a;
-  }
+  fill_constants(*p, I);
   BatchDev B{};
   B.inst = reinterpret_cast<InstDev*>(base + L.inst);
   B.tile_start = reinterpret_cast<int*>(base + L.tile_start);
@@ -208,39 +200,15 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   NA_TRY(cudaMemcpyAsync(I.X, d_state6, 6 * sizeof(double) * p->nx * p->ny, cudaMemcpyDeviceToDevice, stream));
   NA_TRY(cudaStreamSynchronize(stream));            // the host-stack sources above go out of scope
 
-  // the steps: the launch sequence of one IMEX step (Algorithm 1, CK/ARS tableau)
+  // the steps: the launch sequence of one IMEX step shared with the handle path
   BatchDev* bp = reinterpret_cast<BatchDev*>(base + L.batch);
-  double weno_eps = p->weno_eps;
-  int f32 = 0;
-  const dim3 blk(ks.tx, ks.ty);
-  auto AEX = [&](int i, int j) { return p->A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
-  auto AIM = [&](int i, int j) { return p->A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
+  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, fft_smem};
+  auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int) -> int {
+    return cudaLaunchKernel(fn, dim3(grid), block, args, smem, stream) == cudaSuccess ? 0 : (int)AP_DVM_ERR_CUDA;
+  };
   for (int step = 0; step < nsteps; ++step) {
-    for (int i = 2; i <= p->s; ++i) {
-      int j = i - 1;
-      unsigned need = (j == 1) ? 2u : 0u;
-      for (int k = j + 1; k <= p->s; ++k) {
-        if (AEX(k, j) != 0.0) need |= 1u;
-        if (AIM(k, j) != 0.0) need |= 2u | 4u | 8u | 16u;
-      }
-      if (need) {
-        void* a[] = {&bp, &j, &need, &weno_eps};
-        NA_TRY(cudaLaunchKernel(ks.k_explicit, dim3(g_exp), blk, a, ks.smem_explicit, stream));
-      }
-      double sign = -1.0;
-      int first = (i == 2) ? 1 : 0;
-      void* r[] = {&bp, &i, &sign, &first};
-      NA_TRY(cudaLaunchKernel(ks.k_rhs, dim3(g_rhs), blk, r, ks.smem_rhs, stream));
-      void* f0[] = {&bp};
-      void* f1[] = {&bp, &i};
-      NA_TRY(cudaLaunchKernel(km.k_rows_fwd, dim3(g_fft), dim3(256), f0, fft_smem, stream));
-      NA_TRY(cudaLaunchKernel(km.k_cols, dim3(g_fft), dim3(256), f1, fft_smem, stream));
-      NA_TRY(cudaLaunchKernel(km.k_rows_inv, dim3(g_fft), dim3(256), f1, fft_smem, stream));
-      void* u[] = {&bp, &i, &weno_eps};
-      NA_TRY(cudaLaunchKernel(ks.k_update, dim3(g_upd), blk, u, ks.smem_update, stream));
-    }
-    void* fa[] = {&bp, &f32};
-    NA_TRY(cudaLaunchKernel(km.k_finish, dim3(g_fin), blk, fa, 0, stream));
+    const int st = enqueue_imex_step(*p, K, bp, 0, ln);
+    if (st) return (ap_dvm_status)st;
   }
   NA_TRY(cudaMemcpyAsync(d_state6, I.X, 6 * sizeof(double) * p->nx * p->ny, cudaMemcpyDeviceToDevice, stream));
   return AP_DVM_OK;
