@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -222,6 +224,75 @@ def cpu_baseline(n, eps, mach, tau, dt, fields, nsteps=1):
             "sample": f"{nsteps} IMEX step(s) of the {n}x{n} workload, numpy float64, 1 thread ({el:.1f} s)"}
 
 
+def run_batched(torch, count=256, steps=200, seed=2512):
+    """Batched form: `count` seeded uneven instances (side uniform in
+    {64,128,256,512}, eps log-uniform [1e-6,1], Ma log-uniform [1e-3,1e-1],
+    random divergence-free fields, tau = 0.05), FP32 deviation storage, tile
+    chosen by the autotuner, all `steps` steps replayed as one CUDA graph."""
+    from paper_2512_19847_gb300 import api, autotune, tableaux, workloads as W
+    draws = W.batched_draws(count, seed=seed, steps=steps)
+    tmpl = api.default_params(512, 512, eps=1e-2, dt=1e-3, tau=0.05, tableau=tableaux.gsa2(), precision=api.FP32_DEV)
+    b = api.Batch(tmpl, capacity=count)
+    cells = 0
+    for k, d in enumerate(draws):
+        u1, u2, p = W.random_divfree(d.n, d.seed)
+        prm = tmpl.copy()
+        prm.nx = prm.ny = d.n
+        prm.eps, prm.mach = d.eps, d.mach
+        prm.dt = W.stable_dt(u1, u2, 2 * math.pi / d.n, prm.tau)
+        b.attach(k, prm)
+        b.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, p)], slot=k)
+        cells += d.n * d.n
+    tuned = autotune.tune(b, steps=2, path=None)
+    b.set_graph_steps(steps)
+    b.step(steps)                          # warm-up (also builds the graph)
+    b.sync_status()
+    torch.cuda.synchronize()
+    for k, d in enumerate(draws):          # restart from the initial data
+        u1, u2, p = W.random_divfree(d.n, d.seed)
+        b.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, p)], slot=k)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.step(steps)                          # one graph launch
+    e1.record(st)
+    e1.synchronize()
+    b.sync_status()
+    ms = e0.elapsed_time(e1)
+    return {"value": round(cells * steps / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "instances": count,
+            "cells": cells, "steps": steps, "ms": round(ms, 2), "graph_launches": 1,
+            "kernel_launches": b.launches_per_step * steps, "tile": tuned["tile"],
+            "tile_ms_per_step": tuned["ms_per_step"], "dtype": "f32 deviation storage"}
+
+
+def run_served(torch, n_requests=48, budget=120e9, load=0.8, v_ref=None, seed=7):
+    """Served form: open-loop Poisson stream (side uniform {128,256,512,1024},
+    eps log-uniform [1e-6,1e-1], 50-500 steps, tau = 0.05), admitted by an HBM
+    budget into one continuous batch (FP32 deviation form), against the same
+    stream served one solve at a time with the plain per-solve path."""
+    from paper_2512_19847_gb300 import api, serve, tableaux, workloads as W
+    sides, steps_rng = (128, 256, 512, 1024), (50, 500)
+    mean_work = np.mean([n * n for n in sides]) * np.mean(steps_rng)
+    rate = load * (v_ref or 1000.0) * 1e6 / mean_work
+    reqs = W.poisson_requests(n_requests, rate_hz=rate, seed=seed, sides=sides, steps_range=steps_rng)
+    tmpl = api.default_params(1024, 1024, eps=1e-2, dt=1e-3, tau=0.05, mach=1e-2, tableau=tableaux.gsa2(),
+                              precision=api.FP32_DEV)
+    cache = {}
+
+    def fields(n, s):
+        if (n, s) not in cache:
+            u1, u2, p = W.random_divfree(n, s)
+            cache[(n, s)] = (u1, u2, p, W.stable_dt(u1, u2, 2 * math.pi / n, 0.05))
+        return cache[(n, s)]
+    jobs = serve.make_jobs(reqs, tmpl, fields)
+    srv = serve.Server(tmpl, capacity=n_requests, hbm_budget=budget, chunk=10, tile=0)
+    mixed = srv.run(jobs).summary()
+    alone_jobs = serve.make_jobs(reqs, tmpl, fields)
+    alone = serve.run_alone(alone_jobs, tile=0).summary()
+    mixed.update({"rate_hz": round(rate, 3), "hbm_budget_gb": budget / 1e9, "chunk_steps": 10, "tile": 0})
+    return {"continuous_batching": mixed, "alone_per_solve": alone}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -279,6 +350,8 @@ def main():
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -351,6 +424,8 @@ def main():
     e2e = {"value": round(world * cells * e2e_steps / el / 1e6, 3), "unit": UNIT,
            "h2d_bytes_per_step": 6 * cells * 8, "d2h_bytes_per_step": 6 * cells * 8}
 
+    batched = None if args.no_batched else run_batched(torch)
+    served = None if args.no_served else run_served(torch, v_ref=(batched or {}).get("value", v32))
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -370,6 +445,8 @@ def main():
                      "dtype": "f32 transport, f64 moment sums and relaxation (eps<=1e-4)",
                      "velocity_rel_err_vs_fp64": vel_err, "pressure_rel_err_vs_fp64": pr_err,
                      "roofline": roof32, "gpu_launches": s32.launches_per_step * args.steps},
+        "batched": batched,
+        "served": served,
         "kernels_fp64_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in prof64.items()},
         "kernels_fp32_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in prof32.items()},
     }
