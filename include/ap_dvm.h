@@ -44,7 +44,7 @@ typedef enum {
   AP_DVM_ERR_WORKSPACE = 3,    /* workspace too small or misaligned */
   AP_DVM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   AP_DVM_ERR_NONFINITE = 5,    /* a step produced a non-finite value (latched on the device) */
-  AP_DVM_ERR_TIMEOUT = 6,      /* reserved: bounded device waits that expired */
+  AP_DVM_ERR_TIMEOUT = 6,      /* a bounded device wait (tile copy) expired; the kernel returned early */
   AP_DVM_ERR_UNSUPPORTED = 7   /* valid but not implemented configuration */
 } ap_dvm_status;
 
@@ -201,8 +201,10 @@ ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, do
  * wrong results; serialise them. */
 ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_state6, int nsteps, void* cuda_stream);
 
-/* Synchronise the stream and return AP_DVM_ERR_NONFINITE if any step since the
- * last call produced a non-finite value (the flag is then cleared). */
+/* Synchronise the stream and return AP_DVM_ERR_TIMEOUT if a kernel gave up a
+ * bounded wait for one of its tile copies (2 s), else AP_DVM_ERR_NONFINITE if
+ * any step since the last call produced a non-finite value; the flags are
+ * then cleared. */
 ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h);
 /* Message of the last error on this handle (never NULL). */
 const char* ap_dvm_last_error(const ap_dvm_handle* h);

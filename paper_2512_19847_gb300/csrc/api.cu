@@ -34,6 +34,7 @@ struct Slot {
   char* ws = nullptr;
   size_t bytes = 0;
   InstDev dev{};
+  CUtensorMap maps[APD_MAXS + 1];   // host copies of the stage-buffer tensor maps
 };
 
 struct ap_dvm_handle {
@@ -67,6 +68,7 @@ struct ap_dvm_handle {
   StencilSet ks{};
   MiscSet km{};
   int grid_explicit = 0, grid_rhs = 0, grid_update = 0, grid_fft = 0, grid_finish = 0;
+  size_t smem_update = 0;
   bool kernels_ready = false;
   // graph
   int graph_steps = 0;
@@ -179,6 +181,7 @@ size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
   I.lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
   I.th_part = reinterpret_cast<double*>(take(cells / 32 * sizeof(double)));
   I.dF = p.precision == AP_DVM_FP32_DEV ? reinterpret_cast<float*>(take(6 * cells * sizeof(float))) : nullptr;
+  I.tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1));
   return align_up(off, 256);
 }
 
@@ -252,7 +255,8 @@ ap_dvm_status prepare_kernels(ap_dvm_handle* h) {
   ap_dvm_status st;
   if ((st = occupancy_grid(h, h->ks.k_explicit, thr, h->ks.smem_explicit, &h->grid_explicit))) return st;
   if ((st = occupancy_grid(h, h->ks.k_rhs, thr, h->ks.smem_rhs, &h->grid_rhs))) return st;
-  if ((st = occupancy_grid(h, h->ks.k_update, thr, h->ks.smem_update, &h->grid_update))) return st;
+  h->smem_update = update_smem(h->ks, h->tmpl);
+  if ((st = occupancy_grid(h, h->ks.k_update, thr, h->smem_update, &h->grid_update))) return st;
   if ((st = occupancy_grid(h, h->km.k_finish, thr, 0, &h->grid_finish))) return st;
   int g1 = 0, g2 = 0, g3 = 0;
   if ((st = occupancy_grid(h, h->km.k_rows_fwd, 256, fft_smem(h), &g1))) return st;
@@ -284,6 +288,11 @@ ap_dvm_status flush(ap_dvm_handle* h) {
     InstDev d = s.dev;
     d.tiles_x = s.p.nx / TX;
     d.tiles_y = s.p.ny / TY;
+    // tensor maps of the stage buffers for the current tile shape (TMA staging)
+    d.tma = encode_stage_maps(s.p, d, h->ks.bw, h->ks.bh, s.maps);
+    if (d.tma)
+      CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.tmap), &s.maps[0], sizeof(CUtensorMap) * (APD_MAXS + 1),
+                                  cudaMemcpyHostToDevice, h->stream));
     d.row_pairs = std::max(1, std::min(h->eblk / s.p.nx, s.p.ny / 2));
     d.col_group = std::max(1, h->eblk / s.p.ny);
     h->up_inst.push_back(d);
@@ -349,7 +358,8 @@ ap_dvm_status profile_collect(ap_dvm_handle* h) {
 
 // Kernels of one IMEX step for all attached solves (see the file header).
 ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream) {
-  StepKernels K{h->ks, h->km, h->grid_explicit, h->grid_rhs, h->grid_update, h->grid_finish, h->grid_fft, fft_smem(h)};
+  StepKernels K{h->ks, h->km, h->grid_explicit, h->grid_rhs, h->grid_update, h->grid_finish, h->grid_fft, fft_smem(h),
+                h->smem_update};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int kind) -> int {
     return (int)launch(h, stream, fn, grid, block, smem, args, kind);
   };
@@ -694,10 +704,9 @@ ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h) {
   CUDA_TRY(h, cudaGetLastError());
   unsigned flags = 0;
   CUDA_TRY(h, cudaMemcpy(&flags, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  if (flags & 1u) {
-    CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
-    return fail(h, AP_DVM_ERR_NONFINITE, "a step produced a non-finite value");
-  }
+  if (flags) CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
+  if (flags & 2u) return fail(h, AP_DVM_ERR_TIMEOUT, "a bounded wait for a tile copy expired (results invalid)");
+  if (flags & 1u) return fail(h, AP_DVM_ERR_NONFINITE, "a step produced a non-finite value");
   return AP_DVM_OK;
 }
 

@@ -60,6 +60,9 @@ struct InstDev {
   double* lamy;                 // 1D Laplacian symbol in y, ky = 0..ny-1
   double* th_part;              // per-tile partial sums of theta^n
   float* dF;                    // FP32 form: deviation populations (6 planes)
+  const void* tmap;             // tensor maps (128 B each) of the stage buffers, [j] = X (j = 1) or Xs[j]
+  int tma;                      // 1: tile loads through the tensor maps; 0: plain loads
+  int pad1;
 };
 
 // Work decomposition of the active instances: item ranges per instance are
@@ -75,7 +78,7 @@ struct BatchDev {
   int s;                 // stages
   double A_ex[APD_MAXS * APD_MAXS];
   double A_im[APD_MAXS * APD_MAXS];
-  unsigned* err;         // device error flags (bit 0: non-finite state)
+  unsigned* err;         // device error flags (bit 0: non-finite state, bit 1: a bounded wait expired)
 };
 
 // Instance owning work item `item`: the last k with start[k] <= item.

@@ -13,8 +13,10 @@ struct StencilSet {
   const void* k_explicit;
   const void* k_rhs;
   const void* k_update;
-  size_t smem_explicit, smem_rhs, smem_update;
+  size_t smem_explicit, smem_rhs;
+  size_t plane_bytes, update_fixed;   // k_update: update_fixed + 2 * (planes staged) * plane_bytes
   int tx, ty;
+  int bw, bh;                          // staged box: (tx + 8) x (ty + 2 * halo)
 };
 
 struct MiscSet {

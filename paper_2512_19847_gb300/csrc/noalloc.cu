@@ -57,6 +57,7 @@ size_t instance_bytes(const ap_dvm_params& p, char* base, InstDev* I) {
   I->lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
   I->th_part = reinterpret_cast<double*>(take((size_t)p.nx * p.ny / 32 * sizeof(double)));
   I->dF = nullptr;
+  I->tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1));
   return up(off);
 }
 
@@ -146,7 +147,8 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   int g_exp = 0, g_rhs = 0, g_upd = 0, g_fin = 0, g1 = 0, g2 = 0, g3 = 0;
   NA_TRY(grid_of(ks.k_explicit, thr, ks.smem_explicit, sms, &g_exp));
   NA_TRY(grid_of(ks.k_rhs, thr, ks.smem_rhs, sms, &g_rhs));
-  NA_TRY(grid_of(ks.k_update, thr, ks.smem_update, sms, &g_upd));
+  const size_t smem_upd = update_smem(ks, *p);
+  NA_TRY(grid_of(ks.k_update, thr, smem_upd, sms, &g_upd));
   NA_TRY(grid_of(km.k_finish, thr, 0, sms, &g_fin));
   NA_TRY(grid_of(km.k_rows_fwd, 256, fft_smem, sms, &g1));
   NA_TRY(grid_of(km.k_cols, 256, fft_smem, sms, &g2));
@@ -162,6 +164,8 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   I.col_group = std::max(1, eblk / p->ny);
   I.relax64 = 0;
   fill_constants(*p, I);
+  CUtensorMap maps[APD_MAXS + 1];
+  I.tma = encode_stage_maps(*p, I, ks.bw, ks.bh, maps);
   BatchDev B{};
   B.inst = reinterpret_cast<InstDev*>(base + L.inst);
   B.tile_start = reinterpret_cast<int*>(base + L.tile_start);
@@ -197,12 +201,14 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   NA_TRY(cudaMemcpyAsync(I.lamx, lx, sizeof(double) * (p->nx / 2 + 1), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(I.lamy, ly, sizeof(double) * p->ny, cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemsetAsync(B.err, 0, 4 * sizeof(unsigned), stream));
+  if (I.tma)
+    NA_TRY(cudaMemcpyAsync(const_cast<void*>(I.tmap), maps, sizeof(maps), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(I.X, d_state6, 6 * sizeof(double) * p->nx * p->ny, cudaMemcpyDeviceToDevice, stream));
   NA_TRY(cudaStreamSynchronize(stream));            // the host-stack sources above go out of scope
 
   // the steps: the launch sequence of one IMEX step shared with the handle path
   BatchDev* bp = reinterpret_cast<BatchDev*>(base + L.batch);
-  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, fft_smem};
+  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, fft_smem, smem_upd};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int) -> int {
     return cudaLaunchKernel(fn, dim3(grid), block, args, smem, stream) == cudaSuccess ? 0 : (int)AP_DVM_ERR_CUDA;
   };

@@ -8,26 +8,155 @@
 //   k_rhs(i):  the right-hand side R_i of the Helmholtz equation (step 2).
 //   k_update(i): step 3 (u^(i)) and step 4 (closed-form q^(i)).
 //
-// Upwind fluxes are computed per tile in shared memory, one axis at a time:
-// for every flux/partner pair the Lax-Friedrichs splitting g+- = (g +- U)/2
-// and the curvature part of the WENO5 smoothness indicators are evaluated
-// once per point, then each interface flux once, then differenced.  Every
-// kernel is a persistent loop over the batch's tile list.
+// Every kernel is a persistent loop over the batch's tile list.  The halo'd
+// plane tiles a kernel reads are staged into shared memory by TMA (one bulk
+// tensor copy per plane, completing on an mbarrier), double-buffered so that
+// the copies of the next tile run while the current one is computed.
+// Upwind fluxes are then computed one axis at a time: for every flux/partner
+// pair the Lax-Friedrichs splitting g+- = (g +- U)/2 and the curvature part
+// of the WENO5 smoothness indicators are evaluated once per point, then each
+// interface flux once, then differenced.
 #pragma once
 #include <type_traits>
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace apd {
 
 enum NeedBits { NEED_E = 1, NEED_DU = 2, NEED_LTH = 4, NEED_GTH = 8, NEED_DLFB = 16, NEED_V = 32 };
 
-template <typename T>
-__device__ __forceinline__ void load_region(T* s, int W, int HH, const T* __restrict__ g, int x0, int y0, int h,
-                                            int mx, int my, int nx, int tid, int nthr) {
-  for (int k = tid; k < W * HH; k += nthr) {
-    const int ly = k / W, lx = k - ly * W;
-    const int gx = (x0 - h + lx) & mx, gy = (y0 - h + ly) & my;
-    s[k] = g[(size_t)gy * nx + gx];
+// Geometry of a staged plane tile: rows y0-H .. y0+TY+H-1, columns
+// x0-4 .. x0+TX+3 (row stride BW); logical tile column 0 (x = x0-H) sits at
+// shared-memory column XO.
+template <typename T, int SCHEME, int TX, int TY>
+struct Geo {
+  static constexpr int H = halo_of(SCHEME), CH = central_halo(SCHEME);
+  static constexpr int W = TX + 2 * H, HH = TY + 2 * H;
+  static constexpr int BW = TX + 8, BH = HH;
+  static constexpr int XO = 4 - H;
+  static constexpr int PL = ((BW * BH * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
+  static constexpr unsigned PLANE_BYTES = (unsigned)(BW * BH * sizeof(T));
+  static constexpr int C00 = H * BW + 4;                // interior cell (0, 0)
+  static constexpr int NX = TY * (TX + 1), NY = (TY + 1) * TX;
+  static constexpr int LS = (TY * W > HH * TX) ? TY * W : HH * TX;
+  static constexpr int SPLIT_PER_PAIR = SCHEME == LF1_C2 ? 0 : 4 * LS;
+  // shared memory besides the double-buffered planes, and its element count
+  static constexpr int EXPLICIT_EXTRA = 3 * SPLIT_PER_PAIR + 3 * NX + 3 * NY;
+  static constexpr int UPDATE_EXTRA = 2 * PL + 2 * SPLIT_PER_PAIR + 2 * NX + 2 * NY;
+  static constexpr int RHS_EXTRA = TY * (TX + 2 * CH) + 64;     // d_y v2 rows, block-sum scratch
+};
+
+// The planes a kernel stages, packed 6 bits each (buffer << 3 | plane) so the
+// list stays in registers.  Buffer 1: X (the state at t^n); buffer j >= 2: X^(j).
+struct PlaneList {
+  uint64_t bits = 0;
+  int n = 0;
+  __device__ __forceinline__ void add(int buf, int plane) { bits |= uint64_t((buf << 3) | plane) << (6 * n); ++n; }
+  __device__ __forceinline__ int buf(int k) const { return int(bits >> (6 * k + 3)) & 7; }
+  __device__ __forceinline__ int plane(int k) const { return int(bits >> (6 * k)) & 7; }
+};
+
+__device__ __forceinline__ const void* stage_buffer(const InstDev& I, int buf) { return buf == 1 ? I.X : I.Xs[buf]; }
+__device__ __forceinline__ const void* stage_map(const InstDev& I, int buf) {
+  return reinterpret_cast<const char*>(I.tmap) + 128 * buf;
+}
+
+struct TileRef { int inst, tile, x0, y0; };
+
+template <int TX, int TY>
+__device__ __forceinline__ TileRef decode_tile(const BatchDev& b, int it) {
+  TileRef t;
+  t.inst = find_inst(b.tile_start, b.counts[3], it);
+  const InstDev& I = b.inst[t.inst];
+  t.tile = it - b.tile_start[t.inst];
+  const int tyi = t.tile / I.tiles_x;
+  t.x0 = (t.tile - tyi * I.tiles_x) * TX;
+  t.y0 = tyi * TY;
+  return t;
+}
+
+// Plain loads of the staged box with periodic wrap; with outside_only, only
+// the cells outside the grid (which a TMA copy fills with zero) are written.
+template <typename T, class G>
+__device__ __forceinline__ void stage_plain(const InstDev& I, const PlaneList& pr, T* dst, int x0, int y0,
+                                            bool outside_only, int tid, int nthr) {
+  const int nx = I.nx, ny = I.ny, mx = nx - 1, my = ny - 1;
+  const size_t pl = (size_t)nx * ny;
+  for (int k = 0; k < pr.n; ++k) {
+    const T* g = reinterpret_cast<const T*>(stage_buffer(I, pr.buf(k))) + (size_t)pr.plane(k) * pl;
+    for (int e = tid; e < G::BW * G::BH; e += nthr) {
+      const int r = e / G::BW, c = e - r * G::BW;
+      const int gx = x0 - 4 + c, gy = y0 - G::H + r;
+      if (outside_only && gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
+      dst[k * G::PL + e] = g[(size_t)(gy & my) * nx + (gx & mx)];
+    }
+  }
+}
+
+template <class G>
+__device__ __forceinline__ bool tile_on_edge(const InstDev& I, int x0, int y0) {
+  return x0 - 4 < 0 || x0 - 4 + G::BW > I.nx || y0 - G::H < 0 || y0 - G::H + G::BH > I.ny;
+}
+
+// Start staging tile `it` into dst: TMA copies issued by thread 0, or plain loads by all threads.
+template <typename T, class G, int TX, int TY>
+__device__ __forceinline__ void stage_begin(const BatchDev& b, int it, const PlaneList& pr, T* dst, uint64_t* bar,
+                                            int tid, int nthr) {
+  const TileRef t = decode_tile<TX, TY>(b, it);
+  const InstDev& I = b.inst[t.inst];
+  if (I.tma) {
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(bar, (unsigned)pr.n * G::PLANE_BYTES);
+      for (int k = 0; k < pr.n; ++k)
+        tma_load_3d(dst + k * G::PL, stage_map(I, pr.buf(k)), t.x0 - 4, t.y0 - G::H, pr.plane(k), bar);
+    }
+  } else {
+    stage_plain<T, G>(I, pr, dst, t.x0, t.y0, false, tid, nthr);
+  }
+}
+
+// The persistent, double-buffered tile loop: body(I, tile, staged planes) runs
+// for every tile of the batch assigned to this block.
+template <typename T, class G, int TX, int TY, class Body>
+__device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr, T* stage0, uint64_t* bars, int tid,
+                                          Body&& body) {
+  constexpr int NT = TX * TY;
+  const int ntiles = b.counts[0];
+  const int bstride = pr.n * G::PL;       // buffer 1 starts at stage0 + bstride
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned phase = 0u;                    // bit c: parity of the next phase of bars[c]
+  int it = blockIdx.x;
+  if (it < ntiles) stage_begin<T, G, TX, TY>(b, it, pr, stage0, &bars[0], tid, NT);
+  for (int cur = 0; it < ntiles; it += gridDim.x, cur ^= 1) {
+    const int nxt = it + gridDim.x;
+    bool next_tma = false;
+    if (nxt < ntiles) {
+      next_tma = b.inst[find_inst(b.tile_start, b.counts[3], nxt)].tma != 0;
+      stage_begin<T, G, TX, TY>(b, nxt, pr, stage0 + (cur ^ 1) * bstride, &bars[cur ^ 1], tid, NT);
+    }
+    T* sbuf = stage0 + cur * bstride;
+    const TileRef t = decode_tile<TX, TY>(b, it);
+    const InstDev& I = b.inst[t.inst];
+    if (I.tma) {
+      const bool ok = mbar_wait(&bars[cur], (phase >> cur) & 1u);
+      phase ^= 1u << cur;
+      if (__syncthreads_or(!ok)) {
+        // a copy did not complete: report, let the other buffer's copy land, stop
+        if (tid == 0) atomicOr(b.err, 2u);
+        if (next_tma) mbar_wait(&bars[cur ^ 1], (phase >> (cur ^ 1)) & 1u);
+        return;
+      }
+      if (tile_on_edge<G>(I, t.x0, t.y0)) stage_plain<T, G>(I, pr, sbuf, t.x0, t.y0, true, tid, NT);
+    }
+    __syncthreads();
+    body(I, t, sbuf);
+    __syncthreads();
   }
 }
 
@@ -79,72 +208,109 @@ __device__ __forceinline__ T combine(T nl, T dl, T nr, T dr) {
   return nl * frcp(dl) + nr * frcp(dr);
 }
 
+// Select a[i] for a small compile-time-sized array without local memory.
+template <int N, class P>
+__device__ __forceinline__ P pick(const P* a, int i) {
+  P r = a[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k)
+    if (i == k) r = a[k];
+  return r;
+}
+
 // One axis of upwind fluxes for NP flux/partner pairs on the interior lines of
-// a tile.  AX = 0: lines are the TY interior rows, points run along x over the
-// W columns of the halo'd tile, TX+1 interfaces per line, output [k][row][m].
-// AX = 1: lines are the TX interior columns, points along y over HH rows, TY+1
-// interfaces per line, output [k][m][col].  g[k], U[k]: halo'd smem tiles;
-// NEG bit k negates the flux of pair k.  split: 4 * NP * LS scratch.
+// a staged tile (row stride G::BW).  AX = 0: lines are the TY interior rows,
+// points run along x over the W logical columns, TX+1 interfaces per line,
+// output [k][row][m].  AX = 1: lines are the TX interior columns, points along
+// y over HH rows, TY+1 interfaces per line, output [k][m][col].  The split
+// scratch is line-major for AX = 0 and point-major for AX = 1, so that
+// neighbouring threads always touch neighbouring words of shared memory.
+// g[k], U[k]: staged tiles; NEG bit k negates the flux of pair k.
+// split: 4*NP*LS scratch.
 template <typename T, int SCHEME, int TX, int TY, int NP, unsigned NEG, int AX>
 __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U, T* split, T* out, T ew, int tid) {
-  constexpr int H = halo_of(SCHEME), W = TX + 2 * H, HH = TY + 2 * H;
+  using G = Geo<T, SCHEME, TX, TY>;
+  constexpr int H = G::H, W = G::W, HH = G::HH, SW = G::BW, XO = G::XO;
   constexpr int NL = AX == 0 ? TY : TX;           // lines
   constexpr int LL = AX == 0 ? W : HH;            // points per line
   constexpr int NI = AX == 0 ? TX + 1 : TY + 1;   // interfaces per line
   constexpr int LS = NL * LL;
+  constexpr int PS = AX == 0 ? 1 : NL;            // split stride between points of a line
   constexpr int NT = TX * TY;
-  auto in_off = [&](int line, int pt) { return AX == 0 ? (H + line) * W + pt : pt * W + (H + line); };
+  // index r of the split scratch -> (line, point), and of the interfaces -> (line, m)
+  auto pt_line = [&](int r, int& line, int& pt) {
+    if (AX == 0) { line = r / LL; pt = r - line * LL; }
+    else { pt = r / NL; line = r - pt * NL; }
+  };
+  auto if_line = [&](int r, int& line, int& m) {
+    if (AX == 0) { line = r / NI; m = r - line * NI; }
+    else { m = r / NL; line = r - m * NL; }
+  };
+  auto in_off = [&](int line, int pt) { return AX == 0 ? (H + line) * SW + XO + pt : pt * SW + XO + H + line; };
+  auto sp_off = [&](int line, int pt) { return AX == 0 ? line * LL + pt : pt * NL + line; };
   auto out_off = [&](int line, int m) { return AX == 0 ? line * NI + m : m * TX + line; };
   if (SCHEME == LF1_C2) {
     // hat g = (g_m + g_{m+1} - (U_{m+1} - U_m))/2 (Sec. 3.2, alpha = 1)
     for (int k = tid; k < NP * NL * NI; k += NT) {
-      const int pr = k / (NL * NI), r = k - pr * (NL * NI), line = r / NI, m = r - line * NI;
+      const int pr = k / (NL * NI);
+      int line, m;
+      if_line(k - pr * (NL * NI), line, m);
       const int o0 = in_off(line, H - 1 + m), o1 = in_off(line, H + m);
       const T sg = ((NEG >> pr) & 1u) ? T(-1) : T(1);
-      const T* gp = g[pr];
-      const T* up = U[pr];
+      const T* gp = pick<NP>(g, pr);
+      const T* up = pick<NP>(U, pr);
       out[pr * NL * NI + out_off(line, m)] = T(0.5) * (sg * gp[o0] + sg * gp[o1] - (up[o1] - up[o0]));
     }
     return;
   }
   // 1. flux splitting g+- = (g +- U)/2 at every point of every line
   for (int k = tid; k < NP * LS; k += NT) {
-    const int pr = k / LS, r = k - pr * LS, line = r / LL, pt = r - line * LL;
+    const int pr = k / LS, r = k - pr * LS;
+    int line, pt;
+    pt_line(r, line, pt);
     const int o = in_off(line, pt);
-    const T gv = ((NEG >> pr) & 1u) ? -g[pr][o] : g[pr][o];
-    const T uv = U[pr][o];
+    const T* gp = pick<NP>(g, pr);
+    const T gv = ((NEG >> pr) & 1u) ? -gp[o] : gp[o];
+    const T uv = pick<NP>(U, pr)[o];
     split[(4 * pr + 0) * LS + r] = T(0.5) * (gv + uv);
     split[(4 * pr + 1) * LS + r] = T(0.5) * (gv - uv);
   }
   __syncthreads();
   if (SCHEME == WENO3_C4) {
     for (int k = tid; k < NP * NL * NI; k += NT) {
-      const int pr = k / (NL * NI), r = k - pr * (NL * NI), line = r / NI, m = r - line * NI;
-      const T* Pp = split + (4 * pr + 0) * LS + line * LL;
-      const T* Mm = split + (4 * pr + 1) * LS + line * LL;
-      const int c = H - 1 + m;
-      out[pr * NL * NI + out_off(line, m)] = weno3<T>(Pp[c - 1], Pp[c], Pp[c + 1], ew) + weno3<T>(Mm[c + 2], Mm[c + 1], Mm[c], ew);
+      const int pr = k / (NL * NI);
+      int line, m;
+      if_line(k - pr * (NL * NI), line, m);
+      const int c = sp_off(line, H - 1 + m);
+      const T* Pp = split + (4 * pr + 0) * LS + c;
+      const T* Mm = split + (4 * pr + 1) * LS + c;
+      out[pr * NL * NI + out_off(line, m)] =
+          weno3<T>(Pp[-PS], Pp[0], Pp[PS], ew) + weno3<T>(Mm[2 * PS], Mm[PS], Mm[0], ew);
     }
     return;
   }
   // 2. curvature part of the smoothness indicators, scaled by 12, plus 12 eps_W
   const T ew12 = T(12) * ew;
   for (int k = tid; k < 2 * NP * LS; k += NT) {
-    const int q = k / LS, r = k - q * LS, pt = r % LL;
+    const int q = k / LS, r = k - q * LS;
+    int line, pt;
+    pt_line(r, line, pt);
     if (pt == 0 || pt == LL - 1) continue;
     const int pr = q >> 1, pm = q & 1;
     const T* f = split + (4 * pr + pm) * LS + r;
-    const T cv = f[-1] - T(2) * f[0] + f[1];
+    const T cv = f[-PS] - T(2) * f[0] + f[PS];
     split[(4 * pr + 2 + pm) * LS + r] = T(13) * cv * cv + ew12;
   }
   __syncthreads();
   // 3. interface fluxes: left-biased reconstruction of g+ centred at m, right-biased of g- centred at m+1
   for (int k = tid; k < NP * NL * NI; k += NT) {
-    const int pr = k / (NL * NI), r = k - pr * (NL * NI), line = r / NI, m = r - line * NI;
-    const int base = line * LL + (H - 1 + m);
+    const int pr = k / (NL * NI);
+    int line, m;
+    if_line(k - pr * (NL * NI), line, m);
+    const int base = sp_off(line, H - 1 + m);
     T nl, dl, nr, dr;
-    w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, 1, nl, dl);
-    w5_nd<T>(split + (4 * pr + 1) * LS + base + 1, split + (4 * pr + 3) * LS + base + 1, -1, nr, dr);
+    w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, PS, nl, dl);
+    w5_nd<T>(split + (4 * pr + 1) * LS + base + PS, split + (4 * pr + 3) * LS + base + PS, -PS, nr, dr);
     out[pr * NL * NI + out_off(line, m)] = combine<T>(nl, dl, nr, dr);
   }
 }
@@ -162,18 +328,35 @@ __device__ __forceinline__ T block_sum(T v, T* red, int tid, int nthr) {
   return r;
 }
 
+// Planes staged by k_update of stage i: theta, v1, v2 of X^(i), then u1, u2 of
+// every earlier stage that enters the dissipation partner.
+__device__ __forceinline__ PlaneList update_planes(const BatchDev& b, int i) {
+  PlaneList pr;
+  pr.add(i, 2);
+  pr.add(i, 3);
+  pr.add(i, 4);
+  for (int jj = 1; jj < i; ++jj)
+    if (aex(b, i, jj) - aim(b, i, jj) != 0.0) {
+      pr.add(jj, 0);
+      pr.add(jj, 1);
+    }
+  return pr;
+}
+
+// Byte sizes of the dynamic shared memory of each kernel (plus 128 for alignment).
 template <typename T, int SCHEME, int TX, int TY>
 struct StencilSmem {
-  static constexpr int H = halo_of(SCHEME), CH = central_halo(SCHEME);
-  static constexpr int W = TX + 2 * H, HH = TY + 2 * H, A = W * HH;
-  static constexpr int NX = TY * (TX + 1), NY = (TY + 1) * TX;
-  static constexpr int LS = (TY * W > HH * TX) ? TY * W : HH * TX;
-  static constexpr int SPLIT_PER_PAIR = SCHEME == LF1_C2 ? 0 : 4 * LS;
-  static constexpr size_t explicit_bytes = sizeof(T) * (6 * A + 3 * SPLIT_PER_PAIR + 3 * NX + 3 * NY);
-  static constexpr size_t rhs_bytes =
-      ((sizeof(T) * (2 * (TX + 2 * CH) * (TY + 2 * CH) + TY * (TX + 2 * CH)) + 15) / 16) * 16 + 32 * sizeof(double);
-  static constexpr size_t update_bytes = sizeof(T) * (5 * A + 2 * SPLIT_PER_PAIR + 2 * NX + 2 * NY);
+  using G = Geo<T, SCHEME, TX, TY>;
+  static constexpr size_t plane_bytes = sizeof(T) * G::PL;
+  static constexpr size_t explicit_bytes = 128 + sizeof(T) * (2 * 6 * G::PL + G::EXPLICIT_EXTRA);
+  static constexpr size_t rhs_bytes = 128 + sizeof(T) * (2 * 2 * G::PL) + sizeof(double) * G::RHS_EXTRA;
+  static constexpr size_t update_fixed_bytes = 128 + sizeof(T) * G::UPDATE_EXTRA;   // + 2 * np * plane_bytes
 };
+
+template <typename T>
+__device__ __forceinline__ T* aligned_smem(unsigned char* raw) {
+  return reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+}
 
 // ---------------------------------------------------------------------------
 // Closed-form v^(i) at one cell (step 1).  E^(jcur) and v^(jcur) may be given
@@ -209,39 +392,29 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_explicit(const BatchDev* __restrict__ bp, int j, unsigned need, double weno_eps) {
-  using SM = StencilSmem<T, SCHEME, TX, TY>;
-  constexpr int H = SM::H, W = SM::W, HH = SM::HH, A = SM::A, NX = SM::NX, NY = SM::NY;
+  using G = Geo<T, SCHEME, TX, TY>;
+  constexpr int BW = G::BW, PL = G::PL, NX = G::NX, NY = G::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su1 = reinterpret_cast<T*>(smem_raw);
-  T* su2 = su1 + A;
-  T* sth = su2 + A;
-  T* sv1 = sth + A;
-  T* sv2 = sv1 + A;
-  T* sq = sv2 + A;
-  T* split = sq + A;                   // 3 pairs
-  T* fx = split + 3 * SM::SPLIT_PER_PAIR;   // [3][NX]: (q;v1), (-v1;u1), (v2;u2)
-  T* fy = fx + 3 * NX;                       // [3][NY]: (q;v2), (v2;u1), (v1;u2)
+  __shared__ uint64_t bars[2];
+  T* stage = aligned_smem<T>(smem_raw);   // 2 x 6 planes
+  T* split = stage + 2 * 6 * PL;          // 3 pairs
+  T* fx = split + 3 * G::SPLIT_PER_PAIR;  // [3][NX]: (q;v1), (-v1;u1), (v2;u2)
+  T* fy = fx + 3 * NX;                    // [3][NY]: (q;v2), (v2;u1), (v1;u2)
   const BatchDev& b = *bp;
-  const int ntiles = b.counts[0];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * TX;
   const T ew = T(weno_eps);
   const bool needB = (need & NEED_DLFB) != 0, needE = (need & NEED_E) != 0;
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    const int k_inst = find_inst(b.tile_start, b.counts[3], it);
-    const InstDev& I = b.inst[k_inst];
-    const int tile = it - b.tile_start[k_inst];
-    const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
-    const int nx = I.nx, ny = I.ny, mx = nx - 1, my = ny - 1;
-    const size_t pl = (size_t)nx * ny;
-    const T* g = reinterpret_cast<const T*>(j == 1 ? I.X : I.Xs[j]);
-    const int x0 = txi * TX, y0 = tyi * TY;
-    load_region<T>(su1, W, HH, g, x0, y0, H, mx, my, nx, tid, TX * TY);
-    load_region<T>(su2, W, HH, g + pl, x0, y0, H, mx, my, nx, tid, TX * TY);
-    load_region<T>(sth, W, HH, g + 2 * pl, x0, y0, H, mx, my, nx, tid, TX * TY);
-    load_region<T>(sv1, W, HH, g + 3 * pl, x0, y0, H, mx, my, nx, tid, TX * TY);
-    load_region<T>(sv2, W, HH, g + 4 * pl, x0, y0, H, mx, my, nx, tid, TX * TY);
-    load_region<T>(sq, W, HH, g + 5 * pl, x0, y0, H, mx, my, nx, tid, TX * TY);
-    __syncthreads();
+  PlaneList pr;
+  for (int k = 0; k < 6; ++k) pr.add(j, k);
+  tile_loop<T, G, TX, TY>(b, pr, stage, bars, tid, [&](const InstDev& I, const TileRef& t, T* s) {
+    const T* su1 = s;
+    const T* su2 = s + PL;
+    const T* sth = s + 2 * PL;
+    const T* sv1 = s + 3 * PL;
+    const T* sv2 = s + 4 * PL;
+    const T* sq = s + 5 * PL;
+    const int nx = I.nx;
+    const size_t pl = (size_t)nx * I.ny;
     // x-interfaces, then y-interfaces (the split scratch is reused)
     if (needE && needB) {
       const T* gx[3] = {sq, sv1, sv2};
@@ -270,12 +443,12 @@ __global__ void __launch_bounds__(TX* TY) k_explicit(const BatchDev* __restrict_
     }
     __syncthreads();
     const T idx = T(I.inv_dx), idy = T(I.inv_dy);
-    const int c = (H + ty) * W + (H + tx);
-    const size_t o = (size_t)(y0 + ty) * nx + (x0 + tx);
+    const int c = G::C00 + ty * BW + tx;
+    const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
     T e1 = T(0), e2 = T(0);
     if (needE) {
-      const T b1 = cdiff<T, SCHEME>(su2 + c, W, idy) - cdiff<T, SCHEME>(su1 + c, 1, idx);
-      const T b2 = cdiff<T, SCHEME>(su2 + c, 1, idx) + cdiff<T, SCHEME>(su1 + c, W, idy);
+      const T b1 = cdiff<T, SCHEME>(su2 + c, BW, idy) - cdiff<T, SCHEME>(su1 + c, 1, idx);
+      const T b2 = cdiff<T, SCHEME>(su2 + c, 1, idx) + cdiff<T, SCHEME>(su1 + c, BW, idy);
       const T g1 = (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * idx;
       const T g2 = (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * idy;
       const T a1 = su1[c], a2 = su2[c];
@@ -288,15 +461,15 @@ __global__ void __launch_bounds__(TX* TY) k_explicit(const BatchDev* __restrict_
       e[o + pl] = e2;
     }
     if (need & NEED_DU) {
-      reinterpret_cast<T*>(I.Du[j])[o] = cdiff<T, SCHEME>(su1 + c, 1, idx) + cdiff<T, SCHEME>(su2 + c, W, idy);
+      reinterpret_cast<T*>(I.Du[j])[o] = cdiff<T, SCHEME>(su1 + c, 1, idx) + cdiff<T, SCHEME>(su2 + c, BW, idy);
     }
     if (need & NEED_LTH) {
-      reinterpret_cast<T*>(I.Lth[j])[o] = cdiff2<T, SCHEME>(sth + c, 1, idx * idx) + cdiff2<T, SCHEME>(sth + c, W, idy * idy);
+      reinterpret_cast<T*>(I.Lth[j])[o] = cdiff2<T, SCHEME>(sth + c, 1, idx * idx) + cdiff2<T, SCHEME>(sth + c, BW, idy * idy);
     }
     if (need & NEED_GTH) {
       T* gt = reinterpret_cast<T*>(I.Gth[j]);
       gt[o] = cdiff<T, SCHEME>(sth + c, 1, idx);
-      gt[o + pl] = cdiff<T, SCHEME>(sth + c, W, idy);
+      gt[o + pl] = cdiff<T, SCHEME>(sth + c, BW, idy);
     }
     if (needB) {
       const T* fxb = fx + NX;
@@ -318,44 +491,39 @@ __global__ void __launch_bounds__(TX* TY) k_explicit(const BatchDev* __restrict_
       vi[o + 3 * pl] = r1;
       vi[o + 4 * pl] = r2;
     }
-    __syncthreads();
-  }
+  });
 }
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign, int first_stage) {
-  constexpr int CH = central_halo(SCHEME), W = TX + 2 * CH, HH = TY + 2 * CH, A = W * HH;
+  using G = Geo<T, SCHEME, TX, TY>;
+  constexpr int BW = G::BW, PL = G::PL, CH = G::CH, WD = TX + 2 * CH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sv1 = reinterpret_cast<T*>(smem_raw);
-  T* sv2 = sv1 + A;
-  T* sdy = sv2 + A;                       // [TY][W]: d_y v2 on interior rows
-  T* red = reinterpret_cast<T*>(smem_raw + ((sizeof(T) * (2 * A + TY * W) + 15) / 16) * 16);  // 32 doubles
+  __shared__ uint64_t bars[2];
+  T* stage = aligned_smem<T>(smem_raw);        // 2 x 2 planes: v1, v2 of X^(i)
+  T* sdy = stage + 2 * 2 * PL;                 // [TY][WD]: d_y v2 on interior rows
+  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(sdy + TY * WD) + 7) & ~uintptr_t(7));
   const BatchDev& b = *bp;
-  const int ntiles = b.counts[0];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * TX;
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    const int k_inst = find_inst(b.tile_start, b.counts[3], it);
-    const InstDev& I = b.inst[k_inst];
-    const int tile = it - b.tile_start[k_inst];
-    const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
-    const int nx = I.nx, ny = I.ny, mx = nx - 1, my = ny - 1;
-    const size_t pl = (size_t)nx * ny;
-    const int x0 = txi * TX, y0 = tyi * TY;
-    const T* vi = reinterpret_cast<const T*>(I.Xs[i]);
-    load_region<T>(sv1, W, HH, vi + 3 * pl, x0, y0, CH, mx, my, nx, tid, TX * TY);
-    load_region<T>(sv2, W, HH, vi + 4 * pl, x0, y0, CH, mx, my, nx, tid, TX * TY);
-    __syncthreads();
+  PlaneList pr;
+  pr.add(i, 3);
+  pr.add(i, 4);
+  tile_loop<T, G, TX, TY>(b, pr, stage, bars, tid, [&](const InstDev& I, const TileRef& t, T* s) {
+    const T* sv1 = s;
+    const T* sv2 = s + PL;
+    const int nx = I.nx;
+    const size_t pl = (size_t)nx * I.ny;
     const T idx = T(I.inv_dx), idy = T(I.inv_dy);
-    for (int k = tid; k < TY * W; k += TX * TY) {
-      const int r = k / W, cc = k - r * W;
-      sdy[k] = cdiff<T, SCHEME>(sv2 + (CH + r) * W + cc, W, idy);
+    for (int k = tid; k < TY * WD; k += TX * TY) {
+      const int r = k / WD, cc = k - r * WD;
+      sdy[k] = cdiff<T, SCHEME>(sv2 + (G::H + r) * BW + (4 - CH) + cc, BW, idy);
     }
     __syncthreads();
-    const int c = (CH + ty) * W + (CH + tx);
-    const size_t o = (size_t)(y0 + ty) * nx + (x0 + tx);
-    const T dbi = -cdiff2<T, SCHEME>(sv1 + c, 1, idx * idx) + T(2) * cdiff<T, SCHEME>(sdy + ty * W + CH + tx, 1, idx) +
-                  cdiff2<T, SCHEME>(sv1 + c, W, idy * idy);
+    const int c = G::C00 + ty * BW + tx;
+    const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
+    const T dbi = -cdiff2<T, SCHEME>(sv1 + c, 1, idx * idx) + T(2) * cdiff<T, SCHEME>(sdy + ty * WD + CH + tx, 1, idx) +
+                  cdiff2<T, SCHEME>(sv1 + c, BW, idy * idy);
     reinterpret_cast<T*>(I.DB[i])[o] = dbi;
     // right-hand side of the Helmholtz equation (Algorithm 1, step 2; theta-history sign per
     // reading G4), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii precomputed
@@ -371,60 +539,51 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
       if (aim(b, i, jj) != 0.0) R = R + T(theta_sign < 0 ? I.c_lth[i][jj] : -I.c_lth[i][jj]) * reinterpret_cast<const T*>(I.Lth[jj])[o];
     reinterpret_cast<T*>(I.R)[o] = R;
     if (first_stage) {
-      const double tsum = block_sum<double>(double(thn), reinterpret_cast<double*>(red), tid, TX * TY);
-      if (tid == 0) I.th_part[tile] = tsum;
-    } else {
-      __syncthreads();
+      const double tsum = block_sum<double>(double(thn), red, tid, TX * TY);
+      if (tid == 0) I.th_part[t.tile] = tsum;
     }
-  }
+  });
 }
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ bp, int i, double weno_eps) {
-  using SM = StencilSmem<T, SCHEME, TX, TY>;
-  constexpr int H = SM::H, W = SM::W, HH = SM::HH, A = SM::A, NX = SM::NX, NY = SM::NY;
+  using G = Geo<T, SCHEME, TX, TY>;
+  constexpr int BW = G::BW, PL = G::PL, NX = G::NX, NY = G::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sv1 = reinterpret_cast<T*>(smem_raw);
-  T* sv2 = sv1 + A;
-  T* sp1 = sv2 + A;
-  T* sp2 = sp1 + A;
-  T* sth = sp2 + A;
-  T* split = sth + A;                     // 2 pairs
-  T* fx = split + 2 * SM::SPLIT_PER_PAIR;  // [2][NX]: (-v1;p1), (v2;p2)
-  T* fy = fx + 2 * NX;                     // [2][NY]: (v2;p1), (v1;p2)
+  __shared__ uint64_t bars[2];
   const BatchDev& b = *bp;
-  const int ntiles = b.counts[0];
+  const PlaneList pr = update_planes(b, i);
+  const int np = pr.n;
+  T* stage = aligned_smem<T>(smem_raw);    // 2 x np planes
+  T* sp1 = stage + 2 * np * PL;            // dissipation partner
+  T* sp2 = sp1 + PL;
+  T* split = sp2 + PL;                     // 2 pairs
+  T* fx = split + 2 * G::SPLIT_PER_PAIR;   // [2][NX]: (-v1;p1), (v2;p2)
+  T* fy = fx + 2 * NX;                     // [2][NY]: (v2;p1), (v1;p2)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * TX;
   const T ew = T(weno_eps);
   const double aii = aim(b, i, i);
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    const int k_inst = find_inst(b.tile_start, b.counts[3], it);
-    const InstDev& I = b.inst[k_inst];
-    const int tile = it - b.tile_start[k_inst];
-    const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
-    const int nx = I.nx, ny = I.ny, mx = nx - 1, my = ny - 1;
-    const size_t pl = (size_t)nx * ny;
-    const int x0 = txi * TX, y0 = tyi * TY;
-    const T* Xi = reinterpret_cast<const T*>(I.Xs[i]);
-    load_region<T>(sv1, W, HH, Xi + 3 * pl, x0, y0, H, mx, my, nx, tid, TX * TY);
-    load_region<T>(sv2, W, HH, Xi + 4 * pl, x0, y0, H, mx, my, nx, tid, TX * TY);
-    load_region<T>(sth, W, HH, Xi + 2 * pl, x0, y0, H, mx, my, nx, tid, TX * TY);
+  tile_loop<T, G, TX, TY>(b, pr, stage, bars, tid, [&](const InstDev& I, const TileRef& t, T* s) {
+    const T* sth = s;
+    const T* sv1 = s + PL;
+    const T* sv2 = s + 2 * PL;
+    const int nx = I.nx;
+    const size_t pl = (size_t)nx * I.ny;
     // dissipation partner of D_LF . B(v^(i)) (reading G6): (1/a_ii) sum_{j<i} (atilde_ij - a_ij) u^(j)
-    for (int k = tid; k < A; k += TX * TY) {
-      const int ly = k / W, lx = k - ly * W;
-      const size_t go = (size_t)((y0 - H + ly) & my) * nx + ((x0 - H + lx) & mx);
+    for (int e = tid; e < G::BW * G::BH; e += TX * TY) {
       T p1 = T(0), p2 = T(0);
+      int k = 3;
       for (int jj = 1; jj < i; ++jj) {
         const double w = aex(b, i, jj) - aim(b, i, jj);
         if (w != 0.0) {
-          const T* u = reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj]);
-          p1 = p1 + T(w) * u[go];
-          p2 = p2 + T(w) * u[go + pl];
+          p1 = p1 + T(w) * s[k * PL + e];
+          p2 = p2 + T(w) * s[(k + 1) * PL + e];
+          k += 2;
         }
       }
-      sp1[k] = p1 * T(I.inv_aii[i]);
-      sp2[k] = p2 * T(I.inv_aii[i]);
+      sp1[e] = p1 * T(I.inv_aii[i]);
+      sp2[e] = p2 * T(I.inv_aii[i]);
     }
     __syncthreads();
     {
@@ -438,13 +597,13 @@ __global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ 
     }
     __syncthreads();
     const T idx = T(I.inv_dx), idy = T(I.inv_dy);
-    const int c = (H + ty) * W + (H + tx);
-    const size_t o = (size_t)(y0 + ty) * nx + (x0 + tx);
+    const int c = G::C00 + ty * BW + tx;
+    const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
     const T d1 = (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * idx + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * idy;
     const T d2 = (fx[NX + ty * (TX + 1) + tx + 1] - fx[NX + ty * (TX + 1) + tx]) * idx +
                  (fy[NY + (ty + 1) * TX + tx] - fy[NY + ty * TX + tx]) * idy;
-    const T g1 = cdiff<T, SCHEME>(sth + c, 1, idx), g2 = cdiff<T, SCHEME>(sth + c, W, idy);
-    const T dvi = cdiff<T, SCHEME>(sv1 + c, 1, idx) + cdiff<T, SCHEME>(sv2 + c, W, idy);
+    const T g1 = cdiff<T, SCHEME>(sth + c, 1, idx), g2 = cdiff<T, SCHEME>(sth + c, BW, idy);
+    const T dvi = cdiff<T, SCHEME>(sv1 + c, 1, idx) + cdiff<T, SCHEME>(sv2 + c, BW, idy);
     // step 3
     T s1 = T(0), s2 = T(0);
     for (int jj = 1; jj < i; ++jj) {
@@ -487,8 +646,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ 
       }
       out[o + 5 * pl] = (T(I.te2) * Xn[o + 5 * pl] - dt * (sD + sQ)) * T(I.inv_den[i]);
     }
-    __syncthreads();
-  }
+  });
 }
 
 }  // namespace apd

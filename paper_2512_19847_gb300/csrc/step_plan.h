@@ -2,6 +2,12 @@
 // stage 1 = X^n, GSA close), shared by the handle path and the
 // no-allocation entry point.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+
 #include "../../include/ap_dvm.h"
 #include "common.cuh"
 #include "dispatch.h"
@@ -15,7 +21,59 @@ struct StepKernels {
   MiscSet km;
   int g_explicit, g_rhs, g_update, g_finish, g_fft;
   size_t fft_smem;
+  size_t smem_update;
 };
+
+// Planes k_update stages at its largest stage: theta, v1, v2 and u1, u2 of every
+// earlier stage entering the dissipation partner (reading G6).
+inline int update_planes_max(const ap_dvm_params& t) {
+  int best = 0;
+  for (int i = 2; i <= t.s; ++i) {
+    int np = 3;
+    for (int j = 1; j < i; ++j)
+      if (t.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)] - t.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)] != 0.0) np += 2;
+    if (np > best) best = np;
+  }
+  return best;
+}
+
+inline size_t update_smem(const StencilSet& ks, const ap_dvm_params& t) {
+  return ks.update_fixed + 2 * (size_t)update_planes_max(t) * ks.plane_bytes;
+}
+
+// Tensor maps of the stage buffers of one instance for TMA staging: map j
+// (j = 1: the state X, j >= 2: X^(j)) describes 6 planes of nx x ny values as a
+// 3D tensor (x, y, plane) with a box of bw x bh x 1.  Writes s+1 maps to out
+// (64-byte aligned) and returns 1, or 0 when TMA is not used for this
+// instance (grid smaller than the box, no driver entry point, or the
+// environment variable AP_DVM_NO_TMA set).
+inline int encode_stage_maps(const ap_dvm_params& p, const InstDev& d, int bw, int bh, CUtensorMap* out) {
+  if (std::getenv("AP_DVM_NO_TMA")) return 0;
+  if (p.nx < bw || p.ny < bh) return 0;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return 0;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const bool f64 = p.precision == AP_DVM_FP64;
+  const size_t es = f64 ? 8 : 4;
+  const cuuint64_t dims[3] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny, 6};
+  const cuuint64_t strides[2] = {(cuuint64_t)p.nx * es, (cuuint64_t)p.nx * p.ny * es};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int j = 1; j <= p.s; ++j) {
+    void* base = (j == 1) ? d.X : d.Xs[j];
+    const CUresult r = encode(&out[j], f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return 0;
+  }
+  return 1;
+}
 
 // launch(fn, grid, block, smem, args, kind) -> int status (0 = success)
 template <class Launch>
@@ -57,7 +115,7 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
     }
     {
       void* a[] = {&bp, &i, &weno_eps};
-      if ((st = launch(K.ks.k_update, K.g_update, blk, K.ks.smem_update, a, KK_UPDATE))) return st;
+      if ((st = launch(K.ks.k_update, K.g_update, blk, K.smem_update, a, KK_UPDATE))) return st;
     }
   }
   void* a[] = {&bp, &f32};
