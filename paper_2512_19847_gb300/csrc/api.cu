@@ -55,6 +55,7 @@ struct ap_dvm_handle {
   int* d_col_start = nullptr;
   int* d_counts = nullptr;
   double2* d_tw = nullptr;
+  float2* d_tw32 = nullptr;
   unsigned* d_err = nullptr;
   BatchDev hb{};
   std::vector<Slot> slots;
@@ -210,6 +211,7 @@ size_t batch_bytes(int capacity, int nmax) {
   take(sizeof(int) * (capacity + 1));
   take(sizeof(int) * 4);
   take(sizeof(double2) * (nmax / 2));
+  take(sizeof(float2) * (nmax / 2));
   take(sizeof(unsigned) * 4);
   return align_up(off, 256);
 }
@@ -471,14 +473,18 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   h->d_col_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
   h->d_counts = reinterpret_cast<int*>(take(sizeof(int) * 4));
   h->d_tw = reinterpret_cast<double2*>(take(sizeof(double2) * (h->nmax / 2)));
+  h->d_tw32 = reinterpret_cast<float2*>(take(sizeof(float2) * (h->nmax / 2)));
   h->d_err = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * 4));
   // twiddles exp(-2 pi i k / nmax) from long double
   std::vector<double2> tw(h->nmax / 2);
+  std::vector<float2> tw32(h->nmax / 2);
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int k = 0; k < h->nmax / 2; ++k) {
     const long double a = -2.0L * pi * (long double)k / (long double)h->nmax;
     tw[k].x = (double)std::cos(a);
     tw[k].y = (double)std::sin(a);
+    tw32[k].x = (float)std::cos(a);
+    tw32[k].y = (float)std::sin(a);
   }
   BatchDev& hb = h->hb;
   hb.inst = h->d_inst;
@@ -487,12 +493,14 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   hb.col_start = h->d_col_start;
   hb.counts = h->d_counts;
   hb.tw = h->d_tw;
+  hb.tw32 = h->d_tw32;
   hb.lnmax = h->lnmax;
   hb.s = tmpl->s;
-  for (int k = 0; k < APD_MAXS * APD_MAXS; ++k) { hb.A_ex[k] = tmpl->A_ex[k]; hb.A_im[k] = tmpl->A_im[k]; }
+  fill_tableau(*tmpl, hb);
   hb.err = h->d_err;
   // synchronous uploads: the host vectors go out of scope
   CUDA_TRY(h, cudaMemcpy(h->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(h, cudaMemcpy(h->d_batch, &hb, sizeof(BatchDev), cudaMemcpyHostToDevice));
   CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned) * 4));
   int zeros[4] = {0, 0, 0, 0};

@@ -23,6 +23,31 @@ enum Scheme { LF1_C2 = 0, WENO3_C4 = 1, WENO5_C4 = 2 };
 __host__ __device__ constexpr int halo_of(int scheme) { return scheme == LF1_C2 ? 1 : (scheme == WENO3_C4 ? 2 : 3); }
 __host__ __device__ constexpr int central_halo(int scheme) { return scheme == LF1_C2 ? 1 : 2; }
 
+// Stage coefficients of one instance in the scalar type T, computed on the
+// host in FP64 and rounded once, so that no kernel converts or combines
+// uniform coefficients per thread.  Stage indices are 1-based as in the paper.
+template <typename T>
+struct Coef {
+  T dt, te2, qtau, htau;                  // dt, tau eps^2, tau/4, tau/2
+  T inv_dx, inv_dy;
+  T kappa[APD_MAXS + 1];                  // 2 eps^2 / (dt a_ii)^2
+  T aex[APD_MAXS + 1][APD_MAXS + 1];      // atilde_ij
+  T aim[APD_MAXS + 1][APD_MAXS + 1];      // a_ij
+  T wp[APD_MAXS + 1][APD_MAXS + 1];       // (atilde_ij - a_ij) / a_ii: dissipation-partner weights (reading G6)
+  // closed forms of steps 1 and 4 with the division folded into the coefficients:
+  //   v^(i) = r_n v^n + sum_j rv_e E^(j) + sum_j rv_v v^(j),
+  //   q^(i) = r_n q^n + sum_{j<=i} rq_d D0.v^(j) + sum_{j<i} rq_q q^(j)
+  T r_n[APD_MAXS + 1];                    // tau eps^2 / (tau eps^2 + dt a_ii)
+  T rv_e[APD_MAXS + 1][APD_MAXS + 1];     // -dt atilde_ij / (tau eps^2 + dt a_ii)
+  T rv_v[APD_MAXS + 1][APD_MAXS + 1];     // -dt a_ij / (tau eps^2 + dt a_ii)
+  T rq_d[APD_MAXS + 1][APD_MAXS + 1];     // -dt a_ij (tau/2) / (tau eps^2 + dt a_ii)
+  // coefficients of the Helmholtz right-hand side of stage i (Algorithm 1, step 2):
+  T c_du[APD_MAXS + 1][APD_MAXS + 1];     // a_ij / (dt a_ii^2), j < i
+  T c_dun[APD_MAXS + 1];                  // 1 / (dt a_ii)
+  T c_db[APD_MAXS + 1][APD_MAXS + 1];     // a_ij / a_ii, j <= i
+  T c_lth[APD_MAXS + 1][APD_MAXS + 1];    // -a_ij / a_ii, j < i (reading G4)
+};
+
 // Per-instance description, resident in device memory.  Plane pointers are
 // untyped: the scalar type is the batch's transport type T (double for the
 // FP64 form, float for the FP32-deviation form).
@@ -39,12 +64,9 @@ struct InstDev {
   double inv_den[APD_MAXS + 1]; // 1 / (tau eps^2 + dt a_ii)
   double sc_u, sc_th, sc_v, sc_q;  // population view: 1/(rho0 A), 1/(2 eps rho0 A), 1/(eps rho0 A), 1/(eps^2 rho0 A)
   double inv_dx, inv_dy;
-  // coefficients of the Helmholtz right-hand side of stage i (Algorithm 1, step 2), by [i][j]:
-  double c_du[APD_MAXS + 1][APD_MAXS + 1];   // a_ij / (dt a_ii^2), j < i
-  double c_dun[APD_MAXS + 1];                // 1 / (dt a_ii)
-  double c_db[APD_MAXS + 1][APD_MAXS + 1];   // a_ij / a_ii, j <= i
-  double c_lth[APD_MAXS + 1][APD_MAXS + 1];  // -a_ij / a_ii, j < i (reading G4)
   double inv_aii[APD_MAXS + 1];              // 1 / a_ii
+  Coef<double> k64;             // the stage coefficients in FP64 ...
+  Coef<float> k32;              // ... and rounded once to FP32
   void* X;                      // 6 planes: state at t^n (moments)
   void* Xs[APD_MAXS + 1];       // stage values X^(j), j = 2..s (6 planes); Xs[s] = next state
   void* E[APD_MAXS + 1];        // explicit term of step 1 for stage j (2 planes)
@@ -74,10 +96,14 @@ struct BatchDev {
   int* col_start;        // [n+1]
   int* counts;           // [0] tiles, [1] row items, [2] column items, [3] instances
   double2* tw;           // twiddles exp(-2 pi i k / nmax), k < nmax/2
+  float2* tw32;          // the same, rounded once to FP32 (FP32 form)
   int lnmax;             // log2 of the largest transform length
   int s;                 // stages
   double A_ex[APD_MAXS * APD_MAXS];
   double A_im[APD_MAXS * APD_MAXS];
+  // nonzero patterns of the tableau rows, bit j for entry (i, j): atilde_ij,
+  // a_ij (j <= i) and atilde_ij - a_ij (the dissipation partner, j < i)
+  unsigned m_ex[APD_MAXS + 1], m_im[APD_MAXS + 1], m_wp[APD_MAXS + 1];
   unsigned* err;         // device error flags (bit 0: non-finite state, bit 1: a bounded wait expired)
 };
 
@@ -90,6 +116,11 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ start, int n, i
   }
   return lo;
 }
+
+template <typename T> __device__ __forceinline__ const Coef<T>& coef(const InstDev& I);
+template <> __device__ __forceinline__ const Coef<double>& coef<double>(const InstDev& I) { return I.k64; }
+template <> __device__ __forceinline__ const Coef<float>& coef<float>(const InstDev& I) { return I.k32; }
+__device__ __forceinline__ bool has(unsigned mask, int j) { return (mask >> j) & 1u; }
 
 // Row-major tableau access, 1-based stage indices as in the paper.
 __device__ __forceinline__ double aex(const BatchDev& b, int i, int j) { return b.A_ex[(i - 1) * APD_MAXS + (j - 1)]; }

@@ -21,12 +21,18 @@ template <typename T> struct Cplx;
 template <> struct Cplx<double> { using type = double2; };
 template <> struct Cplx<float> { using type = float2; };
 
+// Twiddles in the transform's own type (no conversion per butterfly).
+template <typename T> __device__ __forceinline__ const typename Cplx<T>::type* twiddles(const BatchDev& b);
+template <> __device__ __forceinline__ const double2* twiddles<double>(const BatchDev& b) { return b.tw; }
+template <> __device__ __forceinline__ const float2* twiddles<float>(const BatchDev& b) { return b.tw32; }
+
 __device__ __forceinline__ int brev(int k, int ln) { return (int)(__brev((unsigned)k) >> (32 - ln)); }
 
 // ntr transforms of length n = 2^ln held back to back in x[], input in
 // bit-reversed order, output natural.  Twiddle W_m^p = tw[p * nmax/m].
 template <typename T>
-__device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int ntr, const double2* __restrict__ tw, int lnmax,
+__device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int ntr,
+                                        const typename Cplx<T>::type* __restrict__ tw, int lnmax,
                                         bool inv, int tid, int nthr) {
   const int n = 1 << ln, nb = ntr * (n >> 1);
   for (int s = 1; s <= ln; ++s) {
@@ -35,8 +41,8 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
       const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
       const int pos = bi & (half - 1), grp = bi >> (s - 1);
       const int i0 = t * n + grp * 2 * half + pos, i1 = i0 + half;
-      const double2 w = tw[pos << sh];
-      const T wr = T(w.x), wi = inv ? T(-w.y) : T(w.y);
+      const auto w = tw[pos << sh];
+      const T wr = w.x, wi = inv ? -w.y : w.y;
       const auto a = x[i0], bb = x[i1];
       const T tr = wr * bb.x - wi * bb.y, ti = wr * bb.y + wi * bb.x;
       x[i1].x = a.x - tr; x[i1].y = a.y - ti;
@@ -48,7 +54,8 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
 
 // Natural-order input, bit-reversed output.
 template <typename T>
-__device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int ntr, const double2* __restrict__ tw, int lnmax,
+__device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int ntr,
+                                        const typename Cplx<T>::type* __restrict__ tw, int lnmax,
                                         bool inv, int tid, int nthr) {
   const int n = 1 << ln, nb = ntr * (n >> 1);
   for (int s = ln; s >= 1; --s) {
@@ -57,8 +64,8 @@ __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int n
       const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
       const int pos = bi & (half - 1), grp = bi >> (s - 1);
       const int i0 = t * n + grp * 2 * half + pos, i1 = i0 + half;
-      const double2 w = tw[pos << sh];
-      const T wr = T(w.x), wi = inv ? T(-w.y) : T(w.y);
+      const auto w = tw[pos << sh];
+      const T wr = w.x, wi = inv ? -w.y : w.y;
       const auto a = x[i0], bb = x[i1];
       const T dr = a.x - bb.x, di = a.y - bb.y;
       x[i0].x = a.x + bb.x; x[i0].y = a.y + bb.y;
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(256) k_fft_rows_fwd(const BatchDev* __restrict
       x[p * n + brev(k, ln)] = z;
     }
     __syncthreads();
-    fft_dit<T>(x, ln, ntr, b.tw, b.lnmax, false, tid, nthr);
+    fft_dit<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, false, tid, nthr);
     C* S = reinterpret_cast<C*>(I.S);
     const int nh = (n >> 1) + 1;
     for (int e = tid; e < ntr * nh; e += nthr) {
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(const BatchDev* __restrict__ b
       x[g * n + brev(y, ln)] = S[(size_t)y * ss + col0 + g];
     }
     __syncthreads();
-    fft_dit<T>(x, ln, ntr, b.tw, b.lnmax, false, tid, nthr);
+    fft_dit<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, false, tid, nthr);
     const double kap = I.kappa[i];
     const double scale = 1.0 / ((double)I.nx * (double)I.ny);
     for (int e = tid; e < ntr * n; e += nthr) {
@@ -160,7 +167,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(const BatchDev* __restrict__ b
       x[e] = v;
     }
     __syncthreads();
-    fft_dif<T>(x, ln, ntr, b.tw, b.lnmax, true, tid, nthr);
+    fft_dif<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, true, tid, nthr);
     for (int e = tid; e < ntr * n; e += nthr) {
       const int g = e >> ln, y = e & (n - 1);
       S[(size_t)y * ss + col0 + g] = x[g * n + brev(y, ln)];
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(256) k_fft_rows_inv(const BatchDev* __restrict
       x[e] = z;
     }
     __syncthreads();
-    fft_dif<T>(x, ln, ntr, b.tw, b.lnmax, true, tid, nthr);
+    fft_dif<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, true, tid, nthr);
     T* th = reinterpret_cast<T*>(I.Xs[i]) + 2 * (size_t)I.nx * I.ny;
     for (int e = tid; e < ntr * n; e += nthr) {
       const int p = e >> ln, m = e & (n - 1);

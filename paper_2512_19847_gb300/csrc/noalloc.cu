@@ -175,7 +175,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   B.tw = reinterpret_cast<double2*>(base + L.tw);
   B.lnmax = ilog2(nmax);
   B.s = p->s;
-  for (int k = 0; k < APD_MAXS * APD_MAXS; ++k) { B.A_ex[k] = p->A_ex[k]; B.A_im[k] = p->A_im[k]; }
+  fill_tableau(*p, B);
   B.err = reinterpret_cast<unsigned*>(base + L.err);
   const int ntiles = I.tiles_x * I.tiles_y;
   const int nrows = (p->ny / 2 + I.row_pairs - 1) / I.row_pairs;

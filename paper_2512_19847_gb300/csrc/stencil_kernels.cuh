@@ -336,7 +336,7 @@ __device__ __forceinline__ PlaneList update_planes(const BatchDev& b, int i) {
   pr.add(i, 3);
   pr.add(i, 4);
   for (int jj = 1; jj < i; ++jj)
-    if (aex(b, i, jj) - aim(b, i, jj) != 0.0) {
+    if (has(b.m_wp[i], jj)) {
       pr.add(jj, 0);
       pr.add(jj, 1);
     }
@@ -359,34 +359,35 @@ __device__ __forceinline__ T* aligned_smem(unsigned char* raw) {
 }
 
 // ---------------------------------------------------------------------------
-// Closed-form v^(i) at one cell (step 1).  E^(jcur) and v^(jcur) may be given
-// in registers (the values the kernel has just computed or loaded).
+// Closed-form v^(i) at one cell (step 1):
+//   v^(i) = (tau eps^2 v^n - dt sum_j atilde_ij E^(j) - dt sum_j a_ij v^(j)) / (tau eps^2 + dt a_ii),
+// evaluated in R with the division folded into the coefficients.  E^(jcur)
+// and v^(jcur) may be given in registers (the values the kernel has just
+// computed or loaded).
 template <typename R, typename T>
 __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I, int i, size_t o, size_t pl, int jcur,
                                              T ecur1, T ecur2, T vcur1, T vcur2, T& r1, T& r2) {
   const T* Xn = reinterpret_cast<const T*>(I.X);
-  R s1 = R(0), s2 = R(0), w1 = R(0), w2 = R(0);
+  const Coef<R>& K = coef<R>(I);
+  R a1 = K.r_n[i] * R(Xn[o + 3 * pl]), a2 = K.r_n[i] * R(Xn[o + 4 * pl]);
   for (int jj = 1; jj < i; ++jj) {
-    const double ae = aex(b, i, jj);
-    if (ae != 0.0) {
+    if (has(b.m_ex[i], jj)) {
       T e1, e2;
       if (jj == jcur) { e1 = ecur1; e2 = ecur2; }
       else { const T* e = reinterpret_cast<const T*>(I.E[jj]); e1 = e[o]; e2 = e[o + pl]; }
-      s1 = s1 + R(ae) * R(e1);
-      s2 = s2 + R(ae) * R(e2);
+      a1 = a1 + K.rv_e[i][jj] * R(e1);
+      a2 = a2 + K.rv_e[i][jj] * R(e2);
     }
-    const double ai = aim(b, i, jj);
-    if (ai != 0.0) {
-      T a1, a2;
-      if (jj == jcur) { a1 = vcur1; a2 = vcur2; }
-      else { const T* v = reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj]); a1 = v[o + 3 * pl]; a2 = v[o + 4 * pl]; }
-      w1 = w1 + R(ai) * R(a1);
-      w2 = w2 + R(ai) * R(a2);
+    if (has(b.m_im[i], jj)) {
+      T x1, x2;
+      if (jj == jcur) { x1 = vcur1; x2 = vcur2; }
+      else { const T* v = reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj]); x1 = v[o + 3 * pl]; x2 = v[o + 4 * pl]; }
+      a1 = a1 + K.rv_v[i][jj] * R(x1);
+      a2 = a2 + K.rv_v[i][jj] * R(x2);
     }
   }
-  const R te2 = R(I.te2), dt = R(I.dt), inv = R(I.inv_den[i]);
-  r1 = T((te2 * R(Xn[o + 3 * pl]) - dt * s1 - dt * w1) * inv);
-  r2 = T((te2 * R(Xn[o + 4 * pl]) - dt * s2 - dt * w2) * inv);
+  r1 = T(a1);
+  r2 = T(a2);
 }
 
 // ---------------------------------------------------------------------------
@@ -442,7 +443,8 @@ __global__ void __launch_bounds__(TX* TY) k_explicit(const BatchDev* __restrict_
       axis_fluxes<T, SCHEME, TX, TY, 2, 0u, 1>(gy, uy, split, fy + NY, ew, tid);
     }
     __syncthreads();
-    const T idx = T(I.inv_dx), idy = T(I.inv_dy);
+    const Coef<T>& K = coef<T>(I);
+    const T idx = K.inv_dx, idy = K.inv_dy;
     const int c = G::C00 + ty * BW + tx;
     const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
     T e1 = T(0), e2 = T(0);
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(TX* TY) k_explicit(const BatchDev* __restrict_
       const T g2 = (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * idy;
       const T a1 = su1[c], a2 = su2[c];
       const T f1 = T(0.5) * (a2 * a2 - a1 * a1), f2 = a1 * a2;
-      const T qt = T(0.25) * T(I.tau), te2 = T(I.te2);
+      const T qt = K.qtau, te2 = K.te2;
       e1 = qt * b1 + te2 * g1 - f1;
       e2 = qt * b2 + te2 * g2 - f2;
       T* e = reinterpret_cast<T*>(I.E[j]);
@@ -514,7 +516,8 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     const T* sv2 = s + PL;
     const int nx = I.nx;
     const size_t pl = (size_t)nx * I.ny;
-    const T idx = T(I.inv_dx), idy = T(I.inv_dy);
+    const Coef<T>& K = coef<T>(I);
+    const T idx = K.inv_dx, idy = K.inv_dy;
     for (int k = tid; k < TY * WD; k += TX * TY) {
       const int r = k / WD, cc = k - r * WD;
       sdy[k] = cdiff<T, SCHEME>(sv2 + (G::H + r) * BW + (4 - CH) + cc, BW, idy);
@@ -529,14 +532,15 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     // reading G4), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii precomputed
     const T* Xn = reinterpret_cast<const T*>(I.X);
     const T thn = Xn[o + 2 * pl];
-    T R = -T(I.kappa[i]) * thn;
+    const unsigned mim = b.m_im[i];
+    T R = -K.kappa[i] * thn;
     for (int jj = 1; jj < i; ++jj)
-      if (aim(b, i, jj) != 0.0) R = R + T(I.c_du[i][jj]) * reinterpret_cast<const T*>(I.Du[jj])[o];
-    R = R + T(I.c_dun[i]) * reinterpret_cast<const T*>(I.Du[1])[o];
+      if (has(mim, jj)) R = R + K.c_du[i][jj] * reinterpret_cast<const T*>(I.Du[jj])[o];
+    R = R + K.c_dun[i] * reinterpret_cast<const T*>(I.Du[1])[o];
     for (int jj = 1; jj <= i; ++jj)
-      if (aim(b, i, jj) != 0.0) R = R - T(I.c_db[i][jj]) * (jj == i ? dbi : reinterpret_cast<const T*>(I.DB[jj])[o]);
+      if (has(mim, jj)) R = R - K.c_db[i][jj] * (jj == i ? dbi : reinterpret_cast<const T*>(I.DB[jj])[o]);
     for (int jj = 1; jj < i; ++jj)
-      if (aim(b, i, jj) != 0.0) R = R + T(theta_sign < 0 ? I.c_lth[i][jj] : -I.c_lth[i][jj]) * reinterpret_cast<const T*>(I.Lth[jj])[o];
+      if (has(mim, jj)) R = R + (theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]) * reinterpret_cast<const T*>(I.Lth[jj])[o];
     reinterpret_cast<T*>(I.R)[o] = R;
     if (first_stage) {
       const double tsum = block_sum<double>(double(thn), red, tid, TX * TY);
@@ -563,7 +567,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ 
   T* fy = fx + 2 * NX;                     // [2][NY]: (v2;p1), (v1;p2)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * TX;
   const T ew = T(weno_eps);
-  const double aii = aim(b, i, i);
+  const unsigned mwp = b.m_wp[i], mim = b.m_im[i];
   tile_loop<T, G, TX, TY>(b, pr, stage, bars, tid, [&](const InstDev& I, const TileRef& t, T* s) {
     const T* sth = s;
     const T* sv1 = s + PL;
@@ -571,19 +575,19 @@ __global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ 
     const int nx = I.nx;
     const size_t pl = (size_t)nx * I.ny;
     // dissipation partner of D_LF . B(v^(i)) (reading G6): (1/a_ii) sum_{j<i} (atilde_ij - a_ij) u^(j)
+    const Coef<T>& K = coef<T>(I);
     for (int e = tid; e < G::BW * G::BH; e += TX * TY) {
       T p1 = T(0), p2 = T(0);
       int k = 3;
       for (int jj = 1; jj < i; ++jj) {
-        const double w = aex(b, i, jj) - aim(b, i, jj);
-        if (w != 0.0) {
-          p1 = p1 + T(w) * s[k * PL + e];
-          p2 = p2 + T(w) * s[(k + 1) * PL + e];
+        if (has(mwp, jj)) {
+          p1 = p1 + K.wp[i][jj] * s[k * PL + e];
+          p2 = p2 + K.wp[i][jj] * s[(k + 1) * PL + e];
           k += 2;
         }
       }
-      sp1[e] = p1 * T(I.inv_aii[i]);
-      sp2[e] = p2 * T(I.inv_aii[i]);
+      sp1[e] = p1;
+      sp2[e] = p2;
     }
     __syncthreads();
     {
@@ -596,7 +600,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ 
       axis_fluxes<T, SCHEME, TX, TY, 2, 0u, 1>(gy, uy, split, fy, ew, tid);
     }
     __syncthreads();
-    const T idx = T(I.inv_dx), idy = T(I.inv_dy);
+    const T idx = K.inv_dx, idy = K.inv_dy;
     const int c = G::C00 + ty * BW + tx;
     const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
     const T d1 = (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * idx + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * idy;
@@ -607,44 +611,41 @@ __global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ 
     // step 3
     T s1 = T(0), s2 = T(0);
     for (int jj = 1; jj < i; ++jj) {
-      const double a = aim(b, i, jj);
-      if (a != 0.0) {
+      if (has(mim, jj)) {
         const T* db = reinterpret_cast<const T*>(I.DLFB[jj]);
         const T* gt = reinterpret_cast<const T*>(I.Gth[jj]);
-        s1 = s1 + T(a) * (db[o] + gt[o]);
-        s2 = s2 + T(a) * (db[o + pl] + gt[o + pl]);
+        s1 = s1 + K.aim[i][jj] * (db[o] + gt[o]);
+        s2 = s2 + K.aim[i][jj] * (db[o + pl] + gt[o + pl]);
       }
     }
-    s1 = s1 + T(aii) * (d1 + g1);
-    s2 = s2 + T(aii) * (d2 + g2);
+    s1 = s1 + K.aim[i][i] * (d1 + g1);
+    s2 = s2 + K.aim[i][i] * (d2 + g2);
     const T* Xn = reinterpret_cast<const T*>(I.X);
     T* out = reinterpret_cast<T*>(I.Xs[i]);
-    const T dt = T(I.dt);
+    const T dt = K.dt;
     out[o] = Xn[o] - dt * s1;
     out[o + pl] = Xn[o + pl] - dt * s2;
     reinterpret_cast<T*>(I.Dv[i])[o] = dvi;
     // step 4
-    const double htau = 0.5 * I.tau;
     if (I.relax64) {
-      double sD = 0.0, sQ = 0.0;
+      const Coef<double>& K64 = I.k64;
+      double aq = K64.r_n[i] * double(Xn[o + 5 * pl]);
       for (int jj = 1; jj <= i; ++jj) {
-        const double a = aim(b, i, jj);
-        if (a == 0.0) continue;
+        if (!has(mim, jj)) continue;
         const double dv = (jj == i) ? double(dvi) : double(reinterpret_cast<const T*>(I.Dv[jj])[o]);
-        sD = sD + a * htau * dv;
-        if (jj < i) sQ = sQ + a * double(reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj])[o + 5 * pl]);
+        aq = aq + K64.rq_d[i][jj] * dv;
+        if (jj < i) aq = aq + K64.rv_v[i][jj] * double(reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj])[o + 5 * pl]);
       }
-      out[o + 5 * pl] = T((I.te2 * double(Xn[o + 5 * pl]) - I.dt * (sD + sQ)) * I.inv_den[i]);
+      out[o + 5 * pl] = T(aq);
     } else {
-      T sD = T(0), sQ = T(0);
+      T aq = K.r_n[i] * Xn[o + 5 * pl];
       for (int jj = 1; jj <= i; ++jj) {
-        const double a = aim(b, i, jj);
-        if (a == 0.0) continue;
+        if (!has(mim, jj)) continue;
         const T dv = (jj == i) ? dvi : reinterpret_cast<const T*>(I.Dv[jj])[o];
-        sD = sD + T(a) * T(htau) * dv;
-        if (jj < i) sQ = sQ + T(a) * reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj])[o + 5 * pl];
+        aq = aq + K.rq_d[i][jj] * dv;
+        if (jj < i) aq = aq + K.rv_v[i][jj] * reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj])[o + 5 * pl];
       }
-      out[o + 5 * pl] = (T(I.te2) * Xn[o + 5 * pl] - dt * (sD + sQ)) * T(I.inv_den[i]);
+      out[o + 5 * pl] = aq;
     }
   });
 }

@@ -123,6 +123,59 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
 }
 
 // Fill the derived per-instance constants of a descriptor from its parameters.
+// Stage coefficients of one instance, computed in FP64 and rounded once to T.
+template <typename T>
+inline void fill_coef(const ap_dvm_params& p, const InstDev& d, Coef<T>& k) {
+  k = Coef<T>{};
+  k.dt = T(d.dt);
+  k.te2 = T(d.te2);
+  k.qtau = T(0.25) * T(d.tau);
+  k.htau = T(0.5 * d.tau);
+  k.inv_dx = T(d.inv_dx);
+  k.inv_dy = T(d.inv_dy);
+  for (int i = 1; i <= p.s; ++i)
+    for (int j = 1; j <= p.s; ++j) {
+      k.aex[i][j] = T(p.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]);
+      k.aim[i][j] = T(p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]);
+    }
+  for (int i = 2; i <= p.s; ++i) {
+    const double aii = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+    k.kappa[i] = T(d.kappa[i]);
+    k.r_n[i] = T(d.te2 * d.inv_den[i]);
+    k.c_dun[i] = T(1.0 / (p.dt * aii));
+    for (int j = 1; j <= i; ++j) {
+      const double a = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)];
+      const double ae = p.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)];
+      k.c_du[i][j] = T(a / (p.dt * aii * aii));
+      k.c_db[i][j] = T(a / aii);
+      k.c_lth[i][j] = T(-1.0 * (a / aii));
+      k.wp[i][j] = T((ae - a) * d.inv_aii[i]);
+      k.rv_e[i][j] = T(-p.dt * ae * d.inv_den[i]);
+      k.rv_v[i][j] = T(-p.dt * a * d.inv_den[i]);
+      k.rq_d[i][j] = T(-p.dt * a * (0.5 * d.tau) * d.inv_den[i]);
+    }
+  }
+}
+
+// Tableau of a batch and the nonzero patterns of its rows.
+inline void fill_tableau(const ap_dvm_params& p, BatchDev& b) {
+  for (int k = 0; k < APD_MAXS * APD_MAXS; ++k) {
+    b.A_ex[k] = p.A_ex[k];
+    b.A_im[k] = p.A_im[k];
+  }
+  for (int i = 1; i <= APD_MAXS; ++i) {
+    b.m_ex[i] = b.m_im[i] = b.m_wp[i] = 0u;
+    for (int j = 1; j <= APD_MAXS; ++j) {
+      const double ae = p.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)];
+      const double ai = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)];
+      if (ae != 0.0) b.m_ex[i] |= 1u << j;
+      if (ai != 0.0 && j <= i) b.m_im[i] |= 1u << j;
+      if (ae - ai != 0.0 && j < i) b.m_wp[i] |= 1u << j;
+    }
+  }
+  b.m_ex[0] = b.m_im[0] = b.m_wp[0] = 0u;
+}
+
 inline void fill_constants(const ap_dvm_params& p, InstDev& d) {
   d.dx = p.Lx / p.nx;
   d.dy = p.Ly / p.ny;
@@ -140,17 +193,9 @@ inline void fill_constants(const ap_dvm_params& p, InstDev& d) {
   }
   d.inv_dx = 1.0 / d.dx;
   d.inv_dy = 1.0 / d.dy;
-  for (int i = 2; i <= p.s; ++i) {
-    const double aii = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
-    d.c_dun[i] = 1.0 / (p.dt * aii);
-    d.inv_aii[i] = 1.0 / aii;
-    for (int j = 1; j <= i; ++j) {
-      const double a = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)];
-      d.c_du[i][j] = a / (p.dt * aii * aii);
-      d.c_db[i][j] = a / aii;
-      d.c_lth[i][j] = -1.0 * (a / aii);
-    }
-  }
+  for (int i = 2; i <= p.s; ++i) d.inv_aii[i] = 1.0 / p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+  fill_coef(p, d, d.k64);
+  fill_coef(p, d, d.k32);
   const double ra = 1.0 / (p.rho0 * p.mach);
   d.sc_u = ra;
   d.sc_th = p.eps > 0 ? ra / (2.0 * p.eps) : 0.0;
