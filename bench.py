@@ -156,6 +156,9 @@ def make_solver(n, eps, mach, tau, dt, f32: bool, scheme="WENO5_C4"):
 def time_form(torch, fields, n, eps, mach, tau, dt, f32, steps, warmup, barrier, graph_steps=1):
     s = make_solver(n, eps, mach, tau, dt, f32)
     s.set_equilibrium(*[torch.from_numpy(a).cuda() for a in fields])
+    # tile shape from the autotuner (state saved and restored bit for bit)
+    from paper_2512_19847_gb300 import autotune
+    s.tuned = autotune.tune(s, steps=2, path=None)
     s.set_graph_steps(graph_steps)
     s.step(warmup)
     s.sync_status()
@@ -431,11 +434,12 @@ def main():
             dist.destroy_process_group()
         return
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(n, args.eps, args.mach, args.tau, dt, fields)
+    from paper_2512_19847_gb300.autotune import TILES as autotune_tiles
     line = {
         "metric": METRIC, "value": round(v64, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms64 / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args),
+        "config": dict(config_dict(args), tile_fp64=list(autotune_tiles[s64.tile]), tile_fp32=list(autotune_tiles[s32.tile])),
         "roofline": roof64,
         "cpu_baseline": cpu,
         "e2e": e2e,

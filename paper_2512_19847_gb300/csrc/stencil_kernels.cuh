@@ -201,6 +201,47 @@ __device__ __forceinline__ void w5_nd(const T* P, const T* C, int st, T& num, T&
   }
 }
 
+// FP32: approximate reciprocal (one MUFU operation, PTX rcp.approx.ftz.f32).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// FP32 WENO5 interface flux with packed f32x2 arithmetic: lane x is the
+// left-biased reconstruction of g+ (points m-2..m+2), lane y the mirrored
+// right-biased reconstruction of g- (points m+3..m-1); the arithmetic is that
+// of w5_nd with reciprocal weights.  P, M: g+ and g- at the interface's left
+// cell m; CP, CM: their curvature terms; st: stride between points.
+__device__ __forceinline__ float w5_flux_f32(const float* P, const float* M, const float* CP, const float* CM, int st) {
+  const float2 A = make_float2(P[-2 * st], M[3 * st]);
+  const float2 B = make_float2(P[-st], M[2 * st]);
+  const float2 Cc = make_float2(P[0], M[st]);
+  const float2 D = make_float2(P[st], M[0]);
+  const float2 E = make_float2(P[2 * st], M[-st]);
+  const float2 C0 = make_float2(CP[-st], CM[2 * st]);
+  const float2 C1 = make_float2(CP[0], CM[st]);
+  const float2 C2 = make_float2(CP[st], CM[0]);
+  const float2 l0 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(B, f2(-4.f), A));
+  const float2 l1 = __ffma2_rn(D, f2(-1.f), B);
+  const float2 l2 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(D, f2(-4.f), E));
+  const float2 e0 = __ffma2_rn(__fmul2_rn(l0, f2(3.f)), l0, C0);
+  const float2 e1 = __ffma2_rn(__fmul2_rn(l1, f2(3.f)), l1, C1);
+  const float2 e2 = __ffma2_rn(__fmul2_rn(l2, f2(3.f)), l2, C2);
+  const float2 s0 = __fmul2_rn(e0, e0), s1 = __fmul2_rn(e1, e1), s2 = __fmul2_rn(e2, e2);
+  const float2 r0 = make_float2(rcp_approx(s0.x), rcp_approx(s0.y));
+  const float2 r1 = make_float2(rcp_approx(s1.x), rcp_approx(s1.y));
+  const float2 r2 = make_float2(rcp_approx(s2.x), rcp_approx(s2.y));
+  // candidate polynomials times their linear weights (1/10, 6/10, 3/10)
+  const float2 q0 = __ffma2_rn(Cc, f2(11.f / 60.f), __ffma2_rn(B, f2(-7.f / 60.f), __fmul2_rn(A, f2(1.f / 30.f))));
+  const float2 q1 = __ffma2_rn(D, f2(0.2f), __ffma2_rn(Cc, f2(0.5f), __fmul2_rn(B, f2(-0.1f))));
+  const float2 q2 = __ffma2_rn(E, f2(-0.05f), __ffma2_rn(D, f2(0.25f), __fmul2_rn(Cc, f2(0.1f))));
+  const float2 num = __ffma2_rn(r2, q2, __ffma2_rn(r1, q1, __fmul2_rn(r0, q0)));
+  const float2 den = __ffma2_rn(r2, f2(0.3f), __ffma2_rn(r1, f2(0.6f), __fmul2_rn(r0, f2(0.1f))));
+  return fmaf(num.y, rcp_approx(den.y), num.x * rcp_approx(den.x));
+}
+
 // Interface flux from the left (g+) and right (g-) reconstructions.
 template <typename T>
 __device__ __forceinline__ T combine(T nl, T dl, T nr, T dr) {
@@ -308,10 +349,16 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
     int line, m;
     if_line(k - pr * (NL * NI), line, m);
     const int base = sp_off(line, H - 1 + m);
-    T nl, dl, nr, dr;
-    w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, PS, nl, dl);
-    w5_nd<T>(split + (4 * pr + 1) * LS + base + PS, split + (4 * pr + 3) * LS + base + PS, -PS, nr, dr);
-    out[pr * NL * NI + out_off(line, m)] = combine<T>(nl, dl, nr, dr);
+    if constexpr (std::is_same<T, float>::value) {
+      out[pr * NL * NI + out_off(line, m)] =
+          w5_flux_f32(split + (4 * pr + 0) * LS + base, split + (4 * pr + 1) * LS + base,
+                      split + (4 * pr + 2) * LS + base, split + (4 * pr + 3) * LS + base, PS);
+    } else {
+      T nl, dl, nr, dr;
+      w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, PS, nl, dl);
+      w5_nd<T>(split + (4 * pr + 1) * LS + base + PS, split + (4 * pr + 3) * LS + base + PS, -PS, nr, dr);
+      out[pr * NL * NI + out_off(line, m)] = combine<T>(nl, dl, nr, dr);
+    }
   }
 }
 
@@ -392,7 +439,7 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_explicit(const BatchDev* __restrict__ bp, int j, unsigned need, double weno_eps) {
+__global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const BatchDev* __restrict__ bp, int j, unsigned need, double weno_eps) {
   using G = Geo<T, SCHEME, TX, TY>;
   constexpr int BW = G::BW, PL = G::PL, NX = G::NX, NY = G::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -551,7 +598,7 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_update(const BatchDev* __restrict__ bp, int i, double weno_eps) {
+__global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const BatchDev* __restrict__ bp, int i, double weno_eps) {
   using G = Geo<T, SCHEME, TX, TY>;
   constexpr int BW = G::BW, PL = G::PL, NX = G::NX, NY = G::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
