@@ -75,7 +75,9 @@ enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1 };                   /* precision fo
  *  precision   AP_DVM_FP64 (all in FP64) or AP_DVM_FP32_DEV (FP32 deviation
  *              populations and FP32 transport; FP64 moment sums, division by
  *              rho0*mach, and closed-form relaxation when eps <= 1e-4).
- *  weno_eps    epsilon of the WENO weights (> 0; 1e-6 by default).
+ *  weno_eps    epsilon of the WENO weights (1e-6 by default); at least 1e-30
+ *              (FP64) or 1e-9 (FP32 form), so that the products and
+ *              reciprocals of the smoothness terms stay in range.
  */
 typedef struct {
   int nx, ny;

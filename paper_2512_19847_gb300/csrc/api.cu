@@ -125,7 +125,10 @@ ap_dvm_status validate(const ap_dvm_params* p, char* buf, size_t n) {
   if (p->space_scheme < AP_DVM_LF1_C2 || p->space_scheme > AP_DVM_WENO5_C4) { snprintf(buf, n, "unknown space_scheme"); return AP_DVM_ERR_ARG; }
   if (p->precision != AP_DVM_FP64 && p->precision != AP_DVM_FP32_DEV) { snprintf(buf, n, "unknown precision"); return AP_DVM_ERR_ARG; }
   if (p->precision == AP_DVM_FP32_DEV && !(p->eps > 0)) { snprintf(buf, n, "the FP32 deviation form needs eps > 0 (population view)"); return AP_DVM_ERR_ARG; }
-  if (!(p->weno_eps > 0)) { snprintf(buf, n, "weno_eps must be > 0"); return AP_DVM_ERR_ARG; }
+  if (!(p->weno_eps >= (p->precision == AP_DVM_FP32_DEV ? 1e-9 : 1e-30))) {
+    snprintf(buf, n, "weno_eps must be >= 1e-30 (FP64) or >= 1e-9 (FP32 form)");
+    return AP_DVM_ERR_ARG;
+  }
   const int s = p->s;
   if (s < 2 || s > AP_DVM_MAX_STAGES) { snprintf(buf, n, "s must be in [2, %d]", AP_DVM_MAX_STAGES); return AP_DVM_ERR_TABLEAU; }
   auto ae = [&](int i, int j) { return p->A_ex[i * AP_DVM_MAX_STAGES + j]; };

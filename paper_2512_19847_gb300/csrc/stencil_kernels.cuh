@@ -164,9 +164,10 @@ __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr
 // WENO5 reconstruction from precomputed point data.  P points at the centre
 // point of the stencil, st is the stride along the line (negative for the
 // right-biased reconstruction, which mirrors the left-biased one).  C holds
-// 13 (f_{m-1} - 2 f_m + f_{m+1})^2 + 12 eps_W per point: the Jiang-Shu
-// indicators and eps_W are both scaled by 12, which leaves the normalised
-// weights unchanged.  Returns numerator and denominator of
+// (13/3) (f_{m-1} - 2 f_m + f_{m+1})^2 + 4 eps_W per point: the Jiang-Shu
+// indicators and eps_W are both scaled by 4, which leaves the normalised
+// weights unchanged and makes (eps_W + beta_k) one FMA from C.  Returns
+// numerator and denominator of
 //   sum_k d_k p_k / s_k  /  sum_k d_k / s_k,   s_k = (eps_W + beta_k)^2,
 // multiplied through by s_0 s_1 s_2 (FP64) so that no division is needed here.
 template <typename T>
@@ -181,9 +182,9 @@ __device__ __forceinline__ void w5_nd(const T* P, const T* C, int st, T& num, T&
   const T l0 = a - T(4) * b + T(3) * c;
   const T l1 = b - d;
   const T l2 = T(3) * c - T(4) * d + e;
-  const T e0 = C[-st] + T(3) * l0 * l0;
-  const T e1 = C[0] + T(3) * l1 * l1;
-  const T e2 = C[st] + T(3) * l2 * l2;
+  const T e0 = C[-st] + l0 * l0;
+  const T e1 = C[0] + l1 * l1;
+  const T e2 = C[st] + l2 * l2;
   // candidate polynomials times their linear weights (1/10, 6/10, 3/10)
   const T q0 = a * T(1.0 / 30.0) - b * T(7.0 / 60.0) + c * T(11.0 / 60.0);
   const T q1 = -b * T(0.1) + c * T(0.5) + d * T(0.2);
@@ -226,9 +227,9 @@ __device__ __forceinline__ float w5_flux_f32(const float* P, const float* M, con
   const float2 l0 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(B, f2(-4.f), A));
   const float2 l1 = __ffma2_rn(D, f2(-1.f), B);
   const float2 l2 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(D, f2(-4.f), E));
-  const float2 e0 = __ffma2_rn(__fmul2_rn(l0, f2(3.f)), l0, C0);
-  const float2 e1 = __ffma2_rn(__fmul2_rn(l1, f2(3.f)), l1, C1);
-  const float2 e2 = __ffma2_rn(__fmul2_rn(l2, f2(3.f)), l2, C2);
+  const float2 e0 = __ffma2_rn(l0, l0, C0);
+  const float2 e1 = __ffma2_rn(l1, l1, C1);
+  const float2 e2 = __ffma2_rn(l2, l2, C2);
   const float2 s0 = __fmul2_rn(e0, e0), s1 = __fmul2_rn(e1, e1), s2 = __fmul2_rn(e2, e2);
   const float2 r0 = make_float2(rcp_approx(s0.x), rcp_approx(s0.y));
   const float2 r1 = make_float2(rcp_approx(s1.x), rcp_approx(s1.y));
@@ -242,10 +243,21 @@ __device__ __forceinline__ float w5_flux_f32(const float* P, const float* M, con
   return fmaf(num.y, rcp_approx(den.y), num.x * rcp_approx(den.x));
 }
 
+// FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined
+// by two Newton-Raphson steps r <- r + r (1 - d r), each doubling the number of
+// correct bits; the result is within a few units in the last place of 1/d.
+__device__ __forceinline__ double rcp_newton(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
 // Interface flux from the left (g+) and right (g-) reconstructions.
 template <typename T>
 __device__ __forceinline__ T combine(T nl, T dl, T nr, T dr) {
-  if (std::is_same<T, double>::value) return (nl * dr + nr * dl) / (dl * dr);
+  if (std::is_same<T, double>::value) return (nl * dr + nr * dl) * rcp_newton(double(dl * dr));
   return nl * frcp(dl) + nr * frcp(dr);
 }
 
@@ -313,8 +325,9 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
     const T* gp = pick<NP>(g, pr);
     const T gv = ((NEG >> pr) & 1u) ? -gp[o] : gp[o];
     const T uv = pick<NP>(U, pr)[o];
-    split[(4 * pr + 0) * LS + r] = T(0.5) * (gv + uv);
-    split[(4 * pr + 1) * LS + r] = T(0.5) * (gv - uv);
+    const T hg = T(0.5) * gv;
+    split[(4 * pr + 0) * LS + r] = hg + T(0.5) * uv;
+    split[(4 * pr + 1) * LS + r] = hg - T(0.5) * uv;
   }
   __syncthreads();
   if (SCHEME == WENO3_C4) {
@@ -330,8 +343,8 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
     }
     return;
   }
-  // 2. curvature part of the smoothness indicators, scaled by 12, plus 12 eps_W
-  const T ew12 = T(12) * ew;
+  // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W
+  const T ew4 = T(4) * ew;
   for (int k = tid; k < 2 * NP * LS; k += NT) {
     const int q = k / LS, r = k - q * LS;
     int line, pt;
@@ -340,7 +353,7 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
     const int pr = q >> 1, pm = q & 1;
     const T* f = split + (4 * pr + pm) * LS + r;
     const T cv = f[-PS] - T(2) * f[0] + f[PS];
-    split[(4 * pr + 2 + pm) * LS + r] = T(13) * cv * cv + ew12;
+    split[(4 * pr + 2 + pm) * LS + r] = T(13.0 / 3.0) * cv * cv + ew4;
   }
   __syncthreads();
   // 3. interface fluxes: left-biased reconstruction of g+ centred at m, right-biased of g- centred at m+1
