@@ -28,48 +28,124 @@ template <> __device__ __forceinline__ const float2* twiddles<float>(const Batch
 
 __device__ __forceinline__ int brev(int k, int ln) { return (int)(__brev((unsigned)k) >> (32 - ln)); }
 
+// Complex helpers.  mul_j(z, inv) multiplies by -i (forward) or +i (inverse):
+// the twiddle W_{4h}^h of the second stage of a radix-2^2 step.
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C cmul_tw(C w, C b, bool inv) {   // w (conjugated when inv) times b
+  C r;
+  if (inv) { r.x = w.x * b.x + w.y * b.y; r.y = w.x * b.y - w.y * b.x; }
+  else { r.x = w.x * b.x - w.y * b.y; r.y = w.x * b.y + w.y * b.x; }
+  return r;
+}
+template <typename C>
+__device__ __forceinline__ C mul_j(C a, bool inv) {
+  C r;
+  if (inv) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+
 // ntr transforms of length n = 2^ln held back to back in x[], input in
 // bit-reversed order, output natural.  Twiddle W_m^p = tw[p * nmax/m].
+// Stages are taken two at a time (radix-2^2): each thread loads four
+// elements p0 + {0, h, 2h, 3h}, applies stage s (half h, twiddle W_{2h}^pos)
+// and stage s+1 (half 2h, twiddles W_{4h}^pos and W_{4h}^pos * W_{4h}^h) in
+// registers, and stores them; the first pair of stages has only trivial twiddles.
 template <typename T>
 __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int ntr,
                                         const typename Cplx<T>::type* __restrict__ tw, int lnmax,
                                         bool inv, int tid, int nthr) {
-  const int n = 1 << ln, nb = ntr * (n >> 1);
-  for (int s = 1; s <= ln; ++s) {
-    const int half = 1 << (s - 1), sh = lnmax - s;
+  using C = typename Cplx<T>::type;
+  const int n = 1 << ln;
+  int s = 1;
+  for (; s + 1 <= ln; s += 2) {
+    const int h = 1 << (s - 1), nq = n >> 2, nb = ntr * nq;
+    for (int k = tid; k < nb; k += nthr) {
+      const int t = k >> (ln - 2), bi = k & (nq - 1);
+      const int pos = bi & (h - 1), grp = bi >> (s - 1);
+      const int p0 = t * n + grp * 4 * h + pos;
+      C x0 = x[p0], x1 = x[p0 + h], x2 = x[p0 + 2 * h], x3 = x[p0 + 3 * h];
+      if (s > 1) {
+        const C w1 = tw[pos << (lnmax - s)];
+        x1 = cmul_tw(w1, x1, inv);
+        x3 = cmul_tw(w1, x3, inv);
+      }
+      const C a0 = cadd(x0, x1), a1 = csub(x0, x1);
+      C a2 = cadd(x2, x3), a3 = csub(x2, x3);
+      if (s > 1) {
+        const C w2 = tw[pos << (lnmax - s - 1)];
+        a2 = cmul_tw(w2, a2, inv);
+        a3 = cmul_tw(w2, a3, inv);
+      }
+      a3 = mul_j(a3, inv);
+      x[p0] = cadd(a0, a2);
+      x[p0 + 2 * h] = csub(a0, a2);
+      x[p0 + h] = cadd(a1, a3);
+      x[p0 + 3 * h] = csub(a1, a3);
+    }
+    __syncthreads();
+  }
+  if (s == ln) {   // one radix-2 stage left (odd ln)
+    const int half = 1 << (s - 1), sh = lnmax - s, nb = ntr * (n >> 1);
     for (int k = tid; k < nb; k += nthr) {
       const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
       const int pos = bi & (half - 1), grp = bi >> (s - 1);
       const int i0 = t * n + grp * 2 * half + pos, i1 = i0 + half;
-      const auto w = tw[pos << sh];
-      const T wr = w.x, wi = inv ? -w.y : w.y;
-      const auto a = x[i0], bb = x[i1];
-      const T tr = wr * bb.x - wi * bb.y, ti = wr * bb.y + wi * bb.x;
-      x[i1].x = a.x - tr; x[i1].y = a.y - ti;
-      x[i0].x = a.x + tr; x[i0].y = a.y + ti;
+      const C a = x[i0], tb = cmul_tw(tw[pos << sh], x[i1], inv);
+      x[i0] = cadd(a, tb);
+      x[i1] = csub(a, tb);
     }
     __syncthreads();
   }
 }
 
-// Natural-order input, bit-reversed output.
+// Natural-order input, bit-reversed output (decimation in frequency), two
+// stages at a time as in fft_dit: stage s (half 2h) then stage s-1 (half h).
 template <typename T>
 __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int ntr,
                                         const typename Cplx<T>::type* __restrict__ tw, int lnmax,
                                         bool inv, int tid, int nthr) {
-  const int n = 1 << ln, nb = ntr * (n >> 1);
-  for (int s = ln; s >= 1; --s) {
-    const int half = 1 << (s - 1), sh = lnmax - s;
+  using C = typename Cplx<T>::type;
+  const int n = 1 << ln;
+  int s = ln;
+  for (; s >= 2; s -= 2) {
+    const int h = 1 << (s - 2), nq = n >> 2, nb = ntr * nq;
     for (int k = tid; k < nb; k += nthr) {
-      const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
-      const int pos = bi & (half - 1), grp = bi >> (s - 1);
-      const int i0 = t * n + grp * 2 * half + pos, i1 = i0 + half;
-      const auto w = tw[pos << sh];
-      const T wr = w.x, wi = inv ? -w.y : w.y;
-      const auto a = x[i0], bb = x[i1];
-      const T dr = a.x - bb.x, di = a.y - bb.y;
-      x[i0].x = a.x + bb.x; x[i0].y = a.y + bb.y;
-      x[i1].x = wr * dr - wi * di; x[i1].y = wr * di + wi * dr;
+      const int t = k >> (ln - 2), bi = k & (nq - 1);
+      const int pos = bi & (h - 1), grp = bi >> (s - 2);
+      const int p0 = t * n + grp * 4 * h + pos;
+      const C x0 = x[p0], x1 = x[p0 + h], x2 = x[p0 + 2 * h], x3 = x[p0 + 3 * h];
+      const C b0 = cadd(x0, x2), b1 = cadd(x1, x3);
+      C b2 = csub(x0, x2), b3 = csub(x1, x3);
+      if (s > 2) {
+        const C w2 = tw[pos << (lnmax - s)];
+        b2 = cmul_tw(w2, b2, inv);
+        b3 = cmul_tw(w2, b3, inv);
+      }
+      b3 = mul_j(b3, inv);
+      C y1 = csub(b0, b1), y3 = csub(b2, b3);
+      if (s > 2) {
+        const C w1 = tw[pos << (lnmax - s + 1)];
+        y1 = cmul_tw(w1, y1, inv);
+        y3 = cmul_tw(w1, y3, inv);
+      }
+      x[p0] = cadd(b0, b1);
+      x[p0 + h] = y1;
+      x[p0 + 2 * h] = cadd(b2, b3);
+      x[p0 + 3 * h] = y3;
+    }
+    __syncthreads();
+  }
+  if (s == 1) {   // last radix-2 stage (odd ln): all twiddles are 1
+    const int nb = ntr * (n >> 1);
+    for (int k = tid; k < nb; k += nthr) {
+      const int i0 = 2 * k, i1 = i0 + 1;
+      const C a = x[i0], b = x[i1];
+      x[i0] = cadd(a, b);
+      x[i1] = csub(a, b);
     }
     __syncthreads();
   }
