@@ -39,7 +39,8 @@ struct Geo {
   static constexpr int C00 = H * BW + 4;                // interior cell (0, 0)
   static constexpr int NX = TY * (TX + 1), NY = (TY + 1) * TX;
   static constexpr int LS = (TY * W > HH * TX) ? TY * W : HH * TX;
-  static constexpr int SPLIT_PER_PAIR = SCHEME == LF1_C2 ? 0 : 4 * LS;
+  // split scratch: none for LF1, and none for FP32 WENO5 (register runs)
+  static constexpr int SPLIT_PER_PAIR = (SCHEME == LF1_C2 || (SCHEME == WENO5_C4 && sizeof(T) == 4)) ? 0 : 4 * LS;
   // shared memory besides the double-buffered planes, and its element count
   static constexpr int EXPLICIT_EXTRA = 3 * SPLIT_PER_PAIR + 3 * NX + 3 * NY;
   static constexpr int UPDATE_EXTRA = 2 * PL + 2 * SPLIT_PER_PAIR + 2 * NX + 2 * NY;
@@ -215,15 +216,8 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // right-biased reconstruction of g- (points m+3..m-1); the arithmetic is that
 // of w5_nd with reciprocal weights.  P, M: g+ and g- at the interface's left
 // cell m; CP, CM: their curvature terms; st: stride between points.
-__device__ __forceinline__ float w5_flux_f32(const float* P, const float* M, const float* CP, const float* CM, int st) {
-  const float2 A = make_float2(P[-2 * st], M[3 * st]);
-  const float2 B = make_float2(P[-st], M[2 * st]);
-  const float2 Cc = make_float2(P[0], M[st]);
-  const float2 D = make_float2(P[st], M[0]);
-  const float2 E = make_float2(P[2 * st], M[-st]);
-  const float2 C0 = make_float2(CP[-st], CM[2 * st]);
-  const float2 C1 = make_float2(CP[0], CM[st]);
-  const float2 C2 = make_float2(CP[st], CM[0]);
+__device__ __forceinline__ float w5_flux_f32_vals(float2 A, float2 B, float2 Cc, float2 D, float2 E, float2 C0, float2 C1,
+                                                  float2 C2) {
   const float2 l0 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(B, f2(-4.f), A));
   const float2 l1 = __ffma2_rn(D, f2(-1.f), B);
   const float2 l2 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(D, f2(-4.f), E));
@@ -241,6 +235,12 @@ __device__ __forceinline__ float w5_flux_f32(const float* P, const float* M, con
   const float2 num = __ffma2_rn(r2, q2, __ffma2_rn(r1, q1, __fmul2_rn(r0, q0)));
   const float2 den = __ffma2_rn(r2, f2(0.3f), __ffma2_rn(r1, f2(0.6f), __fmul2_rn(r0, f2(0.1f))));
   return fmaf(num.y, rcp_approx(den.y), num.x * rcp_approx(den.x));
+}
+
+__device__ __forceinline__ float w5_flux_f32(const float* P, const float* M, const float* CP, const float* CM, int st) {
+  return w5_flux_f32_vals(make_float2(P[-2 * st], M[3 * st]), make_float2(P[-st], M[2 * st]), make_float2(P[0], M[st]),
+                          make_float2(P[st], M[0]), make_float2(P[2 * st], M[-st]), make_float2(CP[-st], CM[2 * st]),
+                          make_float2(CP[0], CM[st]), make_float2(CP[st], CM[0]));
 }
 
 // FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined
@@ -375,6 +375,88 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
   }
 }
 
+// FP32 WENO5 fluxes of both axes without shared scratch: a work item is a run
+// of KR = 3 consecutive interfaces of one line of one pair.  Its thread loads
+// the KR + 5 points the run needs, splits them (g+, g-) and forms their
+// curvature terms in registers as (g+, g-) lane pairs, then evaluates the
+// interfaces with the packed arithmetic of w5_flux_f32.  Items of the x axis
+// come first, then those of the y axis; consecutive threads take consecutive
+// lines.  Points past the end of a line are clamped: they only feed
+// interfaces of the last run that are not stored.
+template <int TX, int TY, int NP, int AX>
+__device__ __forceinline__ void w5_runs_item(const float* g, const float* U, bool neg, float* out, float ew4, int line,
+                                             int run) {
+  using G = Geo<float, WENO5_C4, TX, TY>;
+  constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = 3, NPT = KR + 5;
+  constexpr int NL = AX == 0 ? TY : TX;
+  constexpr int LL = AX == 0 ? G::W : G::HH;
+  constexpr int NI = AX == 0 ? TX + 1 : TY + 1;
+  const int m0 = run * KR;
+  float2 P[NPT];   // (g+, g-) at points m0 .. m0 + KR + 4 of the line (interface m has centre point m + 2)
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int pt = min(m0 + j, LL - 1);
+    const int o = AX == 0 ? (H + line) * SW + XO + pt : pt * SW + XO + H + line;
+    const float gv = neg ? -g[o] : g[o];
+    P[j] = __ffma2_rn(make_float2(0.5f, -0.5f), f2(U[o]), f2(0.5f * gv));
+  }
+  float2 C[NPT];   // curvature terms (13/3) (f_{j-1} - 2 f_j + f_{j+1})^2 + 4 eps_W, j = 1 .. KR + 3
+#pragma unroll
+  for (int j = 1; j <= KR + 3; ++j) {
+    const float2 cv = __fadd2_rn(__ffma2_rn(P[j], f2(-2.f), P[j - 1]), P[j + 1]);
+    C[j] = __ffma2_rn(__fmul2_rn(cv, f2(13.f / 3.f)), cv, f2(ew4));
+  }
+#pragma unroll
+  for (int i = 0; i < KR; ++i) {
+    const int m = m0 + i;
+    if (m >= NI) break;
+    const float2 A = make_float2(P[i].x, P[i + 5].y);
+    const float2 B = make_float2(P[i + 1].x, P[i + 4].y);
+    const float2 Cc = make_float2(P[i + 2].x, P[i + 3].y);
+    const float2 D = make_float2(P[i + 3].x, P[i + 2].y);
+    const float2 E = make_float2(P[i + 4].x, P[i + 1].y);
+    const float2 C0 = make_float2(C[i + 1].x, C[i + 4].y);
+    const float2 C1 = make_float2(C[i + 2].x, C[i + 3].y);
+    const float2 C2 = make_float2(C[i + 3].x, C[i + 2].y);
+    out[AX == 0 ? line * NI + m : m * TX + line] = w5_flux_f32_vals(A, B, Cc, D, E, C0, C1, C2);
+  }
+  (void)NL;
+}
+
+template <int TX, int TY, int NP, unsigned NEGX, unsigned NEGY>
+__device__ __forceinline__ void w5_runs_both_axes(const float* const* gx, const float* const* ux, const float* const* gy,
+                                                  const float* const* uy, float* fx, float* fy, float ew, int tid) {
+  constexpr int KR = 3, NT = TX * TY;
+  constexpr int RX = (TX + 1 + KR - 1) / KR, RY = (TY + 1 + KR - 1) / KR;
+  constexpr int IX = NP * TY * RX, IY = NP * TX * RY;
+  constexpr int NXI = TY * (TX + 1), NYI = (TY + 1) * TX;
+  const float ew4 = 4.f * ew;
+  for (int k = tid; k < IX + IY; k += NT) {
+    if (k < IX) {
+      const int pr = k / (TY * RX), r = k - pr * (TY * RX), run = r / TY, line = r - run * TY;
+      w5_runs_item<TX, TY, NP, 0>(pick<NP>(gx, pr), pick<NP>(ux, pr), (NEGX >> pr) & 1u, fx + pr * NXI, ew4, line, run);
+    } else {
+      const int kk = k - IX;
+      const int pr = kk / (TX * RY), r = kk - pr * (TX * RY), run = r / TX, line = r - run * TX;
+      w5_runs_item<TX, TY, NP, 1>(pick<NP>(gy, pr), pick<NP>(uy, pr), (NEGY >> pr) & 1u, fy + pr * NYI, ew4, line, run);
+    }
+  }
+}
+
+// Fluxes of both axes for NP pairs: x-axis pairs (gx, ux) into fx [NP][TY][TX+1],
+// y-axis pairs (gy, uy) into fy [NP][TY+1][TX].
+template <typename T, int SCHEME, int TX, int TY, int NP, unsigned NEGX, unsigned NEGY>
+__device__ __forceinline__ void both_axes(const T* const* gx, const T* const* ux, const T* const* gy, const T* const* uy,
+                                          T* split, T* fx, T* fy, T ew, int tid) {
+  if constexpr (std::is_same<T, float>::value && SCHEME == WENO5_C4) {
+    w5_runs_both_axes<TX, TY, NP, NEGX, NEGY>(gx, ux, gy, uy, fx, fy, ew, tid);
+  } else {
+    axis_fluxes<T, SCHEME, TX, TY, NP, NEGX, 0>(gx, ux, split, fx, ew, tid);
+    __syncthreads();
+    axis_fluxes<T, SCHEME, TX, TY, NP, NEGY, 1>(gy, uy, split, fy, ew, tid);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red, int tid, int nthr) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -480,27 +562,21 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const 
     if (needE && needB) {
       const T* gx[3] = {sq, sv1, sv2};
       const T* ux[3] = {sv1, su1, su2};
-      axis_fluxes<T, SCHEME, TX, TY, 3, 2u, 0>(gx, ux, split, fx, ew, tid);
-      __syncthreads();
       const T* gy[3] = {sq, sv2, sv1};
       const T* uy[3] = {sv2, su1, su2};
-      axis_fluxes<T, SCHEME, TX, TY, 3, 0u, 1>(gy, uy, split, fy, ew, tid);
+      both_axes<T, SCHEME, TX, TY, 3, 2u, 0u>(gx, ux, gy, uy, split, fx, fy, ew, tid);
     } else if (needE) {
       const T* gx[1] = {sq};
       const T* ux[1] = {sv1};
-      axis_fluxes<T, SCHEME, TX, TY, 1, 0u, 0>(gx, ux, split, fx, ew, tid);
-      __syncthreads();
       const T* gy[1] = {sq};
       const T* uy[1] = {sv2};
-      axis_fluxes<T, SCHEME, TX, TY, 1, 0u, 1>(gy, uy, split, fy, ew, tid);
+      both_axes<T, SCHEME, TX, TY, 1, 0u, 0u>(gx, ux, gy, uy, split, fx, fy, ew, tid);
     } else if (needB) {
       const T* gx[2] = {sv1, sv2};
       const T* ux[2] = {su1, su2};
-      axis_fluxes<T, SCHEME, TX, TY, 2, 1u, 0>(gx, ux, split, fx + NX, ew, tid);
-      __syncthreads();
       const T* gy[2] = {sv2, sv1};
       const T* uy[2] = {su1, su2};
-      axis_fluxes<T, SCHEME, TX, TY, 2, 0u, 1>(gy, uy, split, fy + NY, ew, tid);
+      both_axes<T, SCHEME, TX, TY, 2, 1u, 0u>(gx, ux, gy, uy, split, fx + NX, fy + NY, ew, tid);
     }
     __syncthreads();
     const Coef<T>& K = coef<T>(I);
@@ -653,11 +729,9 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
     {
       const T* gx[2] = {sv1, sv2};
       const T* ux[2] = {sp1, sp2};
-      axis_fluxes<T, SCHEME, TX, TY, 2, 1u, 0>(gx, ux, split, fx, ew, tid);
-      __syncthreads();
       const T* gy[2] = {sv2, sv1};
       const T* uy[2] = {sp1, sp2};
-      axis_fluxes<T, SCHEME, TX, TY, 2, 0u, 1>(gy, uy, split, fy, ew, tid);
+      both_axes<T, SCHEME, TX, TY, 2, 1u, 0u>(gx, ux, gy, uy, split, fx, fy, ew, tid);
     }
     __syncthreads();
     const T idx = K.inv_dx, idy = K.inv_dy;
