@@ -54,10 +54,11 @@ def step_flops_per_cell(scheme: str, n: int) -> dict:
     c1 = 6 if scheme != "LF1_C2" else 2           # first central difference
     c2 = 8 if scheme != "LF1_C2" else 4           # second central difference
     lg = math.log2(n)
-    explicit = (2 * c1 + 1) * 2 + 2 * FP + 13 + (2 * c1 + 1)          # stage 1: E, D0.u^n
-    explicit += (2 * c1 + 1) * 2 + 2 * FP + 13 + (2 * c1 + 1) + (2 * c2 + 1) + 2 * c1 + 4 * FP + 2   # stage 2: all
+    # stage 1: E, D0.u^n and the closed-form v^(2); stage 2: all derived operators and v^(3)
+    explicit = (2 * c1 + 1) * 2 + 2 * FP + 13 + (2 * c1 + 1) + 14
+    explicit += (2 * c1 + 1) * 2 + 2 * FP + 13 + (2 * c1 + 1) + (2 * c2 + 1) + 2 * c1 + 4 * FP + 2 + 22
     dbf = 2 * c2 + 2 * c1 + 3
-    rhs = (14 + dbf + 5 + 1) + (22 + dbf + 11)
+    rhs = (dbf + 5 + 1) + (dbf + 11)
     # radix-2 butterflies (10 flops) of the two real-row, column and inverse-row passes, two solves
     rows = 2 * (2.5 * lg + 2)
     cols = 2 * (5 * lg + 2.5)
@@ -71,15 +72,17 @@ def step_bytes_per_cell(f32: bool) -> dict:
     every plane a kernel must read or write, once."""
     e = 4 if f32 else 8
     planes = {
-        # stage 1: read u, v, q (5), write E, D0.u (3); stage 2: read 6, write E, D0.u, D_Delta theta, D0 theta, D_LF.B(v) (8)
-        "explicit": (5 + 3) + (6 + 8),
-        # stage 2: read v^n, E^(1), theta^n, D0.u^n (6), write v, DB, R (4);
-        # stage 3: read v^n, E^(1), E^(2), v^(2), theta^n, D0.u^n, D0.u^(2), DB^(2), D_Delta theta^(2) (13), write 4
-        "rhs": (6 + 4) + (13 + 4),
+        # stage 1: read u, v, q (5), write E, D0.u, v^(2) (5);
+        # stage 2: read X^(2) (6), E^(1), v^n (4), write E, D0.u, D_Delta theta, D0 theta, D_LF.B(v), v^(3) (10)
+        "explicit": (5 + 5) + (10 + 10),
+        # stage 2: read v^(2), theta^n, D0.u^n (4), write DB, R (2);
+        # stage 3: read v^(3), theta^n, D0.u^n, D0.u^(2), DB^(2), D_Delta theta^(2) (7), write 2
+        "rhs": (4 + 2) + (7 + 2),
         # each pass reads and writes one plane-equivalent (real plane or half spectrum), two solves
         "fft_rows_fwd": 4, "fft_cols": 4, "fft_rows_inv": 4,
-        # stage 2: read v, u^n, theta, q^n (6), write u, q, D0.v (4); stage 3: read 14, write 4
-        "update": (6 + 4) + (14 + 4),
+        # stage 2: read theta, v, u^(1), u^n, q^n (8), write u, q, D0.v (4);
+        # stage 3: read theta, v, u^(1), u^(2), u^n, q^n, D_LF.B(v)^(2), D0 theta^(2), D0.v^(2), q^(2) (16), write 4
+        "update": (8 + 4) + (16 + 4),
         "finish": 12, "unpack": 12 if f32 else 0}
     return {k: v * e for k, v in planes.items()}
 
@@ -185,6 +188,37 @@ def profile_form(s, steps):
     return prof
 
 
+TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic_tg2048.json")
+
+
+def csrc_digest() -> str:
+    """SHA-256 over the CUDA sources (names and contents): DRAM counters taken
+    with ncu are only reported while the kernels are unchanged."""
+    import hashlib
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2512_19847_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".inc")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kind: str, f32: bool, n: int):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kind` from the
+    committed ncu capture, or None when it was taken on other kernels or sizes."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("n") != n or rec.get("csrc_sha256") != csrc_digest():
+        return None
+    v = rec.get("fp32" if f32 else "fp64", {}).get(kind)
+    return None if v is None else float(v)
+
+
 def roofline(prof: dict, steps: int, cells: int, f32: bool, scheme: str, n: int, peaks: dict):
     flops = step_flops_per_cell(scheme, n)
     byts = step_bytes_per_cell(f32)
@@ -196,16 +230,16 @@ def roofline(prof: dict, steps: int, cells: int, f32: bool, scheme: str, n: int,
         achieved = alg / (per_launch_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs") or 6800.0
         return kind, {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                      "frac": round(achieved / peak, 4), "traffic": None, "kernel": kind,
+                      "frac": round(achieved / peak, 4), "traffic": measured_traffic(kind, True, n), "kernel": kind,
                       "algorithmic_bytes_per_launch": alg, "ms_per_launch": round(per_launch_ms, 4),
                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
     alg = flops[kind] * cells / launches_per_step                # flops per launch
     achieved = alg / (per_launch_ms * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS
     return kind, {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-                  "frac": round(achieved / peak, 4), "traffic": None, "kernel": kind,
+                  "frac": round(achieved / peak, 4), "traffic": measured_traffic(kind, False, n), "kernel": kind,
                   "algorithmic_flops_per_launch": alg, "ms_per_launch": round(per_launch_ms, 4),
-                  "peak_source": "FP64 FMA pipe, measured: 0.505e12 DFMA/s x 2 (DESIGN.md)"}
+                  "peak_source": "FP64 FMA pipe of this GPU model, measured with an FMA-chain microbenchmark: 0.505e12 DFMA/s x 2"}
 
 
 # measured on this machine's GB300 (FMA-chain microbenchmark, 152 SMs x 8 blocks x 256 threads)
@@ -288,11 +322,12 @@ def run_served(torch, n_requests=48, budget=120e9, load=0.8, v_ref=None, seed=7)
             cache[(n, s)] = (u1, u2, p, W.stable_dt(u1, u2, 2 * math.pi / n, 0.05))
         return cache[(n, s)]
     jobs = serve.make_jobs(reqs, tmpl, fields)
-    srv = serve.Server(tmpl, capacity=n_requests, hbm_budget=budget, chunk=10, tile=0)
+    tile = 2                                             # 16x8: the autotuner's pick for the FP32 form at 2048^2 and for the batched mix
+    srv = serve.Server(tmpl, capacity=n_requests, hbm_budget=budget, chunk=10, tile=tile)
     mixed = srv.run(jobs).summary()
     alone_jobs = serve.make_jobs(reqs, tmpl, fields)
-    alone = serve.run_alone(alone_jobs, tile=0).summary()
-    mixed.update({"rate_hz": round(rate, 3), "hbm_budget_gb": budget / 1e9, "chunk_steps": 10, "tile": 0})
+    alone = serve.run_alone(alone_jobs, tile=tile).summary()
+    mixed.update({"rate_hz": round(rate, 3), "hbm_budget_gb": budget / 1e9, "chunk_steps": 10, "tile": tile})
     return {"continuous_batching": mixed, "alone_per_solve": alone}
 
 

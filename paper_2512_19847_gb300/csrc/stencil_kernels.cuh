@@ -209,39 +209,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-
-// FP32 WENO5 interface flux with packed f32x2 arithmetic: lane x is the
-// left-biased reconstruction of g+ (points m-2..m+2), lane y the mirrored
-// right-biased reconstruction of g- (points m+3..m-1); the arithmetic is that
-// of w5_nd with reciprocal weights.  P, M: g+ and g- at the interface's left
-// cell m; CP, CM: their curvature terms; st: stride between points.
-__device__ __forceinline__ float w5_flux_f32_vals(float2 A, float2 B, float2 Cc, float2 D, float2 E, float2 C0, float2 C1,
-                                                  float2 C2) {
-  const float2 l0 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(B, f2(-4.f), A));
-  const float2 l1 = __ffma2_rn(D, f2(-1.f), B);
-  const float2 l2 = __ffma2_rn(Cc, f2(3.f), __ffma2_rn(D, f2(-4.f), E));
-  const float2 e0 = __ffma2_rn(l0, l0, C0);
-  const float2 e1 = __ffma2_rn(l1, l1, C1);
-  const float2 e2 = __ffma2_rn(l2, l2, C2);
-  const float2 s0 = __fmul2_rn(e0, e0), s1 = __fmul2_rn(e1, e1), s2 = __fmul2_rn(e2, e2);
-  const float2 r0 = make_float2(rcp_approx(s0.x), rcp_approx(s0.y));
-  const float2 r1 = make_float2(rcp_approx(s1.x), rcp_approx(s1.y));
-  const float2 r2 = make_float2(rcp_approx(s2.x), rcp_approx(s2.y));
-  // candidate polynomials times their linear weights (1/10, 6/10, 3/10)
-  const float2 q0 = __ffma2_rn(Cc, f2(11.f / 60.f), __ffma2_rn(B, f2(-7.f / 60.f), __fmul2_rn(A, f2(1.f / 30.f))));
-  const float2 q1 = __ffma2_rn(D, f2(0.2f), __ffma2_rn(Cc, f2(0.5f), __fmul2_rn(B, f2(-0.1f))));
-  const float2 q2 = __ffma2_rn(E, f2(-0.05f), __ffma2_rn(D, f2(0.25f), __fmul2_rn(Cc, f2(0.1f))));
-  const float2 num = __ffma2_rn(r2, q2, __ffma2_rn(r1, q1, __fmul2_rn(r0, q0)));
-  const float2 den = __ffma2_rn(r2, f2(0.3f), __ffma2_rn(r1, f2(0.6f), __fmul2_rn(r0, f2(0.1f))));
-  return fmaf(num.y, rcp_approx(den.y), num.x * rcp_approx(den.x));
-}
-
-__device__ __forceinline__ float w5_flux_f32(const float* P, const float* M, const float* CP, const float* CM, int st) {
-  return w5_flux_f32_vals(make_float2(P[-2 * st], M[3 * st]), make_float2(P[-st], M[2 * st]), make_float2(P[0], M[st]),
-                          make_float2(P[st], M[0]), make_float2(P[2 * st], M[-st]), make_float2(CP[-st], CM[2 * st]),
-                          make_float2(CP[0], CM[st]), make_float2(CP[st], CM[0]));
-}
 
 // FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined
 // by two Newton-Raphson steps r <- r + r (1 - d r), each doubling the number of
@@ -362,65 +329,74 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
     int line, m;
     if_line(k - pr * (NL * NI), line, m);
     const int base = sp_off(line, H - 1 + m);
-    if constexpr (std::is_same<T, float>::value) {
-      out[pr * NL * NI + out_off(line, m)] =
-          w5_flux_f32(split + (4 * pr + 0) * LS + base, split + (4 * pr + 1) * LS + base,
-                      split + (4 * pr + 2) * LS + base, split + (4 * pr + 3) * LS + base, PS);
-    } else {
-      T nl, dl, nr, dr;
-      w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, PS, nl, dl);
-      w5_nd<T>(split + (4 * pr + 1) * LS + base + PS, split + (4 * pr + 3) * LS + base + PS, -PS, nr, dr);
-      out[pr * NL * NI + out_off(line, m)] = combine<T>(nl, dl, nr, dr);
-    }
+    T nl, dl, nr, dr;
+    w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, PS, nl, dl);
+    w5_nd<T>(split + (4 * pr + 1) * LS + base + PS, split + (4 * pr + 3) * LS + base + PS, -PS, nr, dr);
+    out[pr * NL * NI + out_off(line, m)] = combine<T>(nl, dl, nr, dr);
   }
 }
 
 // FP32 WENO5 fluxes of both axes without shared scratch: a work item is a run
 // of KR = 3 consecutive interfaces of one line of one pair.  Its thread loads
 // the KR + 5 points the run needs, splits them (g+, g-) and forms their
-// curvature terms in registers as (g+, g-) lane pairs, then evaluates the
-// interfaces with the packed arithmetic of w5_flux_f32.  Items of the x axis
-// come first, then those of the y axis; consecutive threads take consecutive
-// lines.  Points past the end of a line are clamped: they only feed
-// interfaces of the last run that are not stored.
+// curvature terms in registers, then evaluates the interfaces.  Items of the
+// x axis come first, then those of the y axis; consecutive threads take
+// consecutive lines.  Points past the end of a line are clamped: they only
+// feed interfaces of the last run that are not stored.  (Scalar FP32 with
+// immediate constants issues fewer instructions here than paired f32x2
+// arithmetic, whose operands and constants must first be packed.)
+
+// Scalar FP32 WENO5 reconstruction from register values (the arithmetic of
+// w5_nd with reciprocal weights); returns num / den.
+__device__ __forceinline__ float w5_rec_f32(float a, float b, float c, float d, float e, float C0, float C1, float C2) {
+  const float l0 = fmaf(3.f, c, fmaf(-4.f, b, a));
+  const float l1 = b - d;
+  const float l2 = fmaf(3.f, c, fmaf(-4.f, d, e));
+  const float e0 = fmaf(l0, l0, C0), e1 = fmaf(l1, l1, C1), e2 = fmaf(l2, l2, C2);
+  const float r0 = rcp_approx(e0 * e0), r1 = rcp_approx(e1 * e1), r2 = rcp_approx(e2 * e2);
+  // candidate polynomials times their linear weights (1/10, 6/10, 3/10)
+  const float q0 = fmaf(11.f / 60.f, c, fmaf(-7.f / 60.f, b, a * (1.f / 30.f)));
+  const float q1 = fmaf(0.2f, d, fmaf(0.5f, c, b * -0.1f));
+  const float q2 = fmaf(-0.05f, e, fmaf(0.25f, d, c * 0.1f));
+  const float num = fmaf(r2, q2, fmaf(r1, q1, r0 * q0));
+  const float den = fmaf(0.3f, r2, fmaf(0.6f, r1, 0.1f * r0));
+  return num * rcp_approx(den);
+}
+
 template <int TX, int TY, int NP, int AX>
 __device__ __forceinline__ void w5_runs_item(const float* g, const float* U, bool neg, float* out, float ew4, int line,
                                              int run) {
   using G = Geo<float, WENO5_C4, TX, TY>;
   constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = 3, NPT = KR + 5;
-  constexpr int NL = AX == 0 ? TY : TX;
   constexpr int LL = AX == 0 ? G::W : G::HH;
   constexpr int NI = AX == 0 ? TX + 1 : TY + 1;
   const int m0 = run * KR;
-  float2 P[NPT];   // (g+, g-) at points m0 .. m0 + KR + 4 of the line (interface m has centre point m + 2)
+  float Pp[NPT], Pm[NPT];   // g+ and g- at points m0 .. m0 + KR + 4 of the line (interface m has centre point m + 2)
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
     const int pt = min(m0 + j, LL - 1);
     const int o = AX == 0 ? (H + line) * SW + XO + pt : pt * SW + XO + H + line;
-    const float gv = neg ? -g[o] : g[o];
-    P[j] = __ffma2_rn(make_float2(0.5f, -0.5f), f2(U[o]), f2(0.5f * gv));
+    const float hg = 0.5f * (neg ? -g[o] : g[o]), hu = 0.5f * U[o];
+    Pp[j] = hg + hu;
+    Pm[j] = hg - hu;
   }
-  float2 C[NPT];   // curvature terms (13/3) (f_{j-1} - 2 f_j + f_{j+1})^2 + 4 eps_W, j = 1 .. KR + 3
+  float Cp[NPT], Cm[NPT];   // (13/3) (f_{j-1} - 2 f_j + f_{j+1})^2 + 4 eps_W
 #pragma unroll
   for (int j = 1; j <= KR + 3; ++j) {
-    const float2 cv = __fadd2_rn(__ffma2_rn(P[j], f2(-2.f), P[j - 1]), P[j + 1]);
-    C[j] = __ffma2_rn(__fmul2_rn(cv, f2(13.f / 3.f)), cv, f2(ew4));
+    const float cp = fmaf(-2.f, Pp[j], Pp[j - 1]) + Pp[j + 1];
+    const float cm = fmaf(-2.f, Pm[j], Pm[j - 1]) + Pm[j + 1];
+    Cp[j] = fmaf(13.f / 3.f * cp, cp, ew4);
+    Cm[j] = fmaf(13.f / 3.f * cm, cm, ew4);
   }
 #pragma unroll
   for (int i = 0; i < KR; ++i) {
     const int m = m0 + i;
     if (m >= NI) break;
-    const float2 A = make_float2(P[i].x, P[i + 5].y);
-    const float2 B = make_float2(P[i + 1].x, P[i + 4].y);
-    const float2 Cc = make_float2(P[i + 2].x, P[i + 3].y);
-    const float2 D = make_float2(P[i + 3].x, P[i + 2].y);
-    const float2 E = make_float2(P[i + 4].x, P[i + 1].y);
-    const float2 C0 = make_float2(C[i + 1].x, C[i + 4].y);
-    const float2 C1 = make_float2(C[i + 2].x, C[i + 3].y);
-    const float2 C2 = make_float2(C[i + 3].x, C[i + 2].y);
-    out[AX == 0 ? line * NI + m : m * TX + line] = w5_flux_f32_vals(A, B, Cc, D, E, C0, C1, C2);
+    // left-biased reconstruction of g+ (points m..m+4 of the run), mirrored right-biased of g- (points m+5..m+1)
+    const float fl = w5_rec_f32(Pp[i], Pp[i + 1], Pp[i + 2], Pp[i + 3], Pp[i + 4], Cp[i + 1], Cp[i + 2], Cp[i + 3]);
+    const float fr = w5_rec_f32(Pm[i + 5], Pm[i + 4], Pm[i + 3], Pm[i + 2], Pm[i + 1], Cm[i + 4], Cm[i + 3], Cm[i + 2]);
+    out[AX == 0 ? line * NI + m : m * TX + line] = fl + fr;
   }
-  (void)NL;
 }
 
 template <int TX, int TY, int NP, unsigned NEGX, unsigned NEGY>

@@ -29,7 +29,7 @@ def cell_centres(nx: int, ny: int, Lx: float = TWO_PI, Ly: float = TWO_PI):
 
 
 def taylor_green(nx: int, ny: int | None = None, t: float = 0.0, nu: float = 0.0):
-    """Taylor-Green vortex on [0, 2pi)^2 (the BASELINE workload, not from the paper).
+    """Taylor-Green vortex on [0, 2pi)^2 (the headline benchmark workload; not one of the paper's experiments).
 
     u = (sin x cos y, -cos x sin y) e^{-2 nu t},  p = (cos 2x + cos 2y)/4 e^{-4 nu t}.
     This (u, p) solves the incompressible Navier-Stokes equations with
@@ -77,7 +77,7 @@ def _spectral_derivatives(f_hat: np.ndarray, L: float):
 
 
 def random_divfree(n: int, seed: int, kmax: int = 16, normalise: bool = True):
-    """Seeded random divergence-free field (BASELINE precision / batched workloads).
+    """Seeded random divergence-free field (precision-form and batched workloads).
 
     Stream function psi = sum_{0<|k|<=kmax} |k|^-2 cos(k.x + phi_k), phases
     phi_k ~ U[0, 2pi) drawn from numpy's PCG64 with ``seed`` for every
@@ -153,7 +153,7 @@ def random_moment_state(nx: int, ny: int, seed: int, amp: float = 1.0, modes: in
 
 
 def cfl_dt(u1: np.ndarray, u2: np.ndarray, dx: float, cfl: float = 0.5) -> float:
-    """dt = cfl * dx / max|u| (the BASELINE CFL rule; the paper does not state dt)."""
+    """dt = cfl * dx / max|u| (the benchmark CFL rule; the paper does not state dt)."""
     umax = float(np.max(np.hypot(u1, u2)))
     return cfl * dx / max(umax, 1e-300)
 
