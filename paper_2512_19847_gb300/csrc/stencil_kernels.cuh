@@ -370,13 +370,18 @@ __device__ __forceinline__ void w5_runs_item(const float* g, const float* U, boo
   constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = 3, NPT = KR + 5;
   constexpr int LL = AX == 0 ? G::W : G::HH;
   constexpr int NI = AX == 0 ? TX + 1 : TY + 1;
+  // the last run reads up to point RUNS*KR + 4: inside the staged row for x (BW = TX + 8
+  // columns), else clamped to the last row of the line
+  constexpr int RUNS = (NI + KR - 1) / KR;
+  constexpr bool CLAMP = RUNS * KR + 4 > (AX == 0 ? TX + 6 : LL - 1);
   const int m0 = run * KR;
+  const float hs = neg ? -0.5f : 0.5f;
   float Pp[NPT], Pm[NPT];   // g+ and g- at points m0 .. m0 + KR + 4 of the line (interface m has centre point m + 2)
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
-    const int pt = min(m0 + j, LL - 1);
+    const int pt = CLAMP ? min(m0 + j, LL - 1) : m0 + j;
     const int o = AX == 0 ? (H + line) * SW + XO + pt : pt * SW + XO + H + line;
-    const float hg = 0.5f * (neg ? -g[o] : g[o]), hu = 0.5f * U[o];
+    const float hg = hs * g[o], hu = 0.5f * U[o];
     Pp[j] = hg + hu;
     Pm[j] = hg - hu;
   }
@@ -391,11 +396,10 @@ __device__ __forceinline__ void w5_runs_item(const float* g, const float* U, boo
 #pragma unroll
   for (int i = 0; i < KR; ++i) {
     const int m = m0 + i;
-    if (m >= NI) break;
     // left-biased reconstruction of g+ (points m..m+4 of the run), mirrored right-biased of g- (points m+5..m+1)
     const float fl = w5_rec_f32(Pp[i], Pp[i + 1], Pp[i + 2], Pp[i + 3], Pp[i + 4], Cp[i + 1], Cp[i + 2], Cp[i + 3]);
     const float fr = w5_rec_f32(Pm[i + 5], Pm[i + 4], Pm[i + 3], Pm[i + 2], Pm[i + 1], Cm[i + 4], Cm[i + 3], Cm[i + 2]);
-    out[AX == 0 ? line * NI + m : m * TX + line] = fl + fr;
+    if (NI % KR == 0 || m < NI) out[AX == 0 ? line * NI + m : m * TX + line] = fl + fr;
   }
 }
 
