@@ -64,7 +64,7 @@ def step_flops_per_cell(scheme: str, n: int) -> dict:
     cols = 2 * (5 * lg + 2.5)
     update = (6 + 4 * FP + 2 + 2 * c1 + (2 * c1 + 1) + 6 + 4 + 8) + (10 + 4 * FP + 2 + 2 * c1 + (2 * c1 + 1) + 12 + 4 + 13)
     return {"explicit": explicit, "rhs": rhs, "fft_rows_fwd": rows, "fft_cols": cols,
-            "fft_rows_inv": rows, "update": update, "finish": 0, "unpack": 0}
+            "fft_rows_inv": rows, "update": update, "finish": 0}
 
 
 def step_bytes_per_cell(f32: bool) -> dict:
@@ -83,7 +83,8 @@ def step_bytes_per_cell(f32: bool) -> dict:
         # stage 2: read theta, v, u^(1), u^n, q^n (8), write u, q, D0.v (4);
         # stage 3: read theta, v, u^(1), u^(2), u^n, q^n, D_LF.B(v)^(2), D0 theta^(2), D0.v^(2), q^(2) (16), write 4
         "update": (8 + 4) + (16 + 4),
-        "finish": 12, "unpack": 12 if f32 else 0}
+        # FP64: X^(s) -> X; FP32: read X^(s), write the populations and the next step's FP64-summed moments
+        "finish": 18 if f32 else 12}
     return {k: v * e for k, v in planes.items()}
 
 

@@ -169,7 +169,8 @@ int ap_dvm_launches_per_step(const ap_dvm_handle* h);
 ap_dvm_status ap_dvm_profile_enable(ap_dvm_handle* h, int enable);
 /* Synchronise and read per-kernel totals since the last reset: up to max
  * entries of kernel name (static string), total milliseconds and launch
- * count.  Returns the number of kernel kinds (8), or -1 on error. */
+ * count.  Returns the number of kernel kinds (7: explicit, rhs, fft_rows_fwd,
+ * fft_cols, fft_rows_inv, update, finish), or -1 on error. */
 int ap_dvm_profile_read(ap_dvm_handle* h, const char** names, double* total_ms, long* launches, int max);
 
 /* End-to-end call on HOST buffers: copy 6 moment planes h_in (double) to the

@@ -322,7 +322,8 @@ ap_dvm_status flush(ap_dvm_handle* h) {
   return AP_DVM_OK;
 }
 
-const char* const kKernelNames[8] = {"explicit", "rhs", "fft_rows_fwd", "fft_cols", "fft_rows_inv", "update", "finish", "unpack"};
+constexpr int kNumKinds = 7;
+const char* const kKernelNames[kNumKinds] = {"explicit", "rhs", "fft_rows_fwd", "fft_cols", "fft_rows_inv", "update", "finish"};
 
 ap_dvm_status launch(ap_dvm_handle* h, cudaStream_t stream, const void* fn, int grid, dim3 block, size_t smem, void** args,
                      int kind = -1) {
@@ -652,19 +653,19 @@ ap_dvm_status ap_dvm_profile_enable(ap_dvm_handle* h, int enable) {
   ap_dvm_status st = profile_collect(h);
   if (st) return st;
   h->profile = enable != 0;
-  for (int k = 0; k < 8; ++k) { h->prof_ms[k] = 0; h->prof_count[k] = 0; }
+  for (int k = 0; k < kNumKinds; ++k) { h->prof_ms[k] = 0; h->prof_count[k] = 0; }
   return AP_DVM_OK;
 }
 
 int ap_dvm_profile_read(ap_dvm_handle* h, const char** names, double* total_ms, long* launches, int max) {
   if (!h || profile_collect(h) != AP_DVM_OK) return -1;
-  const int n = std::min(max, 8);
+  const int n = std::min(max, kNumKinds);
   for (int k = 0; k < n; ++k) {
     if (names) names[k] = kKernelNames[k];
     if (total_ms) total_ms[k] = h->prof_ms[k];
     if (launches) launches[k] = h->prof_count[k];
   }
-  return 8;
+  return kNumKinds;
 }
 
 ap_dvm_status ap_dvm_set_graph_steps(ap_dvm_handle* h, int k) {
@@ -691,7 +692,7 @@ int ap_dvm_get_tile(const ap_dvm_handle* h) { return h ? h->tile : -1; }
 int ap_dvm_launches_per_step(const ap_dvm_handle* h) {
   if (!h) return 0;
   const ap_dvm_params& t = h->tmpl;
-  return (h->f32 ? 1 : 0) + 6 * (t.s - 1) + 1;
+  return 6 * (t.s - 1) + 1;
 }
 
 ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage, int nsteps) {

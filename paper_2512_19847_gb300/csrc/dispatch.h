@@ -21,7 +21,6 @@ struct StencilSet {
 
 struct MiscSet {
   const void* k_finish;    // per tile shape
-  const void* k_unpack;    // FP32 form only
   const void* k_rows_fwd;
   const void* k_cols;
   const void* k_rows_inv;

@@ -54,6 +54,20 @@ __device__ __forceinline__ void mom_to_pop(const R* m, R eps, R rho0, R amp, R* 
   dF[2] = a * (S3 + D3); dF[5] = a * (S3 - D3);
 }
 
+// FP32 form: store the deviation populations dF (the persistent state) and
+// the moments the next step starts from, summed from those FP32 values in
+// FP64 with the division by rho0 A (rounded once into the FP32 planes X).
+__device__ __forceinline__ void store_f32_state(const InstDev& I, size_t o, size_t pl, const float* d) {
+  double dd[6], m[6];
+  for (int k = 0; k < 6; ++k) {
+    I.dF[o + k * pl] = d[k];
+    dd[k] = double(d[k]);
+  }
+  pop_to_mom(dd, I, m);
+  float* X = reinterpret_cast<float*>(I.X);
+  for (int k = 0; k < 6; ++k) X[o + k * pl] = float(m[k]);
+}
+
 // ---- per-instance conversions (one instance, grid-stride over cells)
 
 // mode 0: moments (double) -> state;  mode 1: equilibrium from (u1, u2, p);
@@ -77,18 +91,24 @@ __global__ void k_set_state(InstDev I, const double* __restrict__ a, const doubl
       double d[6];
       for (int k = 0; k < 6; ++k) d[k] = a[o + k * pl];
       if (f32form) {
-        for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = float(d[k]);
+        float df[6];
+        for (int k = 0; k < 6; ++k) df[k] = float(d[k]);
+        store_f32_state(I, o, pl, df);
         continue;
       }
       pop_to_mom(d, I, m);
     } else {
-      for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = f32[o + k * pl];
+      float df[6];
+      for (int k = 0; k < 6; ++k) df[k] = f32[o + k * pl];
+      store_f32_state(I, o, pl, df);
       continue;
     }
     if (f32form) {
       double d[6];
+      float df[6];
       mom_to_pop<double>(m, I.eps, I.rho0, I.amp, d);
-      for (int k = 0; k < 6; ++k) I.dF[o + k * pl] = float(d[k]);
+      for (int k = 0; k < 6; ++k) df[k] = float(d[k]);
+      store_f32_state(I, o, pl, df);
     } else {
       T* X = reinterpret_cast<T*>(I.X);
       for (int k = 0; k < 6; ++k) X[o + k * pl] = T(m[k]);
@@ -131,7 +151,9 @@ __global__ void k_get_state(InstDev I, double* __restrict__ out, double* __restr
 // ---- per-step batched kernels over the tile list (one thread per cell)
 
 // FP64 form: X^(s) -> X (GSA: the last stage is the new state), with a
-// finiteness check.  FP32 form: pack X^(s) into the FP32 deviation populations.
+// finiteness check.  FP32 form: pack X^(s) into the FP32 deviation
+// populations and store the moments of those populations (store_f32_state)
+// as the next step's X.
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ bp, int f32form) {
   const BatchDev& b = *bp;
@@ -150,11 +172,8 @@ __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ 
       float m[6], d[6];
       for (int k = 0; k < 6; ++k) m[k] = float(Y[o + k * pl]);
       mom_to_pop<float>(m, float(I.eps), float(I.rho0), float(I.amp), d);
-      for (int k = 0; k < 6; ++k) {
-        const float v = d[k];
-        bad |= !isfinite(v);
-        I.dF[o + k * pl] = v;
-      }
+      for (int k = 0; k < 6; ++k) bad |= !isfinite(d[k]);
+      store_f32_state(I, o, pl, d);
     } else {
       T* X = reinterpret_cast<T*>(I.X);
       for (int k = 0; k < 6; ++k) {
@@ -164,27 +183,6 @@ __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ 
       }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(b.err, 1u);
-  }
-}
-
-// FP32 form, start of a step: moments of the FP32 populations in FP64
-// (sums and the division by rho0 A), rounded once into the FP32 planes X.
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_unpack(const BatchDev* __restrict__ bp) {
-  const BatchDev& b = *bp;
-  const int ntiles = b.counts[0];
-  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    const int k_inst = find_inst(b.tile_start, b.counts[3], it);
-    const InstDev& I = b.inst[k_inst];
-    const int tile = it - b.tile_start[k_inst];
-    const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
-    const size_t pl = (size_t)I.nx * I.ny;
-    const size_t o = (size_t)(tyi * TY + threadIdx.y) * I.nx + (txi * TX + threadIdx.x);
-    double d[6], m[6];
-    for (int k = 0; k < 6; ++k) d[k] = double(I.dF[o + k * pl]);
-    pop_to_mom(d, I, m);
-    float* X = reinterpret_cast<float*>(I.X);
-    for (int k = 0; k < 6; ++k) X[o + k * pl] = float(m[k]);
   }
 }
 

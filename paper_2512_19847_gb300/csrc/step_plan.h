@@ -14,7 +14,7 @@
 
 namespace apd {
 
-enum KernelKind { KK_EXPLICIT, KK_RHS, KK_ROWS_FWD, KK_COLS, KK_ROWS_INV, KK_UPDATE, KK_FINISH, KK_UNPACK };
+enum KernelKind { KK_EXPLICIT, KK_RHS, KK_ROWS_FWD, KK_COLS, KK_ROWS_INV, KK_UPDATE, KK_FINISH };
 
 struct StepKernels {
   StencilSet ks;
@@ -84,10 +84,6 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
   int st;
   auto AEX = [&](int i, int j) { return t.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
   auto AIM = [&](int i, int j) { return t.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
-  if (f32) {
-    void* a[] = {&bp};
-    if ((st = launch(K.km.k_unpack, K.g_finish, blk, 0, a, KK_UNPACK))) return st;
-  }
   for (int i = 2; i <= s; ++i) {
     int j = i - 1;
     unsigned need = 32u;                                   // v^(i), step 1 of stage i
