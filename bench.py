@@ -264,11 +264,14 @@ def cpu_baseline(n, eps, mach, tau, dt, fields, nsteps=1):
 
 def run_batched(torch, count=256, steps=200, seed=2512):
     """Batched form: `count` seeded uneven instances (side uniform in
-    {64,128,256,512}, eps log-uniform [1e-6,1], Ma log-uniform [1e-3,1e-1],
+    {64,128,256,512}, eps log-uniform [1e-6,0.5], Ma log-uniform [1e-3,1e-1],
     random divergence-free fields, tau = 0.05), FP32 deviation storage, tile
     chosen by the autotuner, all `steps` steps replayed as one CUDA graph."""
     from paper_2512_19847_gb300 import api, autotune, tableaux, workloads as W
-    draws = W.batched_draws(count, seed=seed, steps=steps)
+    # eps up to 0.5: at eps ~ 1 with O(1) velocities the 512^2 random fields blow up at a
+    # time that does not depend on dt (a property of the discrete model there, not of
+    # the time step); long random-field runs take 0.8 of the CFL / viscous bounds
+    draws = W.batched_draws(count, seed=seed, steps=steps, eps_range=(1e-6, 0.5))
     tmpl = api.default_params(512, 512, eps=1e-2, dt=1e-3, tau=0.05, tableau=tableaux.gsa2(), precision=api.FP32_DEV)
     b = api.Batch(tmpl, capacity=count)
     cells = 0
@@ -277,7 +280,7 @@ def run_batched(torch, count=256, steps=200, seed=2512):
         prm = tmpl.copy()
         prm.nx = prm.ny = d.n
         prm.eps, prm.mach = d.eps, d.mach
-        prm.dt = W.stable_dt(u1, u2, 2 * math.pi / d.n, prm.tau)
+        prm.dt = W.stable_dt(u1, u2, 2 * math.pi / d.n, prm.tau, cfl=0.4, visc=0.32)
         b.attach(k, prm)
         b.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, p)], slot=k)
         cells += d.n * d.n
@@ -320,7 +323,7 @@ def run_served(torch, n_requests=48, budget=120e9, load=0.8, v_ref=None, seed=7)
     def fields(n, s):
         if (n, s) not in cache:
             u1, u2, p = W.random_divfree(n, s)
-            cache[(n, s)] = (u1, u2, p, W.stable_dt(u1, u2, 2 * math.pi / n, 0.05))
+            cache[(n, s)] = (u1, u2, p, W.stable_dt(u1, u2, 2 * math.pi / n, 0.05, cfl=0.4, visc=0.32))
         return cache[(n, s)]
     jobs = serve.make_jobs(reqs, tmpl, fields)
     tile = 2                                             # 16x8: the autotuner's pick for the FP32 form at 2048^2 and for the batched mix
@@ -463,8 +466,16 @@ def main():
     e2e = {"value": round(world * cells * e2e_steps / el / 1e6, 3), "unit": UNIT,
            "h2d_bytes_per_step": 6 * cells * 8, "d2h_bytes_per_step": 6 * cells * 8}
 
-    batched = None if args.no_batched else run_batched(torch)
-    served = None if args.no_served else run_served(torch, v_ref=(batched or {}).get("value", v32))
+    def leg(fn, *a, **kw):
+        # a failing secondary leg is reported in the line instead of losing the line
+        try:
+            return fn(*a, **kw)
+        except Exception as e:            # noqa: BLE001
+            torch.cuda.synchronize()
+            return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+    batched = None if args.no_batched else leg(run_batched, torch)
+    served = None if args.no_served else leg(run_served, torch, v_ref=(batched or {}).get("value", v32))
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
