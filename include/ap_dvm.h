@@ -147,6 +147,17 @@ ap_dvm_status ap_dvm_get_populations(ap_dvm_handle* h, int slot, void* d_dF6, in
  * velocity u1, u2 and pressure p = theta - |u|^2/2 (Sec. 3.1, theta = p + |u|^2/2). */
 ap_dvm_status ap_dvm_moments(ap_dvm_handle* h, int slot, double* d_rho, double* d_u1, double* d_u2, double* d_p);
 
+/* Flow diagnostics of the state of slot (Sec. 4: the divergence history of
+ * Figs. 2-3 and the vorticity of Tables 1-2), with the central difference D_0
+ * of the solve's scheme (2nd order for AP_DVM_LF1_C2, 4th order otherwise):
+ *   out3[0] = max |D_0 . u|,  out3[1] = (sum (D_0 . u)^2 dx dy)^(1/2),
+ *   out3[2] = (1/2) sum omega^2 dx dy,  omega = D_0x u2 - D_0y u1.
+ * d_vorticity (device, nullable) receives omega as nx*ny doubles.  out3 is a
+ * host array of 3 doubles.  Synchronises the stream; the slot's right-hand-side
+ * plane serves as scratch, so call it between steps, not while a graph of
+ * steps is being captured. */
+ap_dvm_status ap_dvm_diagnostics(ap_dvm_handle* h, int slot, double* d_vorticity, double* out3);
+
 /* ---- time stepping ------------------------------------------------------------ */
 
 /* Advance every attached solve by nsteps IMEX steps (Algorithm 1; the GSA
@@ -157,7 +168,7 @@ ap_dvm_status ap_dvm_step(ap_dvm_handle* h, int nsteps);
 /* Use a captured CUDA graph of k steps for ap_dvm_step (k = 0: direct launches). */
 ap_dvm_status ap_dvm_set_graph_steps(ap_dvm_handle* h, int k);
 /* Tile shape of the stencil kernels: 0 = 32x8, 1 = 32x4, 2 = 16x8, 3 = 8x8,
- * 4 = 64x4, -1 = automatic.  Every attached grid must be at least the tile. */
+ * 4 = 64x4, 5 = 32x16, -1 = automatic.  Every attached grid must be at least the tile. */
 ap_dvm_status ap_dvm_set_tile(ap_dvm_handle* h, int tile);
 int ap_dvm_get_tile(const ap_dvm_handle* h);
 /* Kernel launches enqueued by one ap_dvm_step(h, 1). */

@@ -199,6 +199,23 @@ def div_c(w1, w2, p: Params):
     return dx_c(w1, p) + dy_c(w2, p)
 
 
+def vorticity(u1, u2, p: Params):
+    """omega = D_0x u2 - D_0y u1, the central vorticity of the Sec. 4 figures and
+    Tables 1-2 (reading G11), with the scheme's central difference."""
+    return dx_c(u2, p) - dy_c(u1, p)
+
+
+def diagnostics(X, p: Params) -> dict:
+    """Flow diagnostics of Sec. 4: max |D_0 . u| (the divergence history of
+    Figs. 2-3), its area-weighted L2 norm (sum (D_0 . u)^2 dx dy)^(1/2), the
+    enstrophy (1/2) sum omega^2 dx dy, and the vorticity plane."""
+    d = div_c(X[0], X[1], p)
+    w = vorticity(X[0], X[1], p)
+    area = p.dx * p.dy
+    return {"div_max": float(np.max(np.abs(d))), "div_l2": float(math.sqrt(np.sum(d * d) * area)),
+            "enstrophy": float(0.5 * np.sum(w * w) * area), "vorticity": w}
+
+
 def d0sq_B(v1, v2, p: Params):
     """D_0^2 : B(v) = -D_xx v1 + 2 D_xy v2 + D_yy v1 (Sec. 3.2)."""
     if p.operators == "consistent":

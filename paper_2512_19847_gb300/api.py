@@ -94,6 +94,7 @@ def lib():
         "ap_dvm_get_state": (i32, [H, i32, vp]),
         "ap_dvm_get_populations": (i32, [H, i32, vp, i32]),
         "ap_dvm_moments": (i32, [H, i32, vp, vp, vp, vp]),
+        "ap_dvm_diagnostics": (i32, [H, i32, vp, ctypes.POINTER(f64)]),
         "ap_dvm_step": (i32, [H, i32]),
         "ap_dvm_set_graph_steps": (i32, [H, i32]),
         "ap_dvm_set_tile": (i32, [H, i32]),
@@ -200,6 +201,17 @@ class _Handle:
         out = torch.empty((4, *self._shape(slot)), dtype=torch.float64, device=self.device)
         self._check(lib().ap_dvm_moments(self._h, slot, *[_ptr(out[k]) for k in range(4)]))
         return out[0], out[1], out[2], out[3]
+
+    def diagnostics(self, slot: int = 0, vorticity: bool = False) -> dict:
+        """Sec. 4 diagnostics of the current state: max |D_0 . u|, its area-weighted
+        L2 norm, the enstrophy and (optionally) the vorticity plane (float64 CUDA tensor)."""
+        out = (ctypes.c_double * 3)()
+        w = torch.empty(self._shape(slot), dtype=torch.float64, device=self.device) if vorticity else None
+        self._check(lib().ap_dvm_diagnostics(self._h, slot, _ptr(w), out))
+        d = {"div_max": out[0], "div_l2": out[1], "enstrophy": out[2]}
+        if w is not None:
+            d["vorticity"] = w
+        return d
 
     # ---- stepping
     def step(self, nsteps: int = 1):

@@ -592,6 +592,36 @@ static ap_dvm_status get_state_impl(ap_dvm_handle* h, int slot, double* out, flo
   return launch(h, h->stream, h->km.k_get_state, grid_for_cells((size_t)s->p.nx * s->p.ny), dim3(256), 0, args);
 }
 
+ap_dvm_status ap_dvm_diagnostics(ap_dvm_handle* h, int slot, double* d_vorticity, double* out3) {
+  if (!out3) return h ? fail(h, AP_DVM_ERR_ARG, "null output") : AP_DVM_ERR_ARG;
+  Slot* s = slot_of(h, slot);
+  if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
+  ap_dvm_status st = prepare_kernels(h);
+  if (st) return st;
+  InstDev d = s->dev;
+  const size_t cells = (size_t)s->p.nx * s->p.ny;
+  const int grid = (int)std::min<size_t>((cells + 255) / 256, 256);
+  // block partials in the slot's right-hand-side plane (free between steps; >= 3 * grid doubles)
+  double* part = reinterpret_cast<double*>(d.R);
+  int c4 = s->p.space_scheme != AP_DVM_LF1_C2;
+  void* args[] = {&d, &c4, &part, &d_vorticity};
+  if ((st = launch(h, h->stream, h->km.k_diagnostics, grid, dim3(256), 0, args))) return st;
+  std::vector<double> hp(3 * (size_t)grid);
+  CUDA_TRY(h, cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  double dmax = 0.0, d2 = 0.0, w2 = 0.0;
+  for (int b = 0; b < grid; ++b) {
+    dmax = std::max(dmax, hp[3 * b]);
+    d2 += hp[3 * b + 1];
+    w2 += hp[3 * b + 2];
+  }
+  const double area = d.dx * d.dy;
+  out3[0] = dmax;
+  out3[1] = std::sqrt(d2 * area);
+  out3[2] = 0.5 * w2 * area;
+  return AP_DVM_OK;
+}
+
 ap_dvm_status ap_dvm_set_state(ap_dvm_handle* h, int slot, const double* d_moments6) {
   if (!d_moments6) return h ? fail(h, AP_DVM_ERR_ARG, "null state pointer") : AP_DVM_ERR_ARG;
   return set_state_impl(h, slot, d_moments6, nullptr, nullptr, nullptr, 0);

@@ -26,6 +26,7 @@ struct MiscSet {
   const void* k_rows_inv;
   const void* k_set_state;
   const void* k_get_state;
+  const void* k_diagnostics;
 };
 
 StencilSet stencil_f64_lf1(int tile);

@@ -148,6 +148,56 @@ __global__ void k_get_state(InstDev I, double* __restrict__ out, double* __restr
   }
 }
 
+// Flow diagnostics of Sec. 4 (the divergence history of Figs. 2-3, the
+// vorticity of Tables 1-2) for one instance: per block, max |D_0 . u| and the
+// sums of (D_0 . u)^2 and omega^2 over a grid-stride range of cells, with
+// omega = D_0x u2 - D_0y u1 and the scheme's central difference (c4: 4th
+// order, else 2nd); written to part[3 * block + {0, 1, 2}].  vort (nullable)
+// receives the vorticity plane.
+template <typename T>
+__global__ void __launch_bounds__(256) k_diagnostics(InstDev I, int c4, double* __restrict__ part,
+                                                     double* __restrict__ vort) {
+  const int nx = I.nx, mx = nx - 1, my = I.ny - 1, lnx = I.lnx;
+  const size_t pl = (size_t)nx * I.ny;
+  const T* u1 = reinterpret_cast<const T*>(I.X);
+  const T* u2 = u1 + pl;
+  auto at = [&](const T* f, int i, int j) { return double(f[(size_t)(j & my) * nx + (i & mx)]); };
+  auto d0x = [&](const T* f, int i, int j) {
+    if (c4) return (-at(f, i + 2, j) + 8.0 * at(f, i + 1, j) - 8.0 * at(f, i - 1, j) + at(f, i - 2, j)) / (12.0 * I.dx);
+    return (at(f, i + 1, j) - at(f, i - 1, j)) / (2.0 * I.dx);
+  };
+  auto d0y = [&](const T* f, int i, int j) {
+    if (c4) return (-at(f, i, j + 2) + 8.0 * at(f, i, j + 1) - 8.0 * at(f, i, j - 1) + at(f, i, j - 2)) / (12.0 * I.dy);
+    return (at(f, i, j + 1) - at(f, i, j - 1)) / (2.0 * I.dy);
+  };
+  double dmax = 0.0, d2 = 0.0, w2 = 0.0;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < pl; o += (size_t)gridDim.x * blockDim.x) {
+    const int i = int(o & (size_t)mx), j = int(o >> lnx);
+    const double d = d0x(u1, i, j) + d0y(u2, i, j);
+    const double w = d0x(u2, i, j) - d0y(u1, i, j);
+    dmax = fmax(dmax, fabs(d));
+    d2 += d * d;
+    w2 += w * w;
+    if (vort) vort[o] = w;
+  }
+  __shared__ double red[3][8];
+  for (int off = 16; off > 0; off >>= 1) {
+    dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, off));
+    d2 += __shfl_down_sync(0xffffffffu, d2, off);
+    w2 += __shfl_down_sync(0xffffffffu, w2, off);
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][warp] = dmax; red[1][warp] = d2; red[2][warp] = w2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a = fmax(a, red[0][k]); b += red[1][k]; c += red[2][k]; }
+    part[3 * blockIdx.x + 0] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
+  }
+}
+
 // ---- per-step batched kernels over the tile list (one thread per cell)
 
 // FP64 form: X^(s) -> X (GSA: the last stage is the new state), with a

@@ -14,6 +14,7 @@ MiscSet make_misc() {
   m.k_rows_inv = reinterpret_cast<const void*>(&k_fft_rows_inv<T>);
   m.k_set_state = reinterpret_cast<const void*>(&k_set_state<T>);
   m.k_get_state = reinterpret_cast<const void*>(&k_get_state<T>);
+  m.k_diagnostics = reinterpret_cast<const void*>(&k_diagnostics<T>);
   return m;
 }
 template <typename T>

@@ -1,0 +1,111 @@
+"""The paper's numerical experiments (Sec. 4) as workloads, run through the C ABI.
+
+* ``shear_thick`` - double shear layer of Sec. 4.1, 1/rho = 15/pi, up to t = 6;
+* ``shear_thin``  - thin double shear layer of Sec. 4.2, 1/rho = 50/pi, up to t = 9.5;
+* ``kelvin_helmholtz`` - the layer u = (cos y, 0.03 sin(x/2)) of Sec. 4.3 on
+  [0, 4pi)^2 up to t = 45 (tau = 0.05, reading G12).
+
+Each run records, every ``record_every`` steps, the diagnostics the paper plots
+(Figs. 2-3: max |D_0 . u| over time) plus the L2 divergence and the enstrophy,
+and returns the final vorticity.  The time step follows the workloads' rule
+(CFL and viscous bounds) shortened so that the run ends exactly at t_end.
+
+    python -m paper_2512_19847_gb300.experiments --case shear_thin --n 512 --eps 1e-6
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from dataclasses import dataclass, field
+
+import torch
+
+from . import api, tableaux
+from . import workloads as W
+
+CASES = {
+    "shear_thick": {"init": lambda n: W.double_shear_layer(n, inv_rho=15.0 / math.pi), "L": 2 * math.pi, "t_end": 6.0},
+    "shear_thin": {"init": lambda n: W.double_shear_layer(n, inv_rho=50.0 / math.pi), "L": 2 * math.pi, "t_end": 9.5},
+    "kelvin_helmholtz": {"init": W.kelvin_helmholtz, "L": 4 * math.pi, "t_end": 45.0},
+}
+
+
+@dataclass
+class History:
+    case: str
+    n: int
+    eps: float
+    tau: float
+    dt: float
+    steps: int
+    t: list = field(default_factory=list)
+    div_max: list = field(default_factory=list)
+    div_l2: list = field(default_factory=list)
+    enstrophy: list = field(default_factory=list)
+    vorticity: torch.Tensor | None = None
+    wall_s: float = 0.0
+
+    def summary(self) -> dict:
+        return {"case": self.case, "n": self.n, "eps": self.eps, "tau": self.tau, "dt": self.dt, "steps": self.steps,
+                "t": self.t, "div_max": self.div_max, "div_l2": self.div_l2, "enstrophy": self.enstrophy,
+                "wall_s": round(self.wall_s, 3)}
+
+
+def run(case: str, n: int, eps: float = 1e-4, tau: float = 0.05, t_end: float | None = None, record_every: int = 50,
+        precision: int = api.FP64, scheme: str = "WENO5_C4", mach: float = 1e-2, cfl: float = 0.4,
+        visc: float = 0.32) -> History:
+    """Run one Sec. 4 experiment on an n x n grid and record its diagnostics
+    (cfl, visc: the coefficients of the step's CFL and viscous bounds)."""
+    c = CASES[case]
+    L = c["L"]
+    t_end = c["t_end"] if t_end is None else t_end
+    u1, u2, p = c["init"](n)
+    dt, steps = W.fixed_time_dt(t_end, W.stable_dt(u1, u2, L / n, tau, cfl=cfl, visc=visc))
+    prm = api.default_params(n, n, eps=eps, dt=dt, tau=tau, mach=mach, Lx=L, Ly=L, space_scheme=scheme,
+                             tableau=tableaux.gsa2(), precision=precision)
+    s = api.Solver(prm)
+    s.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, p)])
+    h = History(case, n, eps, tau, dt, steps)
+
+    def record(k):
+        d = s.diagnostics()
+        h.t.append(k * dt)
+        h.div_max.append(d["div_max"])
+        h.div_l2.append(d["div_l2"])
+        h.enstrophy.append(d["enstrophy"])
+
+    t0 = time.perf_counter()
+    record(0)
+    done = 0
+    while done < steps:
+        k = min(record_every, steps - done)
+        s.step(k)
+        done += k
+        record(done)
+    s.sync_status()
+    h.vorticity = s.diagnostics(vorticity=True)["vorticity"]
+    h.wall_s = time.perf_counter() - t0
+    return h
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--case", choices=sorted(CASES), default="shear_thick")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--tau", type=float, default=0.05)
+    ap.add_argument("--t-end", type=float, default=None)
+    ap.add_argument("--every", type=int, default=50)
+    ap.add_argument("--fp32", action="store_true", help="FP32 deviation form")
+    ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--visc", type=float, default=0.32)
+    args = ap.parse_args()
+    h = run(args.case, args.n, args.eps, args.tau, args.t_end, args.every,
+            api.FP32_DEV if args.fp32 else api.FP64, cfl=args.cfl, visc=args.visc)
+    print(json.dumps(h.summary()))
+
+
+if __name__ == "__main__":
+    main()

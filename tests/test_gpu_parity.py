@@ -100,7 +100,7 @@ def test_double_shear_layer_sweep(eps):
     assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
 def test_tile_shapes_agree(tile):
     n = 64
     X0 = W.random_moment_state(n, n, seed=5, amp=0.3)
@@ -173,3 +173,69 @@ def test_run_host_matches_device_path():
     s = api.Solver(p)
     b = s.run_host(torch.from_numpy(X0).pin_memory(), 3).numpy()
     assert np.array_equal(a, b)
+
+
+def _pair_domain(nx, ny, Lx, Ly, scheme, eps, dt, tau=0.05):
+    A_ex, A_im = tableaux.gsa2()
+    p = api.default_params(nx, ny, eps=eps, dt=dt, tau=tau, space_scheme=scheme, tableau=(A_ex, A_im), Lx=Lx, Ly=Ly)
+    o = O.Params(nx, ny, eps, tau, dt, np.array(A_ex), np.array(A_im), scheme=scheme, Lx=Lx, Ly=Ly)
+    return p, o
+
+
+@pytest.mark.parametrize("Lx,Ly", [(2 * math.pi, math.pi), (4 * math.pi, math.pi), (math.pi, 3.0)])
+def test_domain_lengths(Lx, Ly):
+    """Periodic domains other than [0, 2pi)^2, with dx != dy (the [0, 4pi)^2 of Sec. 4.3 below)."""
+    nx, ny = 64, 32
+    X0 = W.random_moment_state(nx, ny, seed=17, amp=0.4)
+    p, o = _pair_domain(nx, ny, Lx, Ly, "WENO5_C4", 1e-2, 0.01)
+    got = run_gpu(p, X0, 3)
+    ref = O.run(X0, o, 3)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+def test_kelvin_helmholtz_domain():
+    """Kelvin-Helmholtz data of Sec. 4.3 on [0, 4pi)^2 (tau = 0.05, reading G12), 5 steps
+    (the layer is unstable, so round-off is compared over a short horizon)."""
+    n = 128
+    u1, u2, pr = W.kelvin_helmholtz(n)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    dt = W.stable_dt(u1, u2, 4 * math.pi / n, 0.05)
+    p, o = _pair_domain(n, n, 4 * math.pi, 4 * math.pi, "WENO5_C4", 1e-4, dt)
+    got = run_gpu(p, X0, 5)
+    ref = O.run(X0, o, 5)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO3_C4", "WENO5_C4"])
+def test_diagnostics_match_oracle(scheme):
+    """ap_dvm_diagnostics (max |D_0 . u|, its L2 norm, enstrophy, vorticity) against the oracle's."""
+    nx, ny = 64, 32
+    X0 = W.random_moment_state(nx, ny, seed=23, amp=0.5)
+    p, o = _pair_domain(nx, ny, 2 * math.pi, 1.5 * math.pi, scheme, 1e-2, 0.01)
+    s = api.Solver(p)
+    s.set_state(torch.from_numpy(X0).cuda())
+    got = s.diagnostics(vorticity=True)
+    ref = O.diagnostics(X0, o)
+    for k in ("div_max", "div_l2", "enstrophy"):
+        assert abs(got[k] - ref[k]) <= TOL * abs(ref[k]), (k, got[k], ref[k])
+    w = got["vorticity"].cpu().numpy()
+    assert np.max(np.abs(w - ref["vorticity"])) <= TOL * np.max(np.abs(ref["vorticity"]))
+
+
+def test_diagnostics_fp32_form():
+    """The FP32 form's diagnostics come from its FP32 moment planes (the populations' moments
+    rounded once): the enstrophy within 1e-5 relative, the divergence norms within 1e-5
+    absolute, of the oracle's on the state the solve holds."""
+    n = 64
+    u1, u2, pr = W.random_divfree(n, 4, kmax=8)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    X0[0] += 0.05 * np.sin(W.cell_centres(n, n)[0])          # a divergent part
+    p, o = _pair_domain(n, n, 2 * math.pi, 2 * math.pi, "WENO5_C4", 1e-2, 0.01)
+    p.precision = api.FP32_DEV
+    s = api.Solver(p)
+    s.set_state(torch.from_numpy(X0).cuda())
+    got = s.diagnostics()
+    ref = O.diagnostics(s.get_state().cpu().numpy(), o)
+    assert abs(got["enstrophy"] - ref["enstrophy"]) <= 1e-5 * ref["enstrophy"]
+    for k in ("div_max", "div_l2"):
+        assert abs(got[k] - ref[k]) <= 1e-5, (k, got[k], ref[k])

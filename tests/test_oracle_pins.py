@@ -436,7 +436,8 @@ def test_temporal_order(tab, order):
 
 def test_viscous_time_step_bound():
     """In the limit the viscous term is explicit (Sec. 3.1), so dt needs
-    nu dt/dx^2 below ~0.5: 0.4 (the workload rule) is stable, 0.7 is not."""
+    nu dt/dx^2 below ~0.5: 0.4 is stable over 150 steps, 0.7 is not; the
+    workload rule keeps margin (0.32) for runs of thousands of steps."""
     n, tau = 32, 2.0
     u1, u2, pr = W.taylor_green(n)
     X0 = O.equilibrium_state(u1, u2, pr) + 1e-8 * np.random.default_rng(0).standard_normal((6, n, n))
@@ -449,4 +450,44 @@ def test_viscous_time_step_bound():
             Y = O.step(Y, p)
         out[r] = float(np.max(np.abs(Y[:2]))) if np.isfinite(Y).all() else float("inf")
     assert out[0.4] < 1.0 and out[0.7] > 10.0, out
-    assert W.stable_dt(u1, u2, h, tau) == pytest.approx(0.4 * h * h / (tau / 4))
+    assert W.stable_dt(u1, u2, h, tau) == pytest.approx(0.32 * h * h / (tau / 4))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4 diagnostics: closed forms on fields whose central differences are exact
+def _central_factor(scheme, h):
+    # symbol of D_0 on sin/cos of unit wavenumber: sin(h)/h (2nd order), (8 sin h - sin 2h)/(6h) (4th)
+    return math.sin(h) / h if scheme == "LF1_C2" else (8 * math.sin(h) - math.sin(2 * h)) / (6 * h)
+
+
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO5_C4"])
+def test_diagnostics_taylor_green_closed_form(scheme):
+    """Taylor-Green u = (sin x cos y, -cos x sin y): D_0 . u = 0, omega = 2 s sin x sin y
+    with s the central-difference factor, enstrophy = 2 pi^2 s^2 on [0, 2pi)^2."""
+    n = 32
+    p = O.Params(n, n, 1e-2, 0.05, 0.01, *O.tableau_gsa2()[::2], scheme=scheme)
+    u1, u2, pr = W.taylor_green(n)
+    X = O.equilibrium_state(u1, u2, pr)
+    d = O.diagnostics(X, p)
+    s = _central_factor(scheme, 2 * math.pi / n)
+    xc, yc = W.cell_centres(n, n)
+    assert d["div_max"] < 1e-13
+    assert np.max(np.abs(d["vorticity"] - 2 * s * np.sin(xc) * np.sin(yc))) < 1e-13
+    assert d["enstrophy"] == pytest.approx(2 * math.pi ** 2 * s * s, rel=1e-13)
+
+
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO5_C4"])
+def test_diagnostics_divergent_field_closed_form(scheme):
+    """u = (sin x, 0) on a non-square grid: D_0 . u = s cos x, so max |div| = s cos(h/2)
+    (cell centres), ||div||_2 = s pi sqrt(2), and omega = 0."""
+    nx, ny = 32, 16
+    p = O.Params(nx, ny, 1e-2, 0.05, 0.01, *O.tableau_gsa2()[::2], scheme=scheme)
+    xc, yc = W.cell_centres(nx, ny)
+    X = np.zeros((6, ny, nx))
+    X[0] = np.sin(xc)
+    d = O.diagnostics(X, p)
+    h = 2 * math.pi / nx
+    s = _central_factor(scheme, h)
+    assert d["div_max"] == pytest.approx(s * math.cos(h / 2), rel=1e-13)
+    assert d["div_l2"] == pytest.approx(s * math.pi * math.sqrt(2), rel=1e-13)
+    assert np.max(np.abs(d["vorticity"])) < 1e-13
