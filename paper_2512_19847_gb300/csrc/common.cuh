@@ -63,6 +63,7 @@ struct InstDev {
   double den[APD_MAXS + 1];     // tau eps^2 + dt a_ii
   double inv_den[APD_MAXS + 1]; // 1 / (tau eps^2 + dt a_ii)
   double sc_u, sc_th, sc_v, sc_q;  // population view: 1/(rho0 A), 1/(2 eps rho0 A), 1/(eps rho0 A), 1/(eps^2 rho0 A)
+  double pmc[8];                   // sc_u, sc_u/2, sqrt3 sc_u/2, sc_th, -sc_v/2, sc_v/4, sqrt3 sc_v/4, sc_q/4
   double inv_dx, inv_dy;
   double inv_aii[APD_MAXS + 1];              // 1 / a_ii
   Coef<double> k64;             // the stage coefficients in FP64 ...

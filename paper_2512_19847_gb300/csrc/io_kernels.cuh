@@ -15,23 +15,19 @@ namespace apd {
 
 constexpr double SQ3 = 1.7320508075688772935;
 
-// dF (six values) -> moments (u1, u2, theta, v1, v2, q); the scalings
-// 1/(rho0 A), 1/(2 eps rho0 A), 1/(eps rho0 A), 1/(eps^2 rho0 A) come precomputed.
+// dF (six values) -> moments (u1, u2, theta, v1, v2, q), in FP64.  The
+// scalings 1/(rho0 A), 1/(2 eps rho0 A), 1/(eps rho0 A), 1/(eps^2 rho0 A) and
+// the basis constants come folded together, precomputed per instance (pmc).
 __device__ __forceinline__ void pop_to_mom(const double* dF, const InstDev& I, double* m) {
   const double s1 = dF[0] + dF[3], s2 = dF[1] + dF[4], s3 = dF[2] + dF[5];
   const double d1 = dF[0] - dF[3], d2 = dF[1] - dF[4], d3 = dF[2] - dF[5];
-  const double M0 = s1 + s2 + s3;
-  const double M1 = d1 + 0.5 * (d2 - d3);
-  const double M2 = 0.5 * SQ3 * (d2 + d3);
-  const double M3 = 0.5 * s1 - 0.25 * (s2 + s3);
-  const double M4 = 0.25 * SQ3 * (s2 - s3);
-  const double M5 = 0.25 * (d2 - d1 - d3);
-  m[0] = M1 * I.sc_u;
-  m[1] = M2 * I.sc_u;
-  m[2] = M0 * I.sc_th;
-  m[3] = -M3 * I.sc_v;
-  m[4] = M4 * I.sc_v;
-  m[5] = M5 * I.sc_q;
+  const double* c = I.pmc;
+  m[0] = c[0] * d1 + c[1] * (d2 - d3);          // u1 = (d1 + (d2 - d3)/2) / (rho0 A)
+  m[1] = c[2] * (d2 + d3);                      // u2 = (sqrt3/2)(d2 + d3) / (rho0 A)
+  m[2] = c[3] * ((s1 + s2) + s3);               // theta = sum / (2 eps rho0 A)
+  m[3] = c[4] * s1 + c[5] * (s2 + s3);          // v1 = -(s1/2 - (s2 + s3)/4) / (eps rho0 A)
+  m[4] = c[6] * (s2 - s3);                      // v2 = (sqrt3/4)(s2 - s3) / (eps rho0 A)
+  m[5] = c[7] * ((d2 - d1) - d3);               // q = (d2 - d1 - d3)/4 / (eps^2 rho0 A)
 }
 
 // moments -> dF, in the arithmetic type R (FP64 in the FP64 form and for

@@ -634,29 +634,60 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     const size_t pl = (size_t)nx * I.ny;
     const Coef<T>& K = coef<T>(I);
     const T idx = K.inv_dx, idy = K.inv_dy;
+    const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
+    // right-hand side of the Helmholtz equation (Algorithm 1, step 2; theta-history sign per
+    // reading G4), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii
+    // precomputed.  Its pointwise inputs: the FP32 form loads them before the shared-memory
+    // pass so that their latency overlaps it; FP64 loads them where they are used (fewer
+    // registers for the FP64-pipe-bound form).
+    const unsigned mim = b.m_im[i];
+    const T* Xn = reinterpret_cast<const T*>(I.X);
+    T thn = T(0), du1 = T(0), ldu[APD_MAXS], ldb[APD_MAXS], llth[APD_MAXS];
+    if constexpr (sizeof(T) == 4) {
+      thn = Xn[o + 2 * pl];
+      du1 = reinterpret_cast<const T*>(I.Du[1])[o];
+#pragma unroll
+      for (int jj = 1; jj < APD_MAXS; ++jj) {
+        const bool use = jj < i && has(mim, jj);
+        ldu[jj] = use ? reinterpret_cast<const T*>(I.Du[jj])[o] : T(0);
+        ldb[jj] = use ? reinterpret_cast<const T*>(I.DB[jj])[o] : T(0);
+        llth[jj] = use ? reinterpret_cast<const T*>(I.Lth[jj])[o] : T(0);
+      }
+    }
     for (int k = tid; k < TY * WD; k += TX * TY) {
       const int r = k / WD, cc = k - r * WD;
       sdy[k] = cdiff<T, SCHEME>(sv2 + (G::H + r) * BW + (4 - CH) + cc, BW, idy);
     }
     __syncthreads();
     const int c = G::C00 + ty * BW + tx;
-    const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
     const T dbi = -cdiff2<T, SCHEME>(sv1 + c, 1, idx * idx) + T(2) * cdiff<T, SCHEME>(sdy + ty * WD + CH + tx, 1, idx) +
                   cdiff2<T, SCHEME>(sv1 + c, BW, idy * idy);
     reinterpret_cast<T*>(I.DB[i])[o] = dbi;
-    // right-hand side of the Helmholtz equation (Algorithm 1, step 2; theta-history sign per
-    // reading G4), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii precomputed
-    const T* Xn = reinterpret_cast<const T*>(I.X);
-    const T thn = Xn[o + 2 * pl];
-    const unsigned mim = b.m_im[i];
-    T R = -K.kappa[i] * thn;
-    for (int jj = 1; jj < i; ++jj)
-      if (has(mim, jj)) R = R + K.c_du[i][jj] * reinterpret_cast<const T*>(I.Du[jj])[o];
-    R = R + K.c_dun[i] * reinterpret_cast<const T*>(I.Du[1])[o];
-    for (int jj = 1; jj <= i; ++jj)
-      if (has(mim, jj)) R = R - K.c_db[i][jj] * (jj == i ? dbi : reinterpret_cast<const T*>(I.DB[jj])[o]);
-    for (int jj = 1; jj < i; ++jj)
-      if (has(mim, jj)) R = R + (theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]) * reinterpret_cast<const T*>(I.Lth[jj])[o];
+    T R;
+    if constexpr (sizeof(T) == 4) {
+      R = -K.kappa[i] * thn;
+#pragma unroll
+      for (int jj = 1; jj < APD_MAXS; ++jj)
+        if (jj < i && has(mim, jj)) R = R + K.c_du[i][jj] * ldu[jj];
+      R = R + K.c_dun[i] * du1;
+#pragma unroll
+      for (int jj = 1; jj < APD_MAXS; ++jj)
+        if (jj < i && has(mim, jj)) R = R - K.c_db[i][jj] * ldb[jj];
+      if (has(mim, i)) R = R - K.c_db[i][i] * dbi;
+#pragma unroll
+      for (int jj = 1; jj < APD_MAXS; ++jj)
+        if (jj < i && has(mim, jj)) R = R + (theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]) * llth[jj];
+    } else {
+      thn = Xn[o + 2 * pl];
+      R = -K.kappa[i] * thn;
+      for (int jj = 1; jj < i; ++jj)
+        if (has(mim, jj)) R = R + K.c_du[i][jj] * reinterpret_cast<const T*>(I.Du[jj])[o];
+      R = R + K.c_dun[i] * reinterpret_cast<const T*>(I.Du[1])[o];
+      for (int jj = 1; jj <= i; ++jj)
+        if (has(mim, jj)) R = R - K.c_db[i][jj] * (jj == i ? dbi : reinterpret_cast<const T*>(I.DB[jj])[o]);
+      for (int jj = 1; jj < i; ++jj)
+        if (has(mim, jj)) R = R + (theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]) * reinterpret_cast<const T*>(I.Lth[jj])[o];
+    }
     reinterpret_cast<T*>(I.R)[o] = R;
     if (first_stage) {
       const double tsum = block_sum<double>(double(thn), red, tid, TX * TY);

@@ -197,6 +197,15 @@ inline void fill_constants(const ap_dvm_params& p, InstDev& d) {
   d.sc_th = p.eps > 0 ? ra / (2.0 * p.eps) : 0.0;
   d.sc_v = p.eps > 0 ? ra / p.eps : 0.0;
   d.sc_q = p.eps > 0 ? ra / (p.eps * p.eps) : 0.0;
+  const double sq3 = 1.7320508075688772935;
+  d.pmc[0] = d.sc_u;
+  d.pmc[1] = 0.5 * d.sc_u;
+  d.pmc[2] = 0.5 * sq3 * d.sc_u;
+  d.pmc[3] = d.sc_th;
+  d.pmc[4] = -0.5 * d.sc_v;
+  d.pmc[5] = 0.25 * d.sc_v;
+  d.pmc[6] = 0.25 * sq3 * d.sc_v;
+  d.pmc[7] = 0.25 * d.sc_q;
 }
 
 }  // namespace apd
