@@ -40,7 +40,7 @@ extern "C" {
 typedef enum {
   AP_DVM_OK = 0,
   AP_DVM_ERR_ARG = 1,          /* invalid argument (message in ap_dvm_last_error) */
-  AP_DVM_ERR_TABLEAU = 2,      /* tableau is not a CK/ARS GSA IMEX tableau with a_ii > 0, i >= 2 */
+  AP_DVM_ERR_TABLEAU = 2,      /* tableau is not a DIRK GSA IMEX tableau with a_11 >= 0, a_ii > 0 for i >= 2 */
   AP_DVM_ERR_WORKSPACE = 3,    /* workspace too small or misaligned */
   AP_DVM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   AP_DVM_ERR_NONFINITE = 5,    /* a step produced a non-finite value (latched on the device) */
@@ -68,9 +68,10 @@ enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1 };                   /* precision fo
  *  s           number of stages, 2..AP_DVM_MAX_STAGES.
  *  A_ex, A_im  explicit (strictly lower) and implicit (lower) tableaux of
  *              Sec. 3.1, row-major with row stride AP_DVM_MAX_STAGES; the
- *              implicit tableau must be of type CK/ARS (a_11 = 0, a_ii > 0 for
- *              i >= 2) and the pair globally stiffly accurate, so that the
- *              last stage is the new state.
+ *              implicit tableau is of type CK/ARS (a_11 = 0: stage 1 is X^n)
+ *              or of type A (a_11 > 0: stage 1 is computed by Algorithm 1
+ *              with i = 1), with a_ii > 0 for i >= 2, and the pair globally
+ *              stiffly accurate, so that the last stage is the new state.
  *  space_scheme  AP_DVM_LF1_C2, AP_DVM_WENO3_C4 or AP_DVM_WENO5_C4.
  *  precision   AP_DVM_FP64 (all in FP64) or AP_DVM_FP32_DEV (FP32 deviation
  *              populations and FP32 transport; FP64 moment sums, division by
@@ -180,8 +181,8 @@ int ap_dvm_launches_per_step(const ap_dvm_handle* h);
 ap_dvm_status ap_dvm_profile_enable(ap_dvm_handle* h, int enable);
 /* Synchronise and read per-kernel totals since the last reset: up to max
  * entries of kernel name (static string), total milliseconds and launch
- * count.  Returns the number of kernel kinds (7: explicit, rhs, fft_rows_fwd,
- * fft_cols, fft_rows_inv, update, finish), or -1 on error. */
+ * count.  Returns the number of kernel kinds (8: explicit, rhs, fft_rows_fwd,
+ * fft_cols, fft_rows_inv, update, finish, stage1), or -1 on error. */
 int ap_dvm_profile_read(ap_dvm_handle* h, const char** names, double* total_ms, long* launches, int max);
 
 /* End-to-end call on HOST buffers: copy 6 moment planes h_in (double) to the

@@ -363,8 +363,8 @@ def _explicit_partner(st, A_ex, A, i):
     sum_{j<=i} a_ij diss(P_j) = sum_{j<i} atilde_ij diss(u^(j)), as the
     convective terms do in the limit (Theorem 3.4)."""
     a_ii = A[i - 1, i - 1]
-    p1 = np.zeros_like(st[1].u1)
-    p2 = np.zeros_like(st[1].u1)
+    p1 = np.zeros_like(st[0].u1)        # stage 1 of a type-A tableau: the sum over j < 1 is empty
+    p2 = np.zeros_like(st[0].u1)
     for j in range(1, i):
         w = A_ex[i - 1, j - 1] - A[i - 1, j - 1]
         if w != 0.0:

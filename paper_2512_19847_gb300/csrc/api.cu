@@ -4,10 +4,11 @@
 // `capacity` attached solves, each with its own caller-owned workspace.  The
 // per-instance descriptors and the prefix sums of the work decomposition
 // live in the batch workspace; every kernel of a step is launched once for
-// all attached solves.  One IMEX step (Algorithm 1, CK/ARS tableau, stage 1
-// = X^n) enqueues, for i = 2..s:
-//   k_explicit(i-1)  explicit term of step 1 and reusable operators of stage i-1
-//   k_rhs(i)         step 1 (v^(i)) and the Helmholtz right-hand side of step 2
+// all attached solves.  One IMEX step (Algorithm 1) enqueues, for a type-A
+// tableau first k_stage1 (v^(1), D_0 . u^n), then for each computed stage i
+// (i = 1..s for type A; i = 2..s for CK/ARS, whose stage 1 is X^n):
+//   k_explicit(i-1)  explicit terms and reusable operators of stage i-1, and step 1 (v^(i))
+//   k_rhs(i)         the Helmholtz right-hand side of step 2
 //   k_fft_rows_fwd, k_fft_cols(i), k_fft_rows_inv(i)   step 2 (theta^(i))
 //   k_update(i)      steps 3 and 4 (u^(i), q^(i))
 // and finally k_finish (GSA: X^{n+1} = X^(s); FP32 form: repack populations).
@@ -139,7 +140,7 @@ ap_dvm_status validate(const ap_dvm_params* p, char* buf, size_t n) {
       if (j >= i && ae(i, j) != 0.0) { snprintf(buf, n, "explicit tableau must be strictly lower triangular"); return AP_DVM_ERR_TABLEAU; }
       if (j > i && ai(i, j) != 0.0) { snprintf(buf, n, "implicit tableau must be lower triangular (DIRK)"); return AP_DVM_ERR_TABLEAU; }
     }
-  if (ai(0, 0) != 0.0) { snprintf(buf, n, "type-A tableaux (a_11 != 0) are not supported; use a CK/ARS tableau"); return AP_DVM_ERR_UNSUPPORTED; }
+  if (ai(0, 0) < 0.0) { snprintf(buf, n, "a_11 must be 0 (CK/ARS) or > 0 (type A)"); return AP_DVM_ERR_TABLEAU; }
   for (int i = 1; i < s; ++i)
     if (!(ai(i, i) > 0)) { snprintf(buf, n, "a_ii must be > 0 for i >= 2"); return AP_DVM_ERR_TABLEAU; }
   return AP_DVM_OK;
@@ -167,7 +168,9 @@ size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
   const int s = p.s;
   InstDev tmp{};
   InstDev& I = d ? *d : tmp;
+  const bool type_a = p.A_im[0] != 0.0;
   I.X = take(6 * plane);
+  I.Xs[1] = type_a ? take(6 * plane) : I.X;           // stage 1: its own values (type A) or X^n
   for (int j = 2; j <= s; ++j) I.Xs[j] = take(6 * plane);
   for (int j = 1; j <= s; ++j) {
     I.E[j] = take(2 * plane);
@@ -178,6 +181,7 @@ size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
     I.Dv[j] = take(plane);
     I.DB[j] = take(plane);
   }
+  I.Dun = type_a ? take(plane) : I.Du[1];
   I.R = take(plane);
   I.sstride = p.nx / 2 + 1;
   I.S = take((size_t)p.ny * I.sstride * 2 * es);
@@ -322,8 +326,9 @@ ap_dvm_status flush(ap_dvm_handle* h) {
   return AP_DVM_OK;
 }
 
-constexpr int kNumKinds = 7;
-const char* const kKernelNames[kNumKinds] = {"explicit", "rhs", "fft_rows_fwd", "fft_cols", "fft_rows_inv", "update", "finish"};
+constexpr int kNumKinds = 8;
+const char* const kKernelNames[kNumKinds] = {"explicit", "rhs",    "fft_rows_fwd", "fft_cols",
+                                             "fft_rows_inv", "update", "finish",       "stage1"};
 
 ap_dvm_status launch(ap_dvm_handle* h, cudaStream_t stream, const void* fn, int grid, dim3 block, size_t smem, void** args,
                      int kind = -1) {
@@ -722,7 +727,7 @@ int ap_dvm_get_tile(const ap_dvm_handle* h) { return h ? h->tile : -1; }
 int ap_dvm_launches_per_step(const ap_dvm_handle* h) {
   if (!h) return 0;
   const ap_dvm_params& t = h->tmpl;
-  return 6 * (t.s - 1) + 1;
+  return t.A_im[0] != 0.0 ? 1 + 5 + 6 * (t.s - 1) + 1 : 6 * (t.s - 1) + 1;
 }
 
 ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage, int nsteps) {

@@ -69,9 +69,11 @@ struct InstDev {
   Coef<double> k64;             // the stage coefficients in FP64 ...
   Coef<float> k32;              // ... and rounded once to FP32
   void* X;                      // 6 planes: state at t^n (moments)
-  void* Xs[APD_MAXS + 1];       // stage values X^(j), j = 2..s (6 planes); Xs[s] = next state
+  void* Xs[APD_MAXS + 1];       // stage values X^(j), j = 1..s (6 planes); Xs[1] = X for CK/ARS tableaux
+                                // (stage 1 = X^n), its own buffer for type-A tableaux; Xs[s] = next state
   void* E[APD_MAXS + 1];        // explicit term of step 1 for stage j (2 planes)
   void* Du[APD_MAXS + 1];       // D_0 . u^(j)
+  void* Dun;                    // D_0 . u^n (= Du[1] when stage 1 is X^n)
   void* Lth[APD_MAXS + 1];      // D_Delta theta^(j)
   void* Gth[APD_MAXS + 1];      // D_0 theta^(j) (2 planes)
   void* DLFB[APD_MAXS + 1];     // D_LF . B(v^(j)) with partner u^(j) (2 planes)
@@ -83,7 +85,7 @@ struct InstDev {
   double* lamy;                 // 1D Laplacian symbol in y, ky = 0..ny-1
   double* th_part;              // per-tile partial sums of theta^n
   float* dF;                    // FP32 form: deviation populations (6 planes)
-  const void* tmap;             // tensor maps (128 B each) of the stage buffers, [j] = X (j = 1) or Xs[j]
+  const void* tmap;             // tensor maps (128 B each) of the stage buffers Xs[j]
   int tma;                      // 1: tile loads through the tensor maps; 0: plain loads
   int pad1;
 };

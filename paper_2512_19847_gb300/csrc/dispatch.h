@@ -21,6 +21,7 @@ struct StencilSet {
 
 struct MiscSet {
   const void* k_finish;    // per tile shape
+  const void* k_stage1;    // per tile shape; type-A tableaux only
   const void* k_rows_fwd;
   const void* k_cols;
   const void* k_rows_inv;

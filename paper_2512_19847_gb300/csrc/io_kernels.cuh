@@ -196,6 +196,46 @@ __global__ void __launch_bounds__(256) k_diagnostics(InstDev I, int c4, double* 
 
 // ---- per-step batched kernels over the tile list (one thread per cell)
 
+// Type-A tableaux (a_11 != 0), start of a step: step 1 of stage 1 in closed form,
+// v^(1) = tau eps^2 v^n / (tau eps^2 + dt a_11) (Algorithm 1 with i = 1: the sums
+// over j < 1 are empty), into X^(1), and D_0 . u^n for the right-hand sides of
+// step 2, with the scheme's central difference (c4: 4th order, else 2nd).
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) k_stage1(const BatchDev* __restrict__ bp, int c4) {
+  const BatchDev& b = *bp;
+  const int ntiles = b.counts[0];
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int k_inst = find_inst(b.tile_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const int tile = it - b.tile_start[k_inst];
+    const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
+    const int nx = I.nx, mx = nx - 1, my = I.ny - 1;
+    const size_t pl = (size_t)nx * I.ny;
+    const int i = txi * TX + threadIdx.x, j = tyi * TY + threadIdx.y;
+    const size_t o = (size_t)j * nx + i;
+    const T* Xn = reinterpret_cast<const T*>(I.X);
+    T* X1 = reinterpret_cast<T*>(I.Xs[1]);
+    if (I.relax64) {
+      X1[o + 3 * pl] = T(I.k64.r_n[1] * double(Xn[o + 3 * pl]));
+      X1[o + 4 * pl] = T(I.k64.r_n[1] * double(Xn[o + 4 * pl]));
+    } else {
+      X1[o + 3 * pl] = coef<T>(I).r_n[1] * Xn[o + 3 * pl];
+      X1[o + 4 * pl] = coef<T>(I).r_n[1] * Xn[o + 4 * pl];
+    }
+    auto at = [&](int plane, int ii, int jj) { return Xn[plane * pl + (size_t)(jj & my) * nx + (ii & mx)]; };
+    const T idx = coef<T>(I).inv_dx, idy = coef<T>(I).inv_dy;
+    T dx1, dy2;
+    if (c4) {
+      dx1 = (-at(0, i + 2, j) + T(8) * at(0, i + 1, j) - T(8) * at(0, i - 1, j) + at(0, i - 2, j)) * (idx * T(1.0 / 12.0));
+      dy2 = (-at(1, i, j + 2) + T(8) * at(1, i, j + 1) - T(8) * at(1, i, j - 1) + at(1, i, j - 2)) * (idy * T(1.0 / 12.0));
+    } else {
+      dx1 = (at(0, i + 1, j) - at(0, i - 1, j)) * (T(0.5) * idx);
+      dy2 = (at(1, i, j + 1) - at(1, i, j - 1)) * (T(0.5) * idy);
+    }
+    reinterpret_cast<T*>(I.Dun)[o] = dx1 + dy2;
+  }
+}
+
 // FP64 form: X^(s) -> X (GSA: the last stage is the new state), with a
 // finiteness check.  FP32 form: pack X^(s) into the FP32 deviation
 // populations and store the moments of those populations (store_f32_state)

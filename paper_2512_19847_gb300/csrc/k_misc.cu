@@ -9,6 +9,7 @@ template <typename T, int TX, int TY>
 MiscSet make_misc() {
   MiscSet m{};
   m.k_finish = reinterpret_cast<const void*>(&k_finish<T, TX, TY>);
+  m.k_stage1 = reinterpret_cast<const void*>(&k_stage1<T, TX, TY>);
   m.k_rows_fwd = reinterpret_cast<const void*>(&k_fft_rows_fwd<T>);
   m.k_cols = reinterpret_cast<const void*>(&k_fft_cols<T>);
   m.k_rows_inv = reinterpret_cast<const void*>(&k_fft_rows_inv<T>);

@@ -39,7 +39,9 @@ size_t instance_bytes(const ap_dvm_params& p, char* base, InstDev* I) {
   const size_t plane = (size_t)p.nx * p.ny * sizeof(double);
   size_t off = 0;
   auto take = [&](size_t b) -> void* { off = up(off); void* r = base ? base + off : nullptr; off += b; return r; };
+  const bool type_a = p.A_im[0] != 0.0;
   I->X = take(6 * plane);
+  I->Xs[1] = type_a ? take(6 * plane) : I->X;
   for (int j = 2; j <= p.s; ++j) I->Xs[j] = take(6 * plane);
   for (int j = 1; j <= p.s; ++j) {
     I->E[j] = take(2 * plane);
@@ -50,6 +52,7 @@ size_t instance_bytes(const ap_dvm_params& p, char* base, InstDev* I) {
     I->Dv[j] = take(plane);
     I->DB[j] = take(plane);
   }
+  I->Dun = type_a ? take(plane) : I->Du[1];
   I->R = take(plane);
   I->sstride = p.nx / 2 + 1;
   I->S = take((size_t)p.ny * I->sstride * 2 * sizeof(double));

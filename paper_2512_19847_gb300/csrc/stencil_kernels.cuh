@@ -48,7 +48,7 @@ struct Geo {
 };
 
 // The planes a kernel stages, packed 6 bits each (buffer << 3 | plane) so the
-// list stays in registers.  Buffer 1: X (the state at t^n); buffer j >= 2: X^(j).
+// list stays in registers.  Buffer j: the stage values X^(j) (X^(1) = X^n for CK/ARS tableaux).
 struct PlaneList {
   uint64_t bits = 0;
   int n = 0;
@@ -57,7 +57,7 @@ struct PlaneList {
   __device__ __forceinline__ int plane(int k) const { return int(bits >> (6 * k)) & 7; }
 };
 
-__device__ __forceinline__ const void* stage_buffer(const InstDev& I, int buf) { return buf == 1 ? I.X : I.Xs[buf]; }
+__device__ __forceinline__ const void* stage_buffer(const InstDev& I, int buf) { return I.Xs[buf]; }
 __device__ __forceinline__ const void* stage_map(const InstDev& I, int buf) {
   return reinterpret_cast<const char*>(I.tmap) + 128 * buf;
 }
@@ -503,7 +503,7 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
     if (has(b.m_im[i], jj)) {
       T x1, x2;
       if (jj == jcur) { x1 = vcur1; x2 = vcur2; }
-      else { const T* v = reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj]); x1 = v[o + 3 * pl]; x2 = v[o + 4 * pl]; }
+      else { const T* v = reinterpret_cast<const T*>(I.Xs[jj]); x1 = v[o + 3 * pl]; x2 = v[o + 4 * pl]; }
       a1 = a1 + K.rv_v[i][jj] * R(x1);
       a2 = a2 + K.rv_v[i][jj] * R(x2);
     }
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     T thn = T(0), du1 = T(0), ldu[APD_MAXS], ldb[APD_MAXS], llth[APD_MAXS];
     if constexpr (sizeof(T) == 4) {
       thn = Xn[o + 2 * pl];
-      du1 = reinterpret_cast<const T*>(I.Du[1])[o];
+      du1 = reinterpret_cast<const T*>(I.Dun)[o];
 #pragma unroll
       for (int jj = 1; jj < APD_MAXS; ++jj) {
         const bool use = jj < i && has(mim, jj);
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
       R = -K.kappa[i] * thn;
       for (int jj = 1; jj < i; ++jj)
         if (has(mim, jj)) R = R + K.c_du[i][jj] * reinterpret_cast<const T*>(I.Du[jj])[o];
-      R = R + K.c_dun[i] * reinterpret_cast<const T*>(I.Du[1])[o];
+      R = R + K.c_dun[i] * reinterpret_cast<const T*>(I.Dun)[o];
       for (int jj = 1; jj <= i; ++jj)
         if (has(mim, jj)) R = R - K.c_db[i][jj] * (jj == i ? dbi : reinterpret_cast<const T*>(I.DB[jj])[o]);
       for (int jj = 1; jj < i; ++jj)
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
         if (!has(mim, jj)) continue;
         const double dv = (jj == i) ? double(dvi) : double(reinterpret_cast<const T*>(I.Dv[jj])[o]);
         aq = aq + K64.rq_d[i][jj] * dv;
-        if (jj < i) aq = aq + K64.rv_v[i][jj] * double(reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj])[o + 5 * pl]);
+        if (jj < i) aq = aq + K64.rv_v[i][jj] * double(reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl]);
       }
       out[o + 5 * pl] = T(aq);
     } else {
@@ -788,7 +788,7 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
         if (!has(mim, jj)) continue;
         const T dv = (jj == i) ? dvi : reinterpret_cast<const T*>(I.Dv[jj])[o];
         aq = aq + K.rq_d[i][jj] * dv;
-        if (jj < i) aq = aq + K.rv_v[i][jj] * reinterpret_cast<const T*>(jj == 1 ? I.X : I.Xs[jj])[o + 5 * pl];
+        if (jj < i) aq = aq + K.rv_v[i][jj] * reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl];
       }
       out[o + 5 * pl] = aq;
     }

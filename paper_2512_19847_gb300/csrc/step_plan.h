@@ -14,7 +14,7 @@
 
 namespace apd {
 
-enum KernelKind { KK_EXPLICIT, KK_RHS, KK_ROWS_FWD, KK_COLS, KK_ROWS_INV, KK_UPDATE, KK_FINISH };
+enum KernelKind { KK_EXPLICIT, KK_RHS, KK_ROWS_FWD, KK_COLS, KK_ROWS_INV, KK_UPDATE, KK_FINISH, KK_STAGE1 };
 
 struct StepKernels {
   StencilSet ks;
@@ -28,7 +28,7 @@ struct StepKernels {
 // earlier stage entering the dissipation partner (reading G6).
 inline int update_planes_max(const ap_dvm_params& t) {
   int best = 0;
-  for (int i = 2; i <= t.s; ++i) {
+  for (int i = 1; i <= t.s; ++i) {
     int np = 3;
     for (int j = 1; j < i; ++j)
       if (t.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)] - t.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)] != 0.0) np += 2;
@@ -66,7 +66,7 @@ inline int encode_stage_maps(const ap_dvm_params& p, const InstDev& d, int bw, i
   const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   for (int j = 1; j <= p.s; ++j) {
-    void* base = (j == 1) ? d.X : d.Xs[j];
+    void* base = d.Xs[j];
     const CUresult r = encode(&out[j], f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
                               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -84,20 +84,27 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
   int st;
   auto AEX = [&](int i, int j) { return t.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
   auto AIM = [&](int i, int j) { return t.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]; };
-  for (int i = 2; i <= s; ++i) {
+  // type-A tableaux (a_11 != 0) compute stage 1 with the four steps; CK/ARS take X^(1) = X^n
+  const bool type_a = AIM(1, 1) != 0.0;
+  if (type_a) {
+    int c4 = t.space_scheme != AP_DVM_LF1_C2;
+    void* a[] = {&bp, &c4};
+    if ((st = launch(K.km.k_stage1, K.g_finish, blk, 0, a, KK_STAGE1))) return st;
+  }
+  for (int i = type_a ? 1 : 2; i <= s; ++i) {
     int j = i - 1;
     unsigned need = 32u;                                   // v^(i), step 1 of stage i
     for (int k = j + 1; k <= s; ++k) {
       if (AEX(k, j) != 0.0) need |= 1u;                    // E^(j)
       if (AIM(k, j) != 0.0) need |= 2u | 4u | 8u | 16u;    // D0.u, D_Delta theta, D0 theta, D_LF.B(v) of stage j
     }
-    if (j == 1) need |= 2u;                                // D0 . u^n enters every right-hand side
-    {
+    if (j == 1 && !type_a) need |= 2u;                     // D0 . u^n (= D0 . u^(1)) enters every right-hand side
+    if (j >= 1) {
       void* a[] = {&bp, &j, &need, &weno_eps};
       if ((st = launch(K.ks.k_explicit, K.g_explicit, blk, K.ks.smem_explicit, a, KK_EXPLICIT))) return st;
     }
     double sign = -1.0;                                    // reading G4
-    int first = (i == 2) ? 1 : 0;
+    int first = (i == (type_a ? 1 : 2)) ? 1 : 0;           // the first right-hand side also sums theta^n
     {
       void* a[] = {&bp, &i, &sign, &first};
       if ((st = launch(K.ks.k_rhs, K.g_rhs, blk, K.ks.smem_rhs, a, KK_RHS))) return st;
@@ -134,8 +141,9 @@ inline void fill_coef(const ap_dvm_params& p, const InstDev& d, Coef<T>& k) {
       k.aex[i][j] = T(p.A_ex[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]);
       k.aim[i][j] = T(p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (j - 1)]);
     }
-  for (int i = 2; i <= p.s; ++i) {
+  for (int i = 1; i <= p.s; ++i) {
     const double aii = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+    if (aii == 0.0) continue;                     // stage 1 of a CK/ARS tableau is X^n
     k.kappa[i] = T(d.kappa[i]);
     k.r_n[i] = T(d.te2 * d.inv_den[i]);
     k.c_dun[i] = T(1.0 / (p.dt * aii));
@@ -181,15 +189,19 @@ inline void fill_constants(const ap_dvm_params& p, InstDev& d) {
   d.te2 = d.tau * p.eps * p.eps;
   d.rho0 = p.rho0;
   d.amp = p.mach;
-  for (int i = 2; i <= p.s; ++i) {
+  for (int i = 1; i <= p.s; ++i) {
     const double a = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+    if (a == 0.0) continue;
     d.kappa[i] = 2.0 * p.eps * p.eps / (p.dt * p.dt * a * a);
     d.den[i] = d.te2 + p.dt * a;
     d.inv_den[i] = 1.0 / d.den[i];
   }
   d.inv_dx = 1.0 / d.dx;
   d.inv_dy = 1.0 / d.dy;
-  for (int i = 2; i <= p.s; ++i) d.inv_aii[i] = 1.0 / p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+  for (int i = 1; i <= p.s; ++i) {
+    const double a = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
+    d.inv_aii[i] = a != 0.0 ? 1.0 / a : 0.0;
+  }
   fill_coef(p, d, d.k64);
   fill_coef(p, d, d.k32);
   const double ra = 1.0 / (p.rho0 * p.mach);

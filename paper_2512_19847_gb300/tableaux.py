@@ -1,4 +1,5 @@
-"""IMEX-RK tableaux of Sec. 4.1 as (A_ex, A_im) lists (GSA, type CK/ARS)."""
+"""IMEX-RK tableaux as (A_ex, A_im) lists: the GSA schemes of Sec. 4.1 (type
+CK/ARS: a_11 = 0) and type-A GSA tableaux (a_ii != 0 for every i, Sec. 3.1)."""
 
 
 def euler():
@@ -11,4 +12,19 @@ def gsa2(c: float = 2.25):
     g = (c - 0.5) / (c - 1.0)
     A_ex = [[0.0, 0.0, 0.0], [c, 0.0, 0.0], [1.0 - 1.0 / (2.0 * c), 1.0 / (2.0 * c), 0.0]]
     A_im = [[0.0, 0.0, 0.0], [0.0, c, 0.0], [0.0, 1.0 - g, g]]
+    return A_ex, A_im
+
+
+def type_a_euler():
+    """First-order type-A GSA pair: the implicit part takes an implicit Euler
+    stage from t^n, the explicit part one explicit Euler step from it
+    (A_ex = [[0, 0], [1, 0]], A_im = [[1, 0], [0, 1]])."""
+    return [[0.0, 0.0], [1.0, 0.0]], [[1.0, 0.0], [0.0, 1.0]]
+
+
+def type_a3():
+    """A three-stage type-A GSA pair (consistent, first order) with every
+    implicit diagonal entry and every off-diagonal coupling nonzero."""
+    A_ex = [[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [0.3, 0.7, 0.0]]
+    A_im = [[0.4, 0.0, 0.0], [0.1, 0.6, 0.0], [0.2, 0.5, 0.3]]
     return A_ex, A_im

@@ -46,8 +46,10 @@ def test_validation_without_gpu():
     assert api.lib().ap_dvm_workspace_size(ctypes.byref(bad)) == 0
     bad = p.copy(); bad.A_ex[0] = 1.0                # explicit diagonal
     assert api.lib().ap_dvm_workspace_size(ctypes.byref(bad)) == 0
-    bad = p.copy(); bad.A_im[0] = 0.5                # type A: unsupported
+    bad = p.copy(); bad.A_im[0] = -0.5               # negative a_11
     assert api.lib().ap_dvm_workspace_size(ctypes.byref(bad)) == 0
+    a = p.copy(); a.A_im[0] = 0.5                    # type A: stage 1 gets its own buffers
+    assert api.lib().ap_dvm_workspace_size(ctypes.byref(a)) > api.lib().ap_dvm_workspace_size(ctypes.byref(p))
     bad = p.copy(); bad.precision = api.FP32_DEV; bad.eps = 0.0
     assert api.lib().ap_dvm_workspace_size(ctypes.byref(bad)) == 0
     e = p.copy(); e.set_tableau(*tableaux.euler())

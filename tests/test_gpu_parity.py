@@ -20,7 +20,7 @@ TOL = 1e-12
 
 
 def _tab(name):
-    return tableaux.gsa2() if name == "gsa2" else tableaux.euler()
+    return getattr(tableaux, name)()
 
 
 def _pair(nx, ny, scheme, tab, eps, tau, dt, **kw):
@@ -239,3 +239,44 @@ def test_diagnostics_fp32_form():
     assert abs(got["enstrophy"] - ref["enstrophy"]) <= 1e-5 * ref["enstrophy"]
     for k in ("div_max", "div_l2"):
         assert abs(got[k] - ref[k]) <= 1e-5, (k, got[k], ref[k])
+
+
+@pytest.mark.parametrize("tab", ["type_a_euler", "type_a3"])
+@pytest.mark.parametrize("scheme", ["LF1_C2", "WENO5_C4"])
+@pytest.mark.parametrize("eps", [1.0, 1e-4, 0.0])
+def test_type_a_tableaux(tab, scheme, eps):
+    """Type-A tableaux (a_11 != 0): stage 1 by Algorithm 1 with i = 1, then the usual stages."""
+    nx, ny = 64, 32
+    X0 = W.random_moment_state(nx, ny, seed=31, amp=0.4)
+    p, o = _pair(nx, ny, scheme, tab, eps, 0.05, 0.01)
+    got = run_gpu(p, X0, 2)
+    ref = O.run(X0, o, 2)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+def test_type_a_batch_equals_alone_and_fp32_form():
+    """Type A in the batched form (bitwise equal to each solve alone) and in the
+    FP32 deviation form (velocity within 1e-5 of FP64 on a resolved flow)."""
+    n = 64
+    u1, u2, pr = W.taylor_green(n)
+    fields = [torch.from_numpy(a).cuda() for a in (u1, u2, pr)]
+    out = {}
+    for prec in (api.FP64, api.FP32_DEV):
+        p = api.default_params(n, n, eps=1e-4, dt=0.01, tau=0.05, mach=1e-3, tableau=tableaux.type_a3(), precision=prec)
+        s = api.Solver(p)
+        s.set_equilibrium(*fields)
+        s.step(10)
+        out[prec] = s.get_state().cpu().numpy()
+        b = api.Batch(p, capacity=2)
+        q = p.copy()
+        q.nx = q.ny = 32
+        b.attach(0, q)
+        b.attach(1, p)
+        small = [torch.from_numpy(a).cuda() for a in W.taylor_green(32)]
+        b.set_equilibrium(*small, slot=0)
+        b.set_equilibrium(*fields, slot=1)
+        b.set_tile(s.tile)
+        b.step(10)
+        assert np.array_equal(b.get_state(1).cpu().numpy(), out[prec])
+    a, c = out[api.FP64], out[api.FP32_DEV]
+    assert np.max(np.hypot(a[0] - c[0], a[1] - c[1])) / np.max(np.hypot(a[0], a[1])) <= 1e-5

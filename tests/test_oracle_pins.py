@@ -491,3 +491,59 @@ def test_diagnostics_divergent_field_closed_form(scheme):
     assert d["div_max"] == pytest.approx(s * math.cos(h / 2), rel=1e-13)
     assert d["div_l2"] == pytest.approx(s * math.pi * math.sqrt(2), rel=1e-13)
     assert np.max(np.abs(d["vorticity"])) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Type-A tableaux (a_11 != 0): stage 1 by Algorithm 1 with i = 1
+def _type_a_params(n, eps, tau, dt, **kw):
+    from paper_2512_19847_gb300 import tableaux
+    A_ex, A_im = tableaux.type_a_euler()
+    return O.Params(n, n, eps, tau, dt, np.array(A_ex), np.array(A_im), **kw)
+
+
+def test_type_a_taylor_green_limit_decay():
+    """eps -> 0 with a type-A tableau: u follows the INS Taylor-Green solution with
+    nu = tau/4 and the kinetic energy decays like exp(-4 nu t) (Theorem 3.4: type-A
+    GSA is consistent with INS in the limit)."""
+    tau, T = 0.4, 0.5
+    nu = tau / 4
+    errs = []
+    for n in (16, 32):
+        u1, u2, pr = W.taylor_green(n)
+        X = O.equilibrium_state(u1, u2, pr)
+        dt, ns = W.fixed_time_dt(T, 0.25 * 2 * math.pi / n)
+        Y = O.run(X, _type_a_params(n, 1e-6, tau, dt, scheme="WENO5_C4"), ns)
+        e1, e2, _ = W.taylor_green(n, t=T, nu=nu)
+        errs.append(max(np.abs(Y[0] - e1).max(), np.abs(Y[1] - e2).max()))
+        ke_ratio = np.mean(Y[0] ** 2 + Y[1] ** 2) / np.mean(X[0] ** 2 + X[1] ** 2)
+        assert abs(ke_ratio / math.exp(-4 * nu * T) - 1) < (0.05 if n == 16 else 0.01)
+    assert errs[1] < errs[0] / 2
+
+
+def test_type_a_temporal_order_one():
+    """Self-convergence under dt halving (consistent operators, limit regime): order 1."""
+    n, T = 16, 0.4
+    u1, u2, pr = W.taylor_green(n)
+    X = O.equilibrium_state(u1, u2, pr)
+    sols = [O.run(X, _type_a_params(n, 1e-6, 0.2, T / ns, scheme="LF1_C2", alpha=0.0, operators="consistent"), ns)
+            for ns in (8, 16, 32)]
+    e1 = np.max(np.abs(sols[0][:2] - sols[1][:2]))
+    e2 = np.max(np.abs(sols[1][:2] - sols[2][:2]))
+    assert abs(math.log2(e1 / e2) - 1.0) < 0.1
+
+
+def test_type_a_projects_non_prepared_data():
+    """Type A needs no well-prepared data (Sec. 3.1): from a divergent initial
+    velocity, one step in the limit returns D_0 . u = O((eps/dt)^2) with
+    mutually consistent operators."""
+    n, dt = 32, 0.01
+    u1, u2, pr = W.taylor_green(n)
+    xc, _ = W.cell_centres(n, n)
+    X0 = O.equilibrium_state(u1 + 0.3 * np.sin(xc), u2, pr)
+    d = {}
+    for eps in (1e-4, 1e-8):
+        p = _type_a_params(n, eps, 0.05, dt, scheme="WENO5_C4", operators="consistent")
+        X = O.step(X0, p)
+        d[eps] = np.max(np.abs(O.div_c(X[0], X[1], p)))
+        assert d[eps] < (eps / dt) ** 2 + 1e-11, (eps, d[eps])
+    assert d[1e-4] / d[1e-8] > 1e7          # it vanishes like eps^2

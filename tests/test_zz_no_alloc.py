@@ -26,11 +26,12 @@ def _rel(a, b):
     return np.max(np.abs(a - b), axis=(1, 2)) / np.maximum(np.max(np.abs(b), axis=(1, 2)), 1e-300)
 
 
-@pytest.mark.parametrize("scheme,n", [("WENO5_C4", 64), ("LF1_C2", 128), ("WENO3_C4", 16)])
-def test_noalloc_matches_handle_path_two_calls(scheme, n):
+@pytest.mark.parametrize("scheme,n,tab", [("WENO5_C4", 64, "gsa2"), ("LF1_C2", 128, "gsa2"), ("WENO3_C4", 16, "gsa2"),
+                                          ("WENO5_C4", 64, "type_a3")])
+def test_noalloc_matches_handle_path_two_calls(scheme, n, tab):
     fn = _noalloc()
     X0 = W.random_moment_state(n, n, seed=404, amp=0.4)
-    p = api.default_params(n, n, eps=1e-2, dt=0.01, tau=0.05, space_scheme=scheme, tableau=tableaux.gsa2())
+    p = api.default_params(n, n, eps=1e-2, dt=0.01, tau=0.05, space_scheme=scheme, tableau=getattr(tableaux, tab)())
     ref = api.Solver(p)
     ref.set_state(torch.from_numpy(X0).cuda())
     d = torch.from_numpy(X0).cuda().contiguous()
