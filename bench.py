@@ -335,6 +335,21 @@ def run_served(torch, n_requests=48, budget=120e9, load=0.8, v_ref=None, seed=7)
     return {"continuous_batching": mixed, "alone_per_solve": alone}
 
 
+def replica_rate(ms_local: float, cells: int, steps: int, dist=None, device: str = "cuda"):
+    """Whole-job throughput of N independent replicas (the solve does not shard):
+    the slowest rank's time (max over ranks) and the cells of all ranks.
+    Returns (Mcell-updates/s, max ms)."""
+    import torch
+    world = 1
+    ms = float(ms_local)
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * cells * steps / (ms * 1e-3) / 1e6, ms
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -424,17 +439,8 @@ def main():
     clocks = clk.summary()
     s32, ms32 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, True, args.steps, args.warmup, barrier)
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms64 = max_over_ranks(ms64)
-    ms32 = max_over_ranks(ms32)
-    v64 = world * cells * args.steps / (ms64 * 1e-3) / 1e6
-    v32 = world * cells * args.steps / (ms32 * 1e-3) / 1e6
+    v64, ms64 = replica_rate(ms64, cells, args.steps, dist, "cuda")
+    v32, ms32 = replica_rate(ms32, cells, args.steps, dist, "cuda")
 
     # accuracy of the FP32 deviation form against the FP64 result after the same steps
     X64 = s64.get_state().cpu().numpy()
