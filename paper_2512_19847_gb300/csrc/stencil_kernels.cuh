@@ -337,9 +337,11 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
 }
 
 // FP32 WENO5 fluxes of both axes without shared scratch: a work item is a run
-// of KR = 3 consecutive interfaces of one line of one pair.  Its thread loads
-// the KR + 5 points the run needs, splits them (g+, g-) and forms their
-// curvature terms in registers, then evaluates the interfaces.  Items of the
+// of KR = 5 consecutive interfaces of one line of one pair (measured faster than
+// runs of 3, 4 or 6 on the 16x8 tile: fewer loaded points per interface and
+// fewer rounds of items per block).  Its thread loads the KR + 5 points the run
+// needs, splits them (g+, g-) and forms their curvature terms in registers,
+// then evaluates the interfaces.  Items of the
 // x axis come first, then those of the y axis; consecutive threads take
 // consecutive lines.  Points past the end of a line are clamped: they only
 // feed interfaces of the last run that are not stored.  (Scalar FP32 with
@@ -367,7 +369,7 @@ template <int TX, int TY, int NP, int AX>
 __device__ __forceinline__ void w5_runs_item(const float* g, const float* U, bool neg, float* out, float ew4, int line,
                                              int run) {
   using G = Geo<float, WENO5_C4, TX, TY>;
-  constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = 3, NPT = KR + 5;
+  constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = 5, NPT = KR + 5;
   constexpr int LL = AX == 0 ? G::W : G::HH;
   constexpr int NI = AX == 0 ? TX + 1 : TY + 1;
   // the last run reads up to point RUNS*KR + 4: inside the staged row for x (BW = TX + 8
@@ -406,7 +408,7 @@ __device__ __forceinline__ void w5_runs_item(const float* g, const float* U, boo
 template <int TX, int TY, int NP, unsigned NEGX, unsigned NEGY>
 __device__ __forceinline__ void w5_runs_both_axes(const float* const* gx, const float* const* ux, const float* const* gy,
                                                   const float* const* uy, float* fx, float* fy, float ew, int tid) {
-  constexpr int KR = 3, NT = TX * TY;
+  constexpr int KR = 5, NT = TX * TY;
   constexpr int RX = (TX + 1 + KR - 1) / KR, RY = (TY + 1 + KR - 1) / KR;
   constexpr int IX = NP * TY * RX, IY = NP * TX * RY;
   constexpr int NXI = TY * (TX + 1), NYI = (TY + 1) * TX;
