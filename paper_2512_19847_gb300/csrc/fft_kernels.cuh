@@ -152,7 +152,7 @@ __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int n
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256) k_fft_rows_fwd(const BatchDev* __restrict
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 4) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(const BatchDev* __restrict__ b
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
