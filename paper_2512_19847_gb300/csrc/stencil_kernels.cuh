@@ -39,11 +39,12 @@ struct Geo {
   static constexpr int C00 = H * BW + 4;                // interior cell (0, 0)
   static constexpr int NX = TY * (TX + 1), NY = (TY + 1) * TX;
   static constexpr int LS = (TY * W > HH * TX) ? TY * W : HH * TX;
-  // split scratch: none for LF1, and none for FP32 WENO5 (register runs)
-  static constexpr int SPLIT_PER_PAIR = (SCHEME == LF1_C2 || (SCHEME == WENO5_C4 && sizeof(T) == 4)) ? 0 : 4 * LS;
+  // FP32 WENO5 computes its fluxes in register runs: no split scratch, no partner planes
+  static constexpr bool RUNS = SCHEME == WENO5_C4 && sizeof(T) == 4;
+  static constexpr int SPLIT_PER_PAIR = (SCHEME == LF1_C2 || RUNS) ? 0 : 4 * LS;
   // shared memory besides the double-buffered planes, and its element count
   static constexpr int EXPLICIT_EXTRA = 3 * SPLIT_PER_PAIR + 3 * NX + 3 * NY;
-  static constexpr int UPDATE_EXTRA = 2 * PL + 2 * SPLIT_PER_PAIR + 2 * NX + 2 * NY;
+  static constexpr int UPDATE_EXTRA = (RUNS ? 0 : 2 * PL) + 2 * SPLIT_PER_PAIR + 2 * NX + 2 * NY;
   static constexpr int RHS_EXTRA = TY * (TX + 2 * CH) + 64;     // d_y v2 rows, block-sum scratch
 };
 
@@ -365,8 +366,28 @@ __device__ __forceinline__ float w5_rec_f32(float a, float b, float c, float d, 
   return num * rcp_approx(den);
 }
 
-template <int TX, int TY, int NP, int AX>
-__device__ __forceinline__ void w5_runs_item(const float* g, const float* U, bool neg, float* out, float ew4, int line,
+// Values of the LF partner U at a staged point: one plane, or the weighted sum of
+// the staged u planes of earlier stages (the dissipation partner of reading G6),
+// summed in stage order.
+struct PlaneOne {
+  const float* p;
+  __device__ __forceinline__ float operator()(int o) const { return p[o]; }
+};
+struct PlaneSum {
+  const float* f[APD_MAXS - 1];
+  float w[APD_MAXS - 1];
+  int n;
+  __device__ __forceinline__ float operator()(int o) const {
+    float r = 0.f;
+#pragma unroll
+    for (int m = 0; m < APD_MAXS - 1; ++m)
+      if (m < n) r = r + w[m] * f[m][o];
+    return r;
+  }
+};
+
+template <int TX, int TY, int NP, int AX, class UF>
+__device__ __forceinline__ void w5_runs_item(const float* g, const UF& U, bool neg, float* out, float ew4, int line,
                                              int run) {
   using G = Geo<float, WENO5_C4, TX, TY>;
   constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = 5, NPT = KR + 5;
@@ -383,7 +404,7 @@ __device__ __forceinline__ void w5_runs_item(const float* g, const float* U, boo
   for (int j = 0; j < NPT; ++j) {
     const int pt = CLAMP ? min(m0 + j, LL - 1) : m0 + j;
     const int o = AX == 0 ? (H + line) * SW + XO + pt : pt * SW + XO + H + line;
-    const float hg = hs * g[o], hu = 0.5f * U[o];
+    const float hg = hs * g[o], hu = 0.5f * U(o);
     Pp[j] = hg + hu;
     Pm[j] = hg - hu;
   }
@@ -405,9 +426,9 @@ __device__ __forceinline__ void w5_runs_item(const float* g, const float* U, boo
   }
 }
 
-template <int TX, int TY, int NP, unsigned NEGX, unsigned NEGY>
-__device__ __forceinline__ void w5_runs_both_axes(const float* const* gx, const float* const* ux, const float* const* gy,
-                                                  const float* const* uy, float* fx, float* fy, float ew, int tid) {
+template <int TX, int TY, int NP, unsigned NEGX, unsigned NEGY, class UF>
+__device__ __forceinline__ void w5_runs_both_axes(const float* const* gx, const UF* ux, const float* const* gy, const UF* uy,
+                                                  float* fx, float* fy, float ew, int tid) {
   constexpr int KR = 5, NT = TX * TY;
   constexpr int RX = (TX + 1 + KR - 1) / KR, RY = (TY + 1 + KR - 1) / KR;
   constexpr int IX = NP * TY * RX, IY = NP * TX * RY;
@@ -431,7 +452,13 @@ template <typename T, int SCHEME, int TX, int TY, int NP, unsigned NEGX, unsigne
 __device__ __forceinline__ void both_axes(const T* const* gx, const T* const* ux, const T* const* gy, const T* const* uy,
                                           T* split, T* fx, T* fy, T ew, int tid) {
   if constexpr (std::is_same<T, float>::value && SCHEME == WENO5_C4) {
-    w5_runs_both_axes<TX, TY, NP, NEGX, NEGY>(gx, ux, gy, uy, fx, fy, ew, tid);
+    PlaneOne px[NP], py[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      px[k].p = ux[k];
+      py[k].p = uy[k];
+    }
+    w5_runs_both_axes<TX, TY, NP, NEGX, NEGY>(gx, px, gy, py, fx, fy, ew, tid);
   } else {
     axis_fluxes<T, SCHEME, TX, TY, NP, NEGX, 0>(gx, ux, split, fx, ew, tid);
     __syncthreads();
@@ -709,9 +736,9 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
   const PlaneList pr = update_planes(b, i);
   const int np = pr.n;
   T* stage = aligned_smem<T>(smem_raw);    // 2 x np planes
-  T* sp1 = stage + 2 * np * PL;            // dissipation partner
+  T* sp1 = stage + 2 * np * PL;            // dissipation partner (not with register runs)
   T* sp2 = sp1 + PL;
-  T* split = sp2 + PL;                     // 2 pairs
+  T* split = G::RUNS ? sp1 : sp2 + PL;     // 2 pairs
   T* fx = split + 2 * G::SPLIT_PER_PAIR;   // [2][NX]: (-v1;p1), (v2;p2)
   T* fy = fx + 2 * NX;                     // [2][NY]: (v2;p1), (v1;p2)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * TX;
@@ -725,21 +752,38 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
     const size_t pl = (size_t)nx * I.ny;
     // dissipation partner of D_LF . B(v^(i)) (reading G6): (1/a_ii) sum_{j<i} (atilde_ij - a_ij) u^(j)
     const Coef<T>& K = coef<T>(I);
-    for (int e = tid; e < G::BW * G::BH; e += TX * TY) {
-      T p1 = T(0), p2 = T(0);
-      int k = 3;
-      for (int jj = 1; jj < i; ++jj) {
-        if (has(mwp, jj)) {
-          p1 = p1 + K.wp[i][jj] * s[k * PL + e];
-          p2 = p2 + K.wp[i][jj] * s[(k + 1) * PL + e];
-          k += 2;
-        }
+    if constexpr (G::RUNS) {
+      // FP32 WENO5: the register runs form the partner at each point they load
+      PlaneSum P1, P2;
+      P1.n = P2.n = i - 1;
+#pragma unroll
+      for (int jj = 1; jj < APD_MAXS; ++jj) {
+        const bool on = jj < i && has(mwp, jj);
+        const int k = 3 + 2 * __popc(mwp & ((1u << jj) - 2u));      // staged plane of u1^(jj)
+        P1.f[jj - 1] = on ? s + k * PL : s;
+        P2.f[jj - 1] = on ? s + (k + 1) * PL : s;
+        P1.w[jj - 1] = P2.w[jj - 1] = on ? K.wp[i][jj] : 0.f;
       }
-      sp1[e] = p1;
-      sp2[e] = p2;
-    }
-    __syncthreads();
-    {
+      const T* gx[2] = {sv1, sv2};
+      const PlaneSum ux[2] = {P1, P2};
+      const T* gy[2] = {sv2, sv1};
+      const PlaneSum uy[2] = {P1, P2};
+      w5_runs_both_axes<TX, TY, 2, 1u, 0u>(gx, ux, gy, uy, fx, fy, ew, tid);
+    } else {
+      for (int e = tid; e < G::BW * G::BH; e += TX * TY) {
+        T p1 = T(0), p2 = T(0);
+        int k = 3;
+        for (int jj = 1; jj < i; ++jj) {
+          if (has(mwp, jj)) {
+            p1 = p1 + K.wp[i][jj] * s[k * PL + e];
+            p2 = p2 + K.wp[i][jj] * s[(k + 1) * PL + e];
+            k += 2;
+          }
+        }
+        sp1[e] = p1;
+        sp2[e] = p2;
+      }
+      __syncthreads();
       const T* gx[2] = {sv1, sv2};
       const T* ux[2] = {sp1, sp2};
       const T* gy[2] = {sv2, sv1};
