@@ -14,7 +14,8 @@ struct StencilSet {
   const void* k_rhs;
   const void* k_update;
   size_t smem_explicit, smem_rhs;
-  size_t plane_bytes, update_fixed;   // k_update: update_fixed + 2 * (planes staged) * plane_bytes
+  size_t plane_bytes, update_fixed;   // k_update: update_fixed + nbuf * (planes staged) * plane_bytes
+  int nbuf;                            // staged plane buffers of k_update (1 or 2)
   int tx, ty;
   int bw, bh;                          // staged box: (tx + 8) x (ty + 2 * halo)
 };

@@ -41,10 +41,16 @@ struct Geo {
   static constexpr int LS = (TY * W > HH * TX) ? TY * W : HH * TX;
   // FP32 WENO5 computes its fluxes in register runs: no split scratch, no partner planes
   static constexpr bool RUNS = SCHEME == WENO5_C4 && sizeof(T) == 4;
+  // FP64 WENO5 update: the passes of both axes run together (split scratch for both
+  // axes at once), its planes staged single-buffered to leave room for it
+  static constexpr bool MERGED = SCHEME == WENO5_C4 && sizeof(T) == 8;
+  static constexpr int NBUF_U = MERGED ? 1 : 2;               // staged plane buffers of k_update
+  static constexpr int LSX = TY * W, LSY = HH * TX;           // split points per pair, x and y
   static constexpr int SPLIT_PER_PAIR = (SCHEME == LF1_C2 || RUNS) ? 0 : 4 * LS;
-  // shared memory besides the double-buffered planes, and its element count
+  static constexpr int SPLIT_U_PER_PAIR = (SCHEME == LF1_C2 || RUNS) ? 0 : (MERGED ? 4 * (LSX + LSY) : 4 * LS);
+  // shared memory besides the staged planes, and its element count
   static constexpr int EXPLICIT_EXTRA = 3 * SPLIT_PER_PAIR + 3 * NX + 3 * NY;
-  static constexpr int UPDATE_EXTRA = (RUNS ? 0 : 2 * PL) + 2 * SPLIT_PER_PAIR + 2 * NX + 2 * NY;
+  static constexpr int UPDATE_EXTRA = (RUNS ? 0 : 2 * PL) + 2 * SPLIT_U_PER_PAIR + 2 * NX + 2 * NY;
   static constexpr int RHS_EXTRA = TY * (TX + 2 * CH) + 64;     // d_y v2 rows, block-sum scratch
 };
 
@@ -120,7 +126,7 @@ __device__ __forceinline__ void stage_begin(const BatchDev& b, int it, const Pla
 
 // The persistent, double-buffered tile loop: body(I, tile, staged planes) runs
 // for every tile of the batch assigned to this block.
-template <typename T, class G, int TX, int TY, class Body>
+template <typename T, class G, int TX, int TY, int NB = 2, class Body>
 __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr, T* stage0, uint64_t* bars, int tid,
                                           Body&& body) {
   constexpr int NT = TX * TY;
@@ -134,6 +140,27 @@ __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr
   __syncthreads();
   unsigned phase = 0u;                    // bit c: parity of the next phase of bars[c]
   int it = blockIdx.x;
+  if constexpr (NB == 1) {
+    // single buffer: stage the tile, wait, compute, then the next tile
+    for (; it < ntiles; it += gridDim.x) {
+      stage_begin<T, G, TX, TY>(b, it, pr, stage0, &bars[0], tid, NT);
+      const TileRef t = decode_tile<TX, TY>(b, it);
+      const InstDev& I = b.inst[t.inst];
+      if (I.tma) {
+        const bool ok = mbar_wait(&bars[0], phase & 1u);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) atomicOr(b.err, 2u);
+          return;
+        }
+        if (tile_on_edge<G>(I, t.x0, t.y0)) stage_plain<T, G>(I, pr, stage0, t.x0, t.y0, true, tid, NT);
+      }
+      __syncthreads();
+      body(I, t, stage0);
+      __syncthreads();
+    }
+    return;
+  }
   if (it < ntiles) stage_begin<T, G, TX, TY>(b, it, pr, stage0, &bars[0], tid, NT);
   for (int cur = 0; it < ntiles; it += gridDim.x, cur ^= 1) {
     const int nxt = it + gridDim.x;
@@ -446,9 +473,88 @@ __device__ __forceinline__ void w5_runs_both_axes(const float* const* gx, const 
   }
 }
 
+// FP64 WENO5 fluxes of both axes with the passes of the two axes run together:
+// the splitting of every point of both axes' lines, then their curvature terms,
+// then every interface of both axes, one barrier after each pass.  Merging the
+// axes balances the rounds of each pass over the block's threads (the FP64 pipe
+// otherwise idles in each pass's last, partly filled round).  The split scratch
+// holds both axes: x lines line-major, y lines point-major, as in axis_fluxes.
+template <typename T, int TX, int TY, int NP, unsigned NEGX, unsigned NEGY>
+__device__ __forceinline__ void w5_fluxes_xy(const T* const* gx, const T* const* ux, const T* const* gy,
+                                             const T* const* uy, T* split, T* fx, T* fy, T ew, int tid) {
+  using G = Geo<T, WENO5_C4, TX, TY>;
+  constexpr int H = G::H, W = G::W, HH = G::HH, SW = G::BW, XO = G::XO, NT = TX * TY;
+  constexpr int LSX = G::LSX, LSY = G::LSY, NIX = TX + 1, NIY = TY + 1;
+  T* spx = split;                    // [4 NP][LSX]: (row, point)
+  T* spy = split + 4 * NP * LSX;     // [4 NP][LSY]: (point, column)
+  // 1. flux splitting g+- = (g +- U)/2
+  for (int k = tid; k < NP * (LSX + LSY); k += NT) {
+    if (k < NP * LSX) {
+      const int pr = k / LSX, r = k - pr * LSX, line = r / W, pt = r - line * W;
+      const int o = (H + line) * SW + XO + pt;
+      const T* gp = pick<NP>(gx, pr);
+      const T gv = ((NEGX >> pr) & 1u) ? -gp[o] : gp[o];
+      const T uv = pick<NP>(ux, pr)[o];
+      const T hg = T(0.5) * gv;
+      spx[(4 * pr + 0) * LSX + r] = hg + T(0.5) * uv;
+      spx[(4 * pr + 1) * LSX + r] = hg - T(0.5) * uv;
+    } else {
+      const int kk = k - NP * LSX;
+      const int pr = kk / LSY, r = kk - pr * LSY, pt = r / TX, line = r - pt * TX;
+      const int o = pt * SW + XO + H + line;
+      const T* gp = pick<NP>(gy, pr);
+      const T gv = ((NEGY >> pr) & 1u) ? -gp[o] : gp[o];
+      const T uv = pick<NP>(uy, pr)[o];
+      const T hg = T(0.5) * gv;
+      spy[(4 * pr + 0) * LSY + r] = hg + T(0.5) * uv;
+      spy[(4 * pr + 1) * LSY + r] = hg - T(0.5) * uv;
+    }
+  }
+  __syncthreads();
+  // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W
+  const T ew4 = T(4) * ew;
+  for (int k = tid; k < 2 * NP * (LSX + LSY); k += NT) {
+    if (k < 2 * NP * LSX) {
+      const int q = k / LSX, r = k - q * LSX, line = r / W, pt = r - line * W;
+      if (pt == 0 || pt == W - 1) continue;
+      const int pr = q >> 1, pm = q & 1;
+      const T* f = spx + (4 * pr + pm) * LSX + r;
+      const T cv = f[-1] - T(2) * f[0] + f[1];
+      spx[(4 * pr + 2 + pm) * LSX + r] = T(13.0 / 3.0) * cv * cv + ew4;
+    } else {
+      const int kk = k - 2 * NP * LSX;
+      const int q = kk / LSY, r = kk - q * LSY, pt = r / TX;
+      if (pt == 0 || pt == HH - 1) continue;
+      const int pr = q >> 1, pm = q & 1;
+      const T* f = spy + (4 * pr + pm) * LSY + r;
+      const T cv = f[-TX] - T(2) * f[0] + f[TX];
+      spy[(4 * pr + 2 + pm) * LSY + r] = T(13.0 / 3.0) * cv * cv + ew4;
+    }
+  }
+  __syncthreads();
+  // 3. interface fluxes: left-biased reconstruction of g+ centred at m, right-biased of g- centred at m+1
+  for (int k = tid; k < NP * (TY * NIX + TX * NIY); k += NT) {
+    T nl, dl, nr, dr;
+    if (k < NP * TY * NIX) {
+      const int pr = k / (TY * NIX), r = k - pr * (TY * NIX), line = r / NIX, m = r - line * NIX;
+      const int base = line * W + (H - 1 + m);
+      w5_nd<T>(spx + (4 * pr + 0) * LSX + base, spx + (4 * pr + 2) * LSX + base, 1, nl, dl);
+      w5_nd<T>(spx + (4 * pr + 1) * LSX + base + 1, spx + (4 * pr + 3) * LSX + base + 1, -1, nr, dr);
+      fx[pr * TY * NIX + line * NIX + m] = combine<T>(nl, dl, nr, dr);
+    } else {
+      const int kk = k - NP * TY * NIX;
+      const int pr = kk / (TX * NIY), r = kk - pr * (TX * NIY), m = r / TX, line = r - m * TX;
+      const int base = (H - 1 + m) * TX + line;
+      w5_nd<T>(spy + (4 * pr + 0) * LSY + base, spy + (4 * pr + 2) * LSY + base, TX, nl, dl);
+      w5_nd<T>(spy + (4 * pr + 1) * LSY + base + TX, spy + (4 * pr + 3) * LSY + base + TX, -TX, nr, dr);
+      fy[pr * TX * NIY + m * TX + line] = combine<T>(nl, dl, nr, dr);
+    }
+  }
+}
+
 // Fluxes of both axes for NP pairs: x-axis pairs (gx, ux) into fx [NP][TY][TX+1],
 // y-axis pairs (gy, uy) into fy [NP][TY+1][TX].
-template <typename T, int SCHEME, int TX, int TY, int NP, unsigned NEGX, unsigned NEGY>
+template <typename T, int SCHEME, int TX, int TY, int NP, unsigned NEGX, unsigned NEGY, bool MERGE = false>
 __device__ __forceinline__ void both_axes(const T* const* gx, const T* const* ux, const T* const* gy, const T* const* uy,
                                           T* split, T* fx, T* fy, T ew, int tid) {
   if constexpr (std::is_same<T, float>::value && SCHEME == WENO5_C4) {
@@ -459,6 +565,8 @@ __device__ __forceinline__ void both_axes(const T* const* gx, const T* const* ux
       py[k].p = uy[k];
     }
     w5_runs_both_axes<TX, TY, NP, NEGX, NEGY>(gx, px, gy, py, fx, fy, ew, tid);
+  } else if constexpr (MERGE && SCHEME == WENO5_C4) {
+    w5_fluxes_xy<T, TX, TY, NP, NEGX, NEGY>(gx, ux, gy, uy, split, fx, fy, ew, tid);
   } else {
     axis_fluxes<T, SCHEME, TX, TY, NP, NEGX, 0>(gx, ux, split, fx, ew, tid);
     __syncthreads();
@@ -501,7 +609,7 @@ struct StencilSmem {
   static constexpr size_t plane_bytes = sizeof(T) * G::PL;
   static constexpr size_t explicit_bytes = 128 + sizeof(T) * (2 * 6 * G::PL + G::EXPLICIT_EXTRA);
   static constexpr size_t rhs_bytes = 128 + sizeof(T) * (2 * 2 * G::PL) + sizeof(double) * G::RHS_EXTRA;
-  static constexpr size_t update_fixed_bytes = 128 + sizeof(T) * G::UPDATE_EXTRA;   // + 2 * np * plane_bytes
+  static constexpr size_t update_fixed_bytes = 128 + sizeof(T) * G::UPDATE_EXTRA;   // + NBUF_U * np * plane_bytes
 };
 
 template <typename T>
@@ -736,15 +844,15 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
   const PlaneList pr = update_planes(b, i);
   const int np = pr.n;
   T* stage = aligned_smem<T>(smem_raw);    // 2 x np planes
-  T* sp1 = stage + 2 * np * PL;            // dissipation partner (not with register runs)
+  T* sp1 = stage + G::NBUF_U * np * PL;    // dissipation partner (not with register runs)
   T* sp2 = sp1 + PL;
   T* split = G::RUNS ? sp1 : sp2 + PL;     // 2 pairs
-  T* fx = split + 2 * G::SPLIT_PER_PAIR;   // [2][NX]: (-v1;p1), (v2;p2)
+  T* fx = split + 2 * G::SPLIT_U_PER_PAIR; // [2][NX]: (-v1;p1), (v2;p2)
   T* fy = fx + 2 * NX;                     // [2][NY]: (v2;p1), (v1;p2)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * TX;
   const T ew = T(weno_eps);
   const unsigned mwp = b.m_wp[i], mim = b.m_im[i];
-  tile_loop<T, G, TX, TY>(b, pr, stage, bars, tid, [&](const InstDev& I, const TileRef& t, T* s) {
+  tile_loop<T, G, TX, TY, G::NBUF_U>(b, pr, stage, bars, tid, [&](const InstDev& I, const TileRef& t, T* s) {
     const T* sth = s;
     const T* sv1 = s + PL;
     const T* sv2 = s + 2 * PL;
@@ -788,7 +896,7 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
       const T* ux[2] = {sp1, sp2};
       const T* gy[2] = {sv2, sv1};
       const T* uy[2] = {sp1, sp2};
-      both_axes<T, SCHEME, TX, TY, 2, 1u, 0u>(gx, ux, gy, uy, split, fx, fy, ew, tid);
+      both_axes<T, SCHEME, TX, TY, 2, 1u, 0u, G::MERGED>(gx, ux, gy, uy, split, fx, fy, ew, tid);
     }
     __syncthreads();
     const T idx = K.inv_dx, idy = K.inv_dy;

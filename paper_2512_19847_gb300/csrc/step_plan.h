@@ -38,7 +38,7 @@ inline int update_planes_max(const ap_dvm_params& t) {
 }
 
 inline size_t update_smem(const StencilSet& ks, const ap_dvm_params& t) {
-  return ks.update_fixed + 2 * (size_t)update_planes_max(t) * ks.plane_bytes;
+  return ks.update_fixed + (size_t)ks.nbuf * update_planes_max(t) * ks.plane_bytes;
 }
 
 // Tensor maps of the stage buffers of one instance for TMA staging: map j
