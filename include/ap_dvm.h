@@ -54,7 +54,12 @@ enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1 };                   /* precision fo
 #define AP_DVM_MAX_STAGES 4
 
 /* Parameters of one solve.
- *  nx, ny      cells per direction, powers of two in [8, 4096].
+ *  nx, ny      cells per direction, in [8, 4096].  Any size: an axis whose
+ *              length is not a power of two takes its Helmholtz transforms
+ *              by Bluestein's chirp-z identity with a power-of-two length
+ *              M >= 2n - 1, and the stencil tiles at the high edges of the
+ *              grid may be ragged.  Grids whose rows are not a multiple of
+ *              16 bytes stage their tiles with plain loads instead of TMA.
  *  Lx, Ly      periodic domain [0,Lx) x [0,Ly), > 0 (the paper uses 2 pi).
  *  velocity_set  AP_DVM_D2V6 (the only set of Sec. 2.1).
  *  eps         Knudsen / scaling parameter epsilon >= 0 (eps = 0 is the exact
@@ -122,7 +127,9 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
                                   void* cuda_stream, ap_dvm_handle** out);
 /* Attach a solve to slot 0 <= slot < capacity with its own workspace of
  * ap_dvm_instance_workspace_size(p) bytes.  p must share the template's
- * scheme, precision and tableau; nx <= tmpl->nx, ny <= tmpl->ny.  Must not be
+ * scheme, precision and tableau; nx <= tmpl->nx, ny <= tmpl->ny, and its
+ * transform lengths (n, or M for a size that is not a power of two) must not
+ * exceed the template's longest (AP_DVM_ERR_ARG otherwise).  Must not be
  * called while the handle's stream is being captured. */
 ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, void* d_workspace, size_t bytes);
 /* Remove a solve from the batch; its workspace may be reused once the stream
@@ -199,13 +206,15 @@ ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, do
  * code running under a host framework that owns every device allocation,
  * real-time loops that forbid allocation after start-up, or plugins loaded
  * into a process whose allocator they may not touch.
- *  p          parameters (FP64 form only; nx, ny <= 128 and the whole
- *             scratch of the solve <= 8 MiB: up to 3 stages at 128 x 128).
+ *  p          parameters (FP64 form only; nx, ny powers of two <= 128 and
+ *             the whole scratch of the solve <= 8 MiB: up to 3 stages at
+ *             128 x 128).
  *  d_state6   device moment state, 6 double planes (u1, u2, theta, v1, v2, q):
  *             read at the start, overwritten with the state after nsteps.
  *  cuda_stream  stream for the copies and kernels.
  * Returns AP_DVM_ERR_ARG for invalid parameters or a grid beyond the limit
- * above, AP_DVM_ERR_UNSUPPORTED for the FP32 form, AP_DVM_ERR_CUDA if a CUDA
+ * above, AP_DVM_ERR_UNSUPPORTED for the FP32 form or a size that is not a
+ * power of two, AP_DVM_ERR_CUDA if a CUDA
  * call fails.  The scratch is one 8 MiB file-scope device array that every
  * GPU which loads this library holds until the process exits.  The first
  * call on a device looks up that array's address (set-up), so make it before

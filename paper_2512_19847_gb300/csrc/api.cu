@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -70,6 +71,7 @@ struct ap_dvm_handle {
   StencilSet ks{};
   MiscSet km{};
   int grid_explicit = 0, grid_rhs = 0, grid_update = 0, grid_fft = 0, grid_finish = 0;
+  unsigned fft_kinds = 0;   // FftKinds of the attached solves (the launches a step enqueues)
   size_t smem_update = 0;
   bool kernels_ready = false;
   // graph
@@ -109,11 +111,57 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Transform length of an axis of n cells: n for a power of two, else the
+// length of Bluestein's circular convolution, the power of two >= 2n - 1.
+int fft_length(int n) {
+  if (is_pow2(n)) return n;
+  int m = 1;
+  while (m < 2 * n - 1) m <<= 1;
+  return m;
+}
+
+// Bluestein tables of an axis of n cells (n not a power of two) with
+// convolution length m: the chirp exp(-i pi k^2 / n), k < n (k^2 reduced
+// modulo 2n before the angle is formed), and the DFT of length m of the filter
+// b_j = exp(i pi j^2 / n) for |j| < n (index j mod m), by radix-2 decimation in
+// frequency, so in bit-reversed order, scaled by 1/m.
+void bluestein_tables(int n, int m, std::vector<std::complex<long double>>& chirp,
+                      std::vector<std::complex<long double>>& filt) {
+  using CL = std::complex<long double>;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  chirp.assign(n, CL(0, 0));
+  for (int k = 0; k < n; ++k) {
+    const long long r = ((long long)k * k) % (2LL * n);
+    const long double a = pi * (long double)r / (long double)n;
+    chirp[k] = CL(std::cos(a), -std::sin(a));
+  }
+  filt.assign(m, CL(0, 0));
+  for (int j = 0; j < n; ++j) {
+    filt[j] = std::conj(chirp[j]);
+    if (j > 0) filt[m - j] = std::conj(chirp[j]);
+  }
+  std::vector<CL> tw(m / 2);
+  for (int k = 0; k < m / 2; ++k) {
+    const long double a = -2.0L * pi * (long double)k / (long double)m;
+    tw[k] = CL(std::cos(a), std::sin(a));
+  }
+  for (int len = m; len >= 2; len >>= 1) {
+    const int half = len >> 1, step = m / len;
+    for (int s0 = 0; s0 < m; s0 += len)
+      for (int j = 0; j < half; ++j) {
+        const CL a = filt[s0 + j], b = filt[s0 + j + half];
+        filt[s0 + j] = a + b;
+        filt[s0 + j + half] = (a - b) * tw[(size_t)j * step];
+      }
+  }
+  for (CL& z : filt) z /= (long double)m;
+}
+
 // Validates one solve's parameters; writes a message into buf.
 ap_dvm_status validate(const ap_dvm_params* p, char* buf, size_t n) {
   if (!p) { snprintf(buf, n, "null parameters"); return AP_DVM_ERR_ARG; }
-  if (!is_pow2(p->nx) || !is_pow2(p->ny) || p->nx < 8 || p->ny < 8 || p->nx > 4096 || p->ny > 4096) {
-    snprintf(buf, n, "nx, ny must be powers of two in [8, 4096] (got %d, %d)", p->nx, p->ny);
+  if (p->nx < 8 || p->ny < 8 || p->nx > 4096 || p->ny > 4096) {
+    snprintf(buf, n, "nx, ny must be in [8, 4096] (got %d, %d)", p->nx, p->ny);
     return AP_DVM_ERR_ARG;
   }
   if (!(p->Lx > 0) || !(p->Ly > 0)) { snprintf(buf, n, "Lx, Ly must be > 0"); return AP_DVM_ERR_ARG; }
@@ -187,7 +235,13 @@ size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
   I.S = take((size_t)p.ny * I.sstride * 2 * es);
   I.lamx = reinterpret_cast<double*>(take((size_t)(p.nx / 2 + 1) * sizeof(double)));
   I.lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
-  I.th_part = reinterpret_cast<double*>(take(cells / 32 * sizeof(double)));
+  // one partial sum per tile: at most ceil(nx/8) * ceil(ny/4) tiles (the smallest tile sides)
+  I.th_part = reinterpret_cast<double*>(take((size_t)((p.nx + 7) / 8) * ((p.ny + 3) / 4) * sizeof(double)));
+  for (int a = 0; a < 2; ++a) {   // Bluestein chirp and filter of an axis that is not a power of two
+    const int na = a ? p.ny : p.nx;
+    I.chirp[a] = is_pow2(na) ? nullptr : take((size_t)na * 2 * es);
+    I.filt[a] = is_pow2(na) ? nullptr : take((size_t)fft_length(na) * 2 * es);
+  }
   I.dF = p.precision == AP_DVM_FP32_DEV ? reinterpret_cast<float*>(take(6 * cells * sizeof(float))) : nullptr;
   I.tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1));
   return align_up(off, 256);
@@ -221,6 +275,19 @@ size_t batch_bytes(int capacity, int nmax) {
   take(sizeof(float2) * (nmax / 2));
   take(sizeof(unsigned) * 4);
   return align_up(off, 256);
+}
+
+// FftKinds of the attached solves (of the template while none is attached).
+unsigned fft_kinds_of(const ap_dvm_handle* h) {
+  unsigned k = 0;
+  auto add = [&](const ap_dvm_params& p) {
+    k |= is_pow2(p.nx) ? FFT_X_POW2 : FFT_X_BS;
+    k |= is_pow2(p.ny) ? FFT_Y_POW2 : FFT_Y_BS;
+  };
+  for (const Slot& s : h->slots)
+    if (s.attached) add(s.p);
+  if (!k) add(h->tmpl);
+  return k;
 }
 
 int auto_tile(const ap_dvm_handle* h) {
@@ -267,11 +334,13 @@ ap_dvm_status prepare_kernels(ap_dvm_handle* h) {
   h->smem_update = update_smem(h->ks, h->tmpl);
   if ((st = occupancy_grid(h, h->ks.k_update, thr, h->smem_update, &h->grid_update))) return st;
   if ((st = occupancy_grid(h, h->km.k_finish, thr, 0, &h->grid_finish))) return st;
-  int g1 = 0, g2 = 0, g3 = 0;
-  if ((st = occupancy_grid(h, h->km.k_rows_fwd, 256, fft_smem(h), &g1))) return st;
-  if ((st = occupancy_grid(h, h->km.k_cols, 256, fft_smem(h), &g2))) return st;
-  if ((st = occupancy_grid(h, h->km.k_rows_inv, 256, fft_smem(h), &g3))) return st;
-  h->grid_fft = std::min(g1, std::min(g2, g3));
+  h->grid_fft = 1 << 30;
+  for (const void* fn : {h->km.k_rows_fwd, h->km.k_cols, h->km.k_rows_inv, h->km.k_rows_fwd_bs, h->km.k_cols_bs,
+                         h->km.k_rows_inv_bs}) {
+    int g = 0;
+    if ((st = occupancy_grid(h, fn, 256, fft_smem(h), &g))) return st;
+    h->grid_fft = std::min(h->grid_fft, g);
+  }
   h->kernels_ready = true;
   h->graph_valid = false;
   return AP_DVM_OK;
@@ -287,6 +356,8 @@ ap_dvm_status flush(ap_dvm_handle* h) {
   if (cs != cudaStreamCaptureStatusNone)
     return fail(h, AP_DVM_ERR_ARG, "the set of solves changed while the stream is being captured");
   const int TX = h->ks.tx, TY = h->ks.ty;
+  const unsigned kinds = fft_kinds_of(h);
+  if (kinds != h->fft_kinds) { h->fft_kinds = kinds; h->graph_valid = false; }   // the launch sequence changed
   h->up_inst.clear();
   h->up_tiles.assign(1, 0);
   h->up_rows.assign(1, 0);
@@ -295,18 +366,19 @@ ap_dvm_status flush(ap_dvm_handle* h) {
     if (!s.attached) continue;
     if (s.p.nx < TX || s.p.ny < TY) return fail(h, AP_DVM_ERR_ARG, "grid %dx%d smaller than the tile %dx%d", s.p.nx, s.p.ny, TX, TY);
     InstDev d = s.dev;
-    d.tiles_x = s.p.nx / TX;
-    d.tiles_y = s.p.ny / TY;
+    d.tiles_x = (s.p.nx + TX - 1) / TX;   // ragged tiles at the high edges
+    d.tiles_y = (s.p.ny + TY - 1) / TY;
     // tensor maps of the stage buffers for the current tile shape (TMA staging)
     d.tma = encode_stage_maps(s.p, d, h->ks.bw, h->ks.bh, s.maps);
     if (d.tma)
       CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.tmap), &s.maps[0], sizeof(CUtensorMap) * (APD_MAXS + 1),
                                   cudaMemcpyHostToDevice, h->stream));
-    d.row_pairs = std::max(1, std::min(h->eblk / s.p.nx, s.p.ny / 2));
-    d.col_group = std::max(1, h->eblk / s.p.ny);
+    const int pairs = (s.p.ny + 1) / 2;   // row pairs (the last one single when ny is odd)
+    d.row_pairs = std::max(1, std::min(h->eblk >> d.lnx, pairs));
+    d.col_group = std::max(1, h->eblk >> d.lny);
     h->up_inst.push_back(d);
     h->up_tiles.push_back(h->up_tiles.back() + d.tiles_x * d.tiles_y);
-    h->up_rows.push_back(h->up_rows.back() + (s.p.ny / 2 + d.row_pairs - 1) / d.row_pairs);
+    h->up_rows.push_back(h->up_rows.back() + (pairs + d.row_pairs - 1) / d.row_pairs);
     h->up_cols.push_back(h->up_cols.back() + (s.p.nx / 2 + 1 + d.col_group - 1) / d.col_group);
   }
   const int n = (int)h->up_inst.size();
@@ -370,7 +442,7 @@ ap_dvm_status profile_collect(ap_dvm_handle* h) {
 // Kernels of one IMEX step for all attached solves (see the file header).
 ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream) {
   StepKernels K{h->ks, h->km, h->grid_explicit, h->grid_rhs, h->grid_update, h->grid_finish, h->grid_fft, fft_smem(h),
-                h->smem_update};
+                h->smem_update, h->fft_kinds};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int kind) -> int {
     return (int)launch(h, stream, fn, grid, block, smem, args, kind);
   };
@@ -442,7 +514,7 @@ size_t ap_dvm_instance_workspace_size(const ap_dvm_params* p) {
 size_t ap_dvm_batch_workspace_size(const ap_dvm_params* tmpl, int capacity) {
   char buf[256];
   if (capacity < 1 || validate(tmpl, buf, sizeof(buf)) != AP_DVM_OK) return 0;
-  return batch_bytes(capacity, std::max(tmpl->nx, tmpl->ny));
+  return batch_bytes(capacity, std::max(fft_length(tmpl->nx), fft_length(tmpl->ny)));
 }
 
 size_t ap_dvm_workspace_size(const ap_dvm_params* p) {
@@ -464,7 +536,7 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   h->capacity = capacity;
   h->f32 = tmpl->precision == AP_DVM_FP32_DEV;
   h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
-  h->nmax = std::max(tmpl->nx, tmpl->ny);
+  h->nmax = std::max(fft_length(tmpl->nx), fft_length(tmpl->ny));   // longest transform of the batch
   h->lnmax = ilog2(h->nmax);
   h->eblk = std::max(2048, h->nmax);
   const size_t need = batch_bytes(capacity, h->nmax);
@@ -527,6 +599,9 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   if (st) return st;
   if (!same_method(*p, h->tmpl)) return fail(h, AP_DVM_ERR_ARG, "scheme, precision and tableau must match the batch");
   if (p->nx > h->tmpl.nx || p->ny > h->tmpl.ny) return fail(h, AP_DVM_ERR_ARG, "grid larger than the batch template");
+  if (std::max(fft_length(p->nx), fft_length(p->ny)) > h->nmax)
+    return fail(h, AP_DVM_ERR_ARG, "grid %dx%d needs transforms of length %d, longer than the batch's %d", p->nx, p->ny,
+                std::max(fft_length(p->nx), fft_length(p->ny)), h->nmax);
   const size_t need = carve_instance(*p, nullptr, nullptr);
   if (!d_workspace || bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
     return fail(h, AP_DVM_ERR_WORKSPACE, "instance workspace needs %zu bytes, 256-byte aligned (got %zu)", need, bytes);
@@ -537,7 +612,7 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   s.bytes = bytes;
   InstDev& d = s.dev;
   carve_instance(*p, s.ws, &d);
-  d.nx = p->nx; d.ny = p->ny; d.lnx = ilog2(p->nx); d.lny = ilog2(p->ny);
+  d.nx = p->nx; d.ny = p->ny; d.lnx = ilog2(fft_length(p->nx)); d.lny = ilog2(fft_length(p->ny));
   fill_constants(*p, d);
   d.relax64 = (p->precision == AP_DVM_FP32_DEV && p->eps <= 1e-4) ? 1 : 0;
   std::vector<double> lx(p->nx / 2 + 1), ly(p->ny);
@@ -545,7 +620,30 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   laplacian_symbol(p->ny, d.dy, p->space_scheme, ly.data(), (int)ly.size());
   CUDA_TRY(h, cudaMemcpyAsync(d.lamx, lx.data(), sizeof(double) * lx.size(), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(d.lamy, ly.data(), sizeof(double) * ly.size(), cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));   // the symbol vectors are about to go out of scope
+  std::vector<double2> tab64[2];
+  std::vector<float2> tab32[2];
+  for (int a = 0; a < 2; ++a) {
+    const int na = a ? p->ny : p->nx;
+    if (is_pow2(na)) continue;
+    std::vector<std::complex<long double>> ch, fl;
+    bluestein_tables(na, fft_length(na), ch, fl);
+    for (const auto* v : {&ch, &fl}) {
+      for (const auto& z : *v) {
+        tab64[a].push_back(make_double2((double)z.real(), (double)z.imag()));
+        tab32[a].push_back(make_float2((float)z.real(), (float)z.imag()));
+      }
+    }
+    // chirp (na values) then filter (fft_length(na) values), in the batch's complex type
+    const size_t nc = ch.size(), nf = fl.size();
+    if (h->f32) {
+      CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.chirp[a]), tab32[a].data(), sizeof(float2) * nc, cudaMemcpyHostToDevice, h->stream));
+      CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.filt[a]), tab32[a].data() + nc, sizeof(float2) * nf, cudaMemcpyHostToDevice, h->stream));
+    } else {
+      CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.chirp[a]), tab64[a].data(), sizeof(double2) * nc, cudaMemcpyHostToDevice, h->stream));
+      CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.filt[a]), tab64[a].data() + nc, sizeof(double2) * nf, cudaMemcpyHostToDevice, h->stream));
+    }
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));   // the symbol and Bluestein vectors are about to go out of scope
   CUDA_TRY(h, cudaMemsetAsync(d.X, 0, (size_t)6 * p->nx * p->ny * (h->f32 ? 4 : 8), h->stream));
   if (d.dF) CUDA_TRY(h, cudaMemsetAsync(d.dF, 0, (size_t)6 * p->nx * p->ny * sizeof(float), h->stream));
   s.attached = true;
@@ -727,7 +825,8 @@ int ap_dvm_get_tile(const ap_dvm_handle* h) { return h ? h->tile : -1; }
 int ap_dvm_launches_per_step(const ap_dvm_handle* h) {
   if (!h) return 0;
   const ap_dvm_params& t = h->tmpl;
-  return t.A_im[0] != 0.0 ? 1 + 5 + 6 * (t.s - 1) + 1 : 6 * (t.s - 1) + 1;
+  const int f = fft_launches(fft_kinds_of(h));   // transform launches per implicit stage
+  return t.A_im[0] != 0.0 ? 1 + (2 + f) + (3 + f) * (t.s - 1) + 1 : (3 + f) * (t.s - 1) + 1;
 }
 
 ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage, int nsteps) {

@@ -52,7 +52,9 @@ struct Coef {
 // untyped: the scalar type is the batch's transport type T (double for the
 // FP64 form, float for the FP32-deviation form).
 struct InstDev {
-  int nx, ny, lnx, lny;         // sizes and their log2
+  int nx, ny;                   // cells per direction (any sizes; tiles at the high edges may be ragged)
+  int lnx, lny;                 // log2 of the transform length per axis: n for a power of two,
+                                // else Bluestein's convolution length M (a power of two >= 2n - 1)
   int tiles_x, tiles_y;         // tile grid for the batch's tile shape
   int row_pairs;                // row pairs per row-FFT work item
   int col_group;                // spectral columns per column-FFT work item
@@ -83,8 +85,12 @@ struct InstDev {
   void* S;                      // half spectrum, complex T, ny rows x sstride
   double* lamx;                 // 1D Laplacian symbol in x, kx = 0..nx/2
   double* lamy;                 // 1D Laplacian symbol in y, ky = 0..ny-1
-  double* th_part;              // per-tile partial sums of theta^n
+  double* th_part;              // per-tile partial sums of theta^n (ceil(nx/8) * ceil(ny/4) entries)
   float* dF;                    // FP32 form: deviation populations (6 planes)
+  const void* chirp[2];         // axes whose n is not a power of two (x, y): exp(-i pi m^2 / n), m < n,
+                                // complex T; null for a power of two
+  const void* filt[2];          // ... and the DFT of length M of the chirp filter exp(i pi m^2 / n),
+                                // |m| < n, in bit-reversed order and scaled by 1/M, complex T
   const void* tmap;             // tensor maps (128 B each) of the stage buffers Xs[j]
   int tma;                      // 1: tile loads through the tensor maps; 0: plain loads
   int pad1;
@@ -182,5 +188,13 @@ __device__ __forceinline__ T cdiff2(const T* f, int st, T inv_h2) {
 }
 
 template <typename T> __device__ __forceinline__ T* P(void* p, size_t k, size_t plane) { return reinterpret_cast<T*>(p) + k * plane; }
+
+// Periodic image of index g on a line of n cells, for g >= -n (any g a tile or
+// stencil reaches: at most a tile width plus the halo past the last cell).
+__device__ __forceinline__ int wrap_index(int g, int n) {
+  if (g < 0) return g + n;
+  while (g >= n) g -= n;
+  return g;
+}
 
 }  // namespace apd

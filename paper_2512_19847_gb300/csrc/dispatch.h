@@ -23,9 +23,12 @@ struct StencilSet {
 struct MiscSet {
   const void* k_finish;    // per tile shape
   const void* k_stage1;    // per tile shape; type-A tableaux only
-  const void* k_rows_fwd;
+  const void* k_rows_fwd;    // Helmholtz transforms, power-of-two axes ...
   const void* k_cols;
   const void* k_rows_inv;
+  const void* k_rows_fwd_bs; // ... and axes of other lengths (Bluestein)
+  const void* k_cols_bs;
+  const void* k_rows_inv_bs;
   const void* k_set_state;
   const void* k_get_state;
   const void* k_diagnostics;

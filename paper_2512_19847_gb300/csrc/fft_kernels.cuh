@@ -11,7 +11,19 @@
 //   k_fft_rows_inv : inverse real row DFTs into theta^(i).
 // Radix-2 in shared memory: decimation in time from bit-reversed order for
 // the forward transforms, decimation in frequency (natural in, bit-reversed
-// out) for the inverse ones, so no permutation pass is needed.
+// out) for the inverse ones, so no permutation pass is needed.  An axis whose
+// length n is not a power of two is transformed by Bluestein's chirp-z
+// identity (L. I. Bluestein, 1970): with w_m = exp(i pi m^2 / n) and
+// jk = (j^2 + k^2 - (k - j)^2) / 2,
+//     sum_j x_j exp(-2 pi i jk / n) = conj(w_k) sum_j (x_j conj(w_j)) w_{k-j},
+// a circular convolution of length M, the power of two >= 2n - 1, taken with
+// two radix-2 transforms of length M and the precomputed DFT of the filter
+// (w_m for |m| < n); the inverse transform conjugates chirp and filter.  A
+// row or spectral column then occupies M complex values in shared memory.
+// Each pass has a power-of-two kernel and a Bluestein kernel (suffix _bs);
+// each takes the work items of its kind and skips the others, and a step
+// launches only the kinds its batch holds.  When ny is odd, the last row pair
+// holds one row (its partner is zero).
 #pragma once
 #include "common.cuh"
 
@@ -151,6 +163,42 @@ __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int n
   }
 }
 
+// Circular convolution of ntr sequences of length M = 2^lm held back to back
+// in x[] (natural order, zero beyond n) with the Bluestein filter whose DFT is
+// filt (bit-reversed order, scaled by 1/M; conjugated when inv): forward
+// radix-2 DFT (natural in, bit-reversed out), product with the filter,
+// inverse DFT (bit-reversed in, natural out).
+template <typename T>
+__device__ __forceinline__ void bluestein_conv(typename Cplx<T>::type* x, int lm, int ntr,
+                                               const typename Cplx<T>::type* __restrict__ filt,
+                                               const typename Cplx<T>::type* __restrict__ tw, int lnmax, bool inv,
+                                               int tid, int nthr) {
+  fft_dif<T>(x, lm, ntr, tw, lnmax, false, tid, nthr);
+  const int m = 1 << lm;
+  for (int e = tid; e < ntr * m; e += nthr) x[e] = cmul_tw(filt[e & (m - 1)], x[e], inv);
+  __syncthreads();
+  fft_dit<T>(x, lm, ntr, tw, lnmax, true, tid, nthr);
+}
+
+// mean(theta^n) of instance I from its per-tile partial sums, in a fixed order,
+// into *mean (shared); every thread of the block calls it.
+__device__ __forceinline__ void theta_mean(const InstDev& I, double* red, double* mean, int tid, int nthr) {
+  const int nt = I.tiles_x * I.tiles_y;
+  double acc = 0.0;
+  for (int k = tid; k < nt; k += nthr) acc += I.th_part[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (nthr + 31) / 32; ++w) sum += red[w];
+    *mean = sum / ((double)I.nx * (double)I.ny);
+  }
+  __syncthreads();
+}
+
+// ---- power-of-two axes
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
   using C = typename Cplx<T>::type;
@@ -161,14 +209,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd(co
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k_inst = find_inst(b.row_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
-    const int n = I.nx, ln = I.lnx, ss = I.sstride;
+    if (I.chirp[0]) continue;                       // a Bluestein item
+    const int n = I.nx, ny = I.ny, ln = I.lnx, ss = I.sstride;
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
-    const int ntr = min(I.row_pairs, (I.ny >> 1) - pair0);
+    const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
     const T* R = reinterpret_cast<const T*>(I.R);
     for (int e = tid; e < ntr * n; e += nthr) {
       const int p = e >> ln, k = e & (n - 1);
       const size_t row = (size_t)(2 * (pair0 + p));
-      C z; z.x = R[row * n + k]; z.y = R[(row + 1) * n + k];
+      C z; z.x = R[row * n + k]; z.y = row + 1 < (size_t)ny ? R[(row + 1) * n + k] : T(0);
       x[p * n + brev(k, ln)] = z;
     }
     __syncthreads();
@@ -183,7 +232,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd(co
       A.x = T(0.5) * (zk.x + zm.x); A.y = T(0.5) * (zk.y - zm.y);
       B.x = T(0.5) * (zk.y + zm.y); B.y = T(-0.5) * (zk.x - zm.x);
       S[row * ss + k] = A;
-      S[(row + 1) * ss + k] = B;
+      if (row + 1 < (size_t)ny) S[(row + 1) * ss + k] = B;
     }
     __syncthreads();
   }
@@ -201,24 +250,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 4) k_fft_cols(const 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k_inst = find_inst(b.col_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
+    if (I.chirp[1]) continue;                       // a Bluestein item
     const int n = I.ny, ln = I.lny, ss = I.sstride, nh = (I.nx >> 1) + 1;
     const int col0 = (it - b.col_start[k_inst]) * I.col_group;
     const int ntr = min(I.col_group, nh - col0);
-    if (col0 == 0) {
-      // mean(theta^n) from the per-tile partial sums, in a fixed order
-      const int nt = I.tiles_x * I.tiles_y;
-      double acc = 0.0;
-      for (int k = tid; k < nt; k += nthr) acc += I.th_part[k];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if ((tid & 31) == 0) red[tid >> 5] = acc;
-      __syncthreads();
-      if (tid == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < (nthr + 31) / 32; ++w) sum += red[w];
-        s_mean = sum / ((double)I.nx * (double)I.ny);
-      }
-      __syncthreads();
-    }
+    if (col0 == 0) theta_mean(I, red, &s_mean, tid, nthr);
     C* S = reinterpret_cast<C*>(I.S);
     for (int e = tid; e < ntr * n; e += nthr) {
       const int g = e >> ln, y = e & (n - 1);
@@ -262,18 +298,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_inv(co
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k_inst = find_inst(b.row_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
-    const int n = I.nx, ln = I.lnx, ss = I.sstride;
+    if (I.chirp[0]) continue;                       // a Bluestein item
+    const int n = I.nx, ny = I.ny, ln = I.lnx, ss = I.sstride;
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
-    const int ntr = min(I.row_pairs, (I.ny >> 1) - pair0);
+    const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
     const C* S = reinterpret_cast<const C*>(I.S);
     for (int e = tid; e < ntr * n; e += nthr) {
       const int p = e >> ln, k = e & (n - 1);
       const size_t row = (size_t)(2 * (pair0 + p));
+      const bool two = row + 1 < (size_t)ny;
       C A, B;
+      B.x = B.y = T(0);
       if (k <= (n >> 1)) {
-        A = S[row * ss + k]; B = S[(row + 1) * ss + k];
+        A = S[row * ss + k];
+        if (two) B = S[(row + 1) * ss + k];
       } else {
-        A = S[row * ss + (n - k)]; B = S[(row + 1) * ss + (n - k)];
+        A = S[row * ss + (n - k)];
+        if (two) B = S[(row + 1) * ss + (n - k)];
         A.y = -A.y; B.y = -B.y;
       }
       C z; z.x = A.x - B.y; z.y = A.y + B.x;
@@ -287,7 +328,160 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_inv(co
       const size_t row = (size_t)(2 * (pair0 + p));
       const C z = x[p * n + brev(m, ln)];
       th[row * n + m] = z.x;
-      th[(row + 1) * n + m] = z.y;
+      if (row + 1 < (size_t)ny) th[(row + 1) * n + m] = z.y;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- axes whose length is not a power of two (Bluestein); x holds ntr
+// sequences of length m = 2^ln (the convolution length) back to back
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd_bs(const BatchDev* __restrict__ bp) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const BatchDev& b = *bp;
+  const int nitems = b.counts[1], tid = threadIdx.x, nthr = blockDim.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k_inst = find_inst(b.row_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const C* ch = reinterpret_cast<const C*>(I.chirp[0]);
+    if (!ch) continue;                              // a power-of-two item
+    const int n = I.nx, ny = I.ny, ln = I.lnx, m = 1 << ln, ss = I.sstride;
+    const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
+    const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
+    const T* R = reinterpret_cast<const T*>(I.R);
+    for (int e = tid; e < ntr * m; e += nthr) {
+      const int p = e >> ln, k = e & (m - 1);
+      const size_t row = (size_t)(2 * (pair0 + p));
+      C z;
+      z.x = T(0); z.y = T(0);
+      if (k < n) {
+        z.x = R[row * n + k];
+        if (row + 1 < (size_t)ny) z.y = R[(row + 1) * n + k];
+        z = cmul_tw(ch[k], z, false);
+      }
+      x[e] = z;
+    }
+    __syncthreads();
+    bluestein_conv<T>(x, ln, ntr, reinterpret_cast<const C*>(I.filt[0]), twiddles<T>(b), b.lnmax, false, tid, nthr);
+    C* S = reinterpret_cast<C*>(I.S);
+    const int nh = (n >> 1) + 1;
+    for (int e = tid; e < ntr * nh; e += nthr) {
+      const int p = e / nh, k = e - p * nh, km = k == 0 ? 0 : n - k;
+      const C zk = cmul_tw(ch[k], x[p * m + k], false), zm = cmul_tw(ch[km], x[p * m + km], false);
+      const size_t row = (size_t)(2 * (pair0 + p));
+      C A, B;
+      A.x = T(0.5) * (zk.x + zm.x); A.y = T(0.5) * (zk.y - zm.y);
+      B.x = T(0.5) * (zk.y + zm.y); B.y = T(-0.5) * (zk.x - zm.x);
+      S[row * ss + k] = A;
+      if (row + 1 < (size_t)ny) S[(row + 1) * ss + k] = B;
+    }
+    __syncthreads();
+  }
+}
+
+// The forward Bluestein convolution differs from the spectrum along y by the
+// factor conj(w_ky), which the inverse transform's input chirp w_ky cancels,
+// so the division by the symbol applies to the convolution directly.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 4) k_fft_cols_bs(const BatchDev* __restrict__ bp, int i) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  __shared__ double red[8];
+  __shared__ double s_mean;
+  const BatchDev& b = *bp;
+  const int nitems = b.counts[2], tid = threadIdx.x, nthr = blockDim.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k_inst = find_inst(b.col_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const C* ch = reinterpret_cast<const C*>(I.chirp[1]);
+    if (!ch) continue;                              // a power-of-two item
+    const C* filt = reinterpret_cast<const C*>(I.filt[1]);
+    const int n = I.ny, ln = I.lny, m = 1 << ln, ss = I.sstride, nh = (I.nx >> 1) + 1;
+    const int col0 = (it - b.col_start[k_inst]) * I.col_group;
+    const int ntr = min(I.col_group, nh - col0);
+    if (col0 == 0) theta_mean(I, red, &s_mean, tid, nthr);
+    C* S = reinterpret_cast<C*>(I.S);
+    for (int e = tid; e < ntr * m; e += nthr) {
+      const int g = e >> ln, y = e & (m - 1);
+      C z;
+      z.x = T(0); z.y = T(0);
+      if (y < n) z = cmul_tw(ch[y], S[(size_t)y * ss + col0 + g], false);
+      x[e] = z;
+    }
+    __syncthreads();
+    bluestein_conv<T>(x, ln, ntr, filt, twiddles<T>(b), b.lnmax, false, tid, nthr);
+    const double kap = I.kappa[i];
+    const double scale = 1.0 / ((double)I.nx * (double)I.ny);
+    for (int e = tid; e < ntr * m; e += nthr) {
+      const int g = e >> ln, ky = e & (m - 1), kx = col0 + g;
+      C v = x[e];
+      if (ky >= n) {
+        v.x = T(0); v.y = T(0);
+      } else if (kx == 0 && ky == 0) {
+        v.x = T(s_mean); v.y = T(0);
+      } else {
+        const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
+        v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
+      }
+      x[e] = v;
+    }
+    __syncthreads();
+    bluestein_conv<T>(x, ln, ntr, filt, twiddles<T>(b), b.lnmax, true, tid, nthr);
+    for (int e = tid; e < ntr * m; e += nthr) {
+      const int g = e >> ln, y = e & (m - 1);
+      if (y < n) S[(size_t)y * ss + col0 + g] = cmul_tw(ch[y], x[e], true);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_inv_bs(const BatchDev* __restrict__ bp, int i) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const BatchDev& b = *bp;
+  const int nitems = b.counts[1], tid = threadIdx.x, nthr = blockDim.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k_inst = find_inst(b.row_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
+    const C* ch = reinterpret_cast<const C*>(I.chirp[0]);
+    if (!ch) continue;                              // a power-of-two item
+    const int n = I.nx, ny = I.ny, ln = I.lnx, m = 1 << ln, ss = I.sstride;
+    const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
+    const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
+    const C* S = reinterpret_cast<const C*>(I.S);
+    for (int e = tid; e < ntr * m; e += nthr) {
+      const int p = e >> ln, k = e & (m - 1);
+      const size_t row = (size_t)(2 * (pair0 + p));
+      const bool two = row + 1 < (size_t)ny;
+      C A, B, z;
+      A.x = A.y = B.x = B.y = z.x = z.y = T(0);
+      if (k < n) {
+        const int kk = k <= (n >> 1) ? k : n - k;   // Hermitian symmetry of a real row
+        A = S[row * ss + kk];
+        if (two) B = S[(row + 1) * ss + kk];
+        if (kk != k) { A.y = -A.y; B.y = -B.y; }
+        z.x = A.x - B.y; z.y = A.y + B.x;
+        z = cmul_tw(ch[k], z, true);
+      }
+      x[e] = z;
+    }
+    __syncthreads();
+    bluestein_conv<T>(x, ln, ntr, reinterpret_cast<const C*>(I.filt[0]), twiddles<T>(b), b.lnmax, true, tid, nthr);
+    T* th = reinterpret_cast<T*>(I.Xs[i]) + 2 * (size_t)I.nx * I.ny;
+    for (int e = tid; e < ntr * m; e += nthr) {
+      const int p = e >> ln, mm = e & (m - 1);
+      if (mm >= n) continue;
+      const size_t row = (size_t)(2 * (pair0 + p));
+      const C z = cmul_tw(ch[mm], x[e], true);
+      th[row * n + mm] = z.x;
+      if (row + 1 < (size_t)ny) th[(row + 1) * n + mm] = z.y;
     }
     __syncthreads();
   }

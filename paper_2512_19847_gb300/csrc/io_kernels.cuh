@@ -153,11 +153,11 @@ __global__ void k_get_state(InstDev I, double* __restrict__ out, double* __restr
 template <typename T>
 __global__ void __launch_bounds__(256) k_diagnostics(InstDev I, int c4, double* __restrict__ part,
                                                      double* __restrict__ vort) {
-  const int nx = I.nx, mx = nx - 1, my = I.ny - 1, lnx = I.lnx;
-  const size_t pl = (size_t)nx * I.ny;
+  const int nx = I.nx, ny = I.ny;
+  const size_t pl = (size_t)nx * ny;
   const T* u1 = reinterpret_cast<const T*>(I.X);
   const T* u2 = u1 + pl;
-  auto at = [&](const T* f, int i, int j) { return double(f[(size_t)(j & my) * nx + (i & mx)]); };
+  auto at = [&](const T* f, int i, int j) { return double(f[(size_t)wrap_index(j, ny) * nx + wrap_index(i, nx)]); };
   auto d0x = [&](const T* f, int i, int j) {
     if (c4) return (-at(f, i + 2, j) + 8.0 * at(f, i + 1, j) - 8.0 * at(f, i - 1, j) + at(f, i - 2, j)) / (12.0 * I.dx);
     return (at(f, i + 1, j) - at(f, i - 1, j)) / (2.0 * I.dx);
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_diagnostics(InstDev I, int c4, double* 
   };
   double dmax = 0.0, d2 = 0.0, w2 = 0.0;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < pl; o += (size_t)gridDim.x * blockDim.x) {
-    const int i = int(o & (size_t)mx), j = int(o >> lnx);
+    const int j = int(o / (size_t)nx), i = int(o - (size_t)j * nx);
     const double d = d0x(u1, i, j) + d0y(u2, i, j);
     const double w = d0x(u2, i, j) - d0y(u1, i, j);
     dmax = fmax(dmax, fabs(d));
@@ -209,9 +209,10 @@ __global__ void __launch_bounds__(TX* TY) k_stage1(const BatchDev* __restrict__ 
     const InstDev& I = b.inst[k_inst];
     const int tile = it - b.tile_start[k_inst];
     const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
-    const int nx = I.nx, mx = nx - 1, my = I.ny - 1;
-    const size_t pl = (size_t)nx * I.ny;
+    const int nx = I.nx, ny = I.ny;
+    const size_t pl = (size_t)nx * ny;
     const int i = txi * TX + threadIdx.x, j = tyi * TY + threadIdx.y;
+    if (i >= nx || j >= ny) continue;   // beyond the grid (ragged edge tile)
     const size_t o = (size_t)j * nx + i;
     const T* Xn = reinterpret_cast<const T*>(I.X);
     T* X1 = reinterpret_cast<T*>(I.Xs[1]);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(TX* TY) k_stage1(const BatchDev* __restrict__ 
       X1[o + 3 * pl] = coef<T>(I).r_n[1] * Xn[o + 3 * pl];
       X1[o + 4 * pl] = coef<T>(I).r_n[1] * Xn[o + 4 * pl];
     }
-    auto at = [&](int plane, int ii, int jj) { return Xn[plane * pl + (size_t)(jj & my) * nx + (ii & mx)]; };
+    auto at = [&](int plane, int ii, int jj) { return Xn[plane * pl + (size_t)wrap_index(jj, ny) * nx + wrap_index(ii, nx)]; };
     const T idx = coef<T>(I).inv_dx, idy = coef<T>(I).inv_dy;
     T dx1, dy2;
     if (c4) {
@@ -251,10 +252,13 @@ __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ 
     const int tile = it - b.tile_start[k_inst];
     const int tyi = tile / I.tiles_x, txi = tile - tyi * I.tiles_x;
     const size_t pl = (size_t)I.nx * I.ny;
-    const size_t o = (size_t)(tyi * TY + threadIdx.y) * I.nx + (txi * TX + threadIdx.x);
+    const int i = txi * TX + threadIdx.x, j = tyi * TY + threadIdx.y;
+    const size_t o = (size_t)j * I.nx + i;
     const T* Y = reinterpret_cast<const T*>(I.Xs[s]);
     bool bad = false;
-    if (f32form) {
+    if (i >= I.nx || j >= I.ny) {
+      // beyond the grid (ragged edge tile): nothing to store
+    } else if (f32form) {
       float m[6], d[6];
       for (int k = 0; k < 6; ++k) m[k] = float(Y[o + k * pl]);
       mom_to_pop<float>(m, float(I.eps), float(I.rho0), float(I.amp), d);

@@ -13,6 +13,9 @@ MiscSet make_misc() {
   m.k_rows_fwd = reinterpret_cast<const void*>(&k_fft_rows_fwd<T>);
   m.k_cols = reinterpret_cast<const void*>(&k_fft_cols<T>);
   m.k_rows_inv = reinterpret_cast<const void*>(&k_fft_rows_inv<T>);
+  m.k_rows_fwd_bs = reinterpret_cast<const void*>(&k_fft_rows_fwd_bs<T>);
+  m.k_cols_bs = reinterpret_cast<const void*>(&k_fft_cols_bs<T>);
+  m.k_rows_inv_bs = reinterpret_cast<const void*>(&k_fft_rows_inv_bs<T>);
   m.k_set_state = reinterpret_cast<const void*>(&k_set_state<T>);
   m.k_get_state = reinterpret_cast<const void*>(&k_get_state<T>);
   m.k_diagnostics = reinterpret_cast<const void*>(&k_diagnostics<T>);

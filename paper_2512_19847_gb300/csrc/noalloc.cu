@@ -119,6 +119,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   if (ap_dvm_instance_workspace_size(p) == 0) return AP_DVM_ERR_ARG;           // invalid parameters or tableau
   if (p->precision != AP_DVM_FP64) return AP_DVM_ERR_UNSUPPORTED;
   if (p->nx > 128 || p->ny > 128 || (long)p->nx * p->ny > kMaxCells) return AP_DVM_ERR_ARG;  // beyond the static scratch
+  if ((p->nx & (p->nx - 1)) || (p->ny & (p->ny - 1))) return AP_DVM_ERR_UNSUPPORTED;         // powers of two only
   const int nmax = std::max(p->nx, p->ny);
   const Layout L = layout(*p, nmax);
   if (L.total > kScratchBytes) return AP_DVM_ERR_ARG;
@@ -211,7 +212,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
 
   // the steps: the launch sequence of one IMEX step shared with the handle path
   BatchDev* bp = reinterpret_cast<BatchDev*>(base + L.batch);
-  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, fft_smem, smem_upd};
+  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, fft_smem, smem_upd, FFT_X_POW2 | FFT_Y_POW2};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int) -> int {
     return cudaLaunchKernel(fn, dim3(grid), block, args, smem, stream) == cudaSuccess ? 0 : (int)AP_DVM_ERR_CUDA;
   };

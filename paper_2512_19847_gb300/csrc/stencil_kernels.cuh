@@ -85,10 +85,12 @@ __device__ __forceinline__ TileRef decode_tile(const BatchDev& b, int it) {
 
 // Plain loads of the staged box with periodic wrap; with outside_only, only
 // the cells outside the grid (which a TMA copy fills with zero) are written.
+// A ragged tile at the high edge of the grid stages periodic images past the
+// last cell as well: its cells beyond the grid are computed but not stored.
 template <typename T, class G>
 __device__ __forceinline__ void stage_plain(const InstDev& I, const PlaneList& pr, T* dst, int x0, int y0,
                                             bool outside_only, int tid, int nthr) {
-  const int nx = I.nx, ny = I.ny, mx = nx - 1, my = ny - 1;
+  const int nx = I.nx, ny = I.ny;
   const size_t pl = (size_t)nx * ny;
   for (int k = 0; k < pr.n; ++k) {
     const T* g = reinterpret_cast<const T*>(stage_buffer(I, pr.buf(k))) + (size_t)pr.plane(k) * pl;
@@ -96,7 +98,7 @@ __device__ __forceinline__ void stage_plain(const InstDev& I, const PlaneList& p
       const int r = e / G::BW, c = e - r * G::BW;
       const int gx = x0 - 4 + c, gy = y0 - G::H + r;
       if (outside_only && gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
-      dst[k * G::PL + e] = g[(size_t)(gy & my) * nx + (gx & mx)];
+      dst[k * G::PL + e] = g[(size_t)wrap_index(gy, ny) * nx + wrap_index(gx, nx)];
     }
   }
 }
@@ -696,6 +698,7 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const 
       both_axes<T, SCHEME, TX, TY, 2, 1u, 0u>(gx, ux, gy, uy, split, fx + NX, fy + NY, ew, tid);
     }
     __syncthreads();
+    if (t.x0 + tx >= nx || t.y0 + ty >= I.ny) return;   // beyond the grid (ragged edge tile)
     const Coef<T>& K = coef<T>(I);
     const T idx = K.inv_dx, idy = K.inv_dy;
     const int c = G::C00 + ty * BW + tx;
@@ -771,7 +774,9 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     const size_t pl = (size_t)nx * I.ny;
     const Coef<T>& K = coef<T>(I);
     const T idx = K.inv_dx, idy = K.inv_dy;
-    const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
+    // cells beyond the grid (ragged edge tile) read cell 0 and store nothing
+    const bool own = t.x0 + tx < nx && t.y0 + ty < I.ny;
+    const size_t o = own ? (size_t)(t.y0 + ty) * nx + (t.x0 + tx) : 0;
     // right-hand side of the Helmholtz equation (Algorithm 1, step 2; theta-history sign per
     // reading G4), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii
     // precomputed.  Its pointwise inputs: the FP32 form loads them before the shared-memory
@@ -799,7 +804,7 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     const int c = G::C00 + ty * BW + tx;
     const T dbi = -cdiff2<T, SCHEME>(sv1 + c, 1, idx * idx) + T(2) * cdiff<T, SCHEME>(sdy + ty * WD + CH + tx, 1, idx) +
                   cdiff2<T, SCHEME>(sv1 + c, BW, idy * idy);
-    reinterpret_cast<T*>(I.DB[i])[o] = dbi;
+    if (own) reinterpret_cast<T*>(I.DB[i])[o] = dbi;
     T R;
     if constexpr (sizeof(T) == 4) {
       R = -K.kappa[i] * thn;
@@ -825,9 +830,9 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
       for (int jj = 1; jj < i; ++jj)
         if (has(mim, jj)) R = R + (theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]) * reinterpret_cast<const T*>(I.Lth[jj])[o];
     }
-    reinterpret_cast<T*>(I.R)[o] = R;
+    if (own) reinterpret_cast<T*>(I.R)[o] = R;
     if (first_stage) {
-      const double tsum = block_sum<double>(double(thn), red, tid, TX * TY);
+      const double tsum = block_sum<double>(own ? double(thn) : 0.0, red, tid, TX * TY);
       if (tid == 0) I.th_part[t.tile] = tsum;
     }
   });
@@ -899,6 +904,7 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
       both_axes<T, SCHEME, TX, TY, 2, 1u, 0u, G::MERGED>(gx, ux, gy, uy, split, fx, fy, ew, tid);
     }
     __syncthreads();
+    if (t.x0 + tx >= nx || t.y0 + ty >= I.ny) return;   // beyond the grid (ragged edge tile)
     const T idx = K.inv_dx, idy = K.inv_dy;
     const int c = G::C00 + ty * BW + tx;
     const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);

@@ -16,12 +16,22 @@ namespace apd {
 
 enum KernelKind { KK_EXPLICIT, KK_RHS, KK_ROWS_FWD, KK_COLS, KK_ROWS_INV, KK_UPDATE, KK_FINISH, KK_STAGE1 };
 
+// Kinds of Helmholtz transform work a batch holds (bits of StepKernels::fft_kinds).
+enum FftKinds { FFT_X_POW2 = 1, FFT_X_BS = 2, FFT_Y_POW2 = 4, FFT_Y_BS = 8 };
+
+// Transform launches of one implicit stage for the given kinds.
+inline int fft_launches(unsigned kinds) {
+  return 2 * (((kinds & FFT_X_POW2) ? 1 : 0) + ((kinds & FFT_X_BS) ? 1 : 0)) + ((kinds & FFT_Y_POW2) ? 1 : 0) +
+         ((kinds & FFT_Y_BS) ? 1 : 0);
+}
+
 struct StepKernels {
   StencilSet ks;
   MiscSet km;
   int g_explicit, g_rhs, g_update, g_finish, g_fft;
   size_t fft_smem;
   size_t smem_update;
+  unsigned fft_kinds;   // FftKinds present among the attached solves
 };
 
 // Planes k_update stages at its largest stage: theta, v1, v2 and u1, u2 of every
@@ -50,6 +60,8 @@ inline size_t update_smem(const StencilSet& ks, const ap_dvm_params& t) {
 inline int encode_stage_maps(const ap_dvm_params& p, const InstDev& d, int bw, int bh, CUtensorMap* out) {
   if (std::getenv("AP_DVM_NO_TMA")) return 0;
   if (p.nx < bw || p.ny < bh) return 0;
+  // a tensor map's row stride must be a multiple of 16 bytes: other widths stage with plain loads
+  if ((size_t)p.nx * (p.precision == AP_DVM_FP64 ? 8 : 4) % 16 != 0) return 0;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -110,11 +122,16 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
       if ((st = launch(K.ks.k_rhs, K.g_rhs, blk, K.ks.smem_rhs, a, KK_RHS))) return st;
     }
     {
+      // each pass: the power-of-two kernel and/or the Bluestein kernel, as the batch needs
       void* a[] = {&bp};
-      if ((st = launch(K.km.k_rows_fwd, K.g_fft, dim3(256), K.fft_smem, a, KK_ROWS_FWD))) return st;
       void* b[] = {&bp, &i};
-      if ((st = launch(K.km.k_cols, K.g_fft, dim3(256), K.fft_smem, b, KK_COLS))) return st;
-      if ((st = launch(K.km.k_rows_inv, K.g_fft, dim3(256), K.fft_smem, b, KK_ROWS_INV))) return st;
+      const unsigned kk = K.fft_kinds;
+      if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_fwd, K.g_fft, dim3(256), K.fft_smem, a, KK_ROWS_FWD))) return st;
+      if ((kk & FFT_X_BS) && (st = launch(K.km.k_rows_fwd_bs, K.g_fft, dim3(256), K.fft_smem, a, KK_ROWS_FWD))) return st;
+      if ((kk & FFT_Y_POW2) && (st = launch(K.km.k_cols, K.g_fft, dim3(256), K.fft_smem, b, KK_COLS))) return st;
+      if ((kk & FFT_Y_BS) && (st = launch(K.km.k_cols_bs, K.g_fft, dim3(256), K.fft_smem, b, KK_COLS))) return st;
+      if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_inv, K.g_fft, dim3(256), K.fft_smem, b, KK_ROWS_INV))) return st;
+      if ((kk & FFT_X_BS) && (st = launch(K.km.k_rows_inv_bs, K.g_fft, dim3(256), K.fft_smem, b, KK_ROWS_INV))) return st;
     }
     {
       void* a[] = {&bp, &i, &weno_eps};

@@ -42,8 +42,11 @@ def test_validation_without_gpu():
     from paper_2512_19847_gb300 import api, tableaux
     p = api.default_params(64, 64, eps=1e-2, dt=0.01)
     assert api.lib().ap_dvm_workspace_size(ctypes.byref(p)) > 0
-    bad = p.copy(); bad.nx = 48                      # not a power of two
-    assert api.lib().ap_dvm_workspace_size(ctypes.byref(bad)) == 0
+    g = p.copy(); g.nx, g.ny = 48, 33                # any size in [8, 4096]: Bluestein tables added
+    assert api.lib().ap_dvm_workspace_size(ctypes.byref(g)) > 0
+    for nx, ny in ((7, 64), (64, 4097), (0, 8)):
+        bad = p.copy(); bad.nx, bad.ny = nx, ny
+        assert api.lib().ap_dvm_workspace_size(ctypes.byref(bad)) == 0
     bad = p.copy(); bad.A_ex[0] = 1.0                # explicit diagonal
     assert api.lib().ap_dvm_workspace_size(ctypes.byref(bad)) == 0
     bad = p.copy(); bad.A_im[0] = -0.5               # negative a_11

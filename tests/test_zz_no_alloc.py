@@ -58,3 +58,6 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     p4.set_tableau(A_ex, A_im)                                         # 4 stages at 128^2 exceed 8 MiB
     d4 = torch.zeros((6, 128, 128), dtype=torch.float64, device="cuda")
     assert fn(ctypes.byref(p4), d4.data_ptr(), 1, stream) == 1
+    p5 = api.default_params(96, 64, eps=1e-2, dt=0.01)                 # not a power of two
+    d5 = torch.zeros((6, 64, 96), dtype=torch.float64, device="cuda")
+    assert fn(ctypes.byref(p5), d5.data_ptr(), 1, stream) == 7         # AP_DVM_ERR_UNSUPPORTED
