@@ -10,7 +10,18 @@ Each run records, every ``record_every`` steps, the diagnostics the paper plots
 and returns the final vorticity.  The time step follows the workloads' rule
 (CFL and viscous bounds) shortened so that the run ends exactly at t_end.
 
+``convergence`` is the study of Tables 1-2 (Sec. 4.1): the thick layer at
+eps = 1e-6, tau = 0, WENO3, up to t = 1 on the paper's grids of N = 33, 65,
+129, 257 points against its 513 x 513 reference, with the area-weighted L1,
+L2 and max norms of the vorticity error and their orders.  The paper does not
+say how N counts points on the periodic square; two readings are offered:
+"nodes" (N points per side including both ends of the period, so N - 1 cells
+and nested grids, compared by injection) and "cells" (N cells, not nested,
+the reference evaluated at the coarse cell centres by its trigonometric
+interpolant, exact for the band-limited part it resolves).
+
     python -m paper_2512_19847_gb300.experiments --case shear_thin --n 512 --eps 1e-6
+    python -m paper_2512_19847_gb300.experiments --table 2
 """
 from __future__ import annotations
 
@@ -20,6 +31,7 @@ import math
 import time
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 from . import api, tableaux
@@ -90,6 +102,56 @@ def run(case: str, n: int, eps: float = 1e-4, tau: float = 0.05, t_end: float | 
     return h
 
 
+def _final_vorticity(n: int, tableau, eps: float, tau: float, t_end: float, cfl: float, scheme: str,
+                     nodes: bool = False, weno_eps: float = 1e-6) -> np.ndarray:
+    u1, u2, p = W.double_shear_layer(n, inv_rho=15.0 / math.pi, nodes=nodes)
+    dt, steps = W.fixed_time_dt(t_end, W.cfl_dt(u1, u2, 2 * math.pi / n, cfl))
+    prm = api.default_params(n, n, eps=eps, dt=dt, tau=tau, space_scheme=scheme, tableau=tableau, weno_eps=weno_eps)
+    s = api.Solver(prm)
+    s.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, p)])
+    s.step(steps)
+    s.sync_status()
+    return s.diagnostics(vorticity=True)["vorticity"].cpu().numpy()
+
+
+def interpolate_periodic(f, n: int):
+    """Values at the cell centres of an n x n grid of the trigonometric interpolant
+    of f, a cell-centred field of an odd size m on the same periodic square."""
+    m = f.shape[0]
+    F = np.fft.fft2(f) / (m * m)
+    k = np.fft.fftfreq(m, d=1.0 / m)                       # -(m-1)/2 .. (m-1)/2 (m odd: no Nyquist mode)
+    s = (np.arange(n) + 0.5) * m / n - 0.5                  # coarse centres in fine index units
+    E = np.exp(2j * np.pi * np.outer(s, k) / m)             # n x m
+    return np.real(E @ F @ E.T)
+
+
+def convergence(table: int = 2, sizes=(33, 65, 129, 257), ref: int = 513, eps: float = 1e-6, tau: float = 0.0,
+                t_end: float = 1.0, cfl: float = 0.5, scheme: str = "WENO3_C4", grids: str = "nodes",
+                weno_eps: float = 1e-6) -> list[dict]:
+    """Tables 1-2 of Sec. 4.1: vorticity errors against the finest grid and their orders,
+    for the first-order (table 1) or second-order (table 2) GSA IMEX scheme; grids
+    "nodes" or "cells" (the two readings of N in the module docstring)."""
+    tab = tableaux.euler() if table == 1 else tableaux.gsa2()
+    nodes = grids == "nodes"
+    cells = (lambda n: n - 1) if nodes else (lambda n: n)
+    wref = _final_vorticity(cells(ref), tab, eps, tau, t_end, cfl, scheme, nodes, weno_eps)
+    rows, prev = [], None
+    for n in sizes:
+        w = _final_vorticity(cells(n), tab, eps, tau, t_end, cfl, scheme, nodes, weno_eps)
+        if nodes:
+            r = cells(ref) // cells(n)
+            e = w - wref[::r, ::r]
+        else:
+            e = w - interpolate_periodic(wref, n)
+        h2 = (2 * math.pi / cells(n)) ** 2
+        norms = (h2 * np.abs(e).sum(), math.sqrt(h2 * (e * e).sum()), float(np.abs(e).max()))
+        orders = [None] * 3 if prev is None else [math.log2(a / b) for a, b in zip(prev, norms)]
+        rows.append({"N": n, "L1": norms[0], "L1_order": orders[0], "L2": norms[1], "L2_order": orders[1],
+                     "Linf": norms[2], "Linf_order": orders[2]})
+        prev = norms
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--case", choices=sorted(CASES), default="shear_thick")
@@ -101,7 +163,14 @@ def main():
     ap.add_argument("--fp32", action="store_true", help="FP32 deviation form")
     ap.add_argument("--cfl", type=float, default=0.4)
     ap.add_argument("--visc", type=float, default=0.32)
+    ap.add_argument("--table", type=int, choices=(1, 2), default=None,
+                    help="run the convergence study of Table 1 or 2 instead")
+    ap.add_argument("--grids", choices=("nodes", "cells"), default="nodes")
     args = ap.parse_args()
+    if args.table:
+        for row in convergence(args.table, grids=args.grids):
+            print(json.dumps(row))
+        return
     h = run(args.case, args.n, args.eps, args.tau, args.t_end, args.every,
             api.FP32_DEV if args.fp32 else api.FP64, cfl=args.cfl, visc=args.visc)
     print(json.dumps(h.summary()))

@@ -46,15 +46,20 @@ def taylor_green(nx: int, ny: int | None = None, t: float = 0.0, nu: float = 0.0
     return u1, u2, p
 
 
-def double_shear_layer(nx: int, ny: int | None = None, inv_rho: float = 30.0, delta: float = 0.05):
+def double_shear_layer(nx: int, ny: int | None = None, inv_rho: float = 30.0, delta: float = 0.05,
+                       nodes: bool = False):
     """Double shear layer of Sec. 4.1 (thick: inv_rho = 15/pi; thin, Sec. 4.2: 50/pi).
 
     u1 = tanh(inv_rho (y - pi/2)) for y <= pi, tanh(inv_rho (3pi/2 - y)) above;
     u2 = delta sin x; pressure input p = 0 (so theta^0 = |u^0|^2/2).
+    Sampled at the cell centres, or with nodes=True at the points (i dx, j dy), so
+    that grids of 2^k cells are nested (every coarse point is a fine one).
     Returns (u1, u2, p).
     """
     ny = nx if ny is None else ny
     X, Y = cell_centres(nx, ny)
+    if nodes:
+        X, Y = X - 0.5 * TWO_PI / nx, Y - 0.5 * TWO_PI / ny
     u1 = np.where(Y <= math.pi, np.tanh(inv_rho * (Y - math.pi / 2)), np.tanh(inv_rho * (1.5 * math.pi - Y)))
     u2 = delta * np.sin(X)
     p = np.zeros_like(u1)
