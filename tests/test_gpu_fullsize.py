@@ -1,7 +1,8 @@
 """Full-size checks in the launch configuration bench.py times (automatic
-tile, one-step CUDA graph): element-wise parity with the oracle at 2048^2
-and 512^2, the FP32 deviation form's error on the 2048^2 precision workload,
-and properties that hold at any size (incompressible limit, convergence)."""
+tile, one-step CUDA graph): element-wise parity with the oracle at 2048^2,
+at the largest grids (4096^2, 4095^2) and at 512^2, the FP32 deviation
+form's error on the 2048^2 precision workload, and properties that hold at
+any size (incompressible limit, convergence)."""
 import math
 
 import numpy as np
@@ -62,6 +63,17 @@ def test_precision_workload_2048_fp32_error():
     print(f"FP32 deviation form, 2048^2 random field, 10 steps: velocity {vel:.2e}, pressure {pr:.2e}")
     assert vel <= 1e-5
     assert pr <= 1e-2
+
+
+@pytest.mark.parametrize("n", [4096, 4095])
+def test_largest_grids_fp64_parity(n):
+    """The largest grids: 4096^2 (power of two) and 4095^2 (Bluestein with M = 8192 on both
+    axes, ragged tiles, plain staging), the bench workload's parameters, one step, every cell."""
+    f = W.taylor_green(n)
+    dt = W.stable_dt(f[0], f[1], 2 * math.pi / n, 0.05)
+    got = _gpu(n, f, 1e-4, 1e-3, 0.05, dt, 1)
+    ref = _oracle(n, f, 1e-4, 0.05, dt, 1)
+    assert np.all(_rel(got, ref) <= 1e-12), _rel(got, ref)
 
 
 @pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-4, 1e-6])
