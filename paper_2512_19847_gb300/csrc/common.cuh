@@ -189,6 +189,35 @@ __device__ __forceinline__ T cdiff2(const T* f, int st, T inv_h2) {
 
 template <typename T> __device__ __forceinline__ T* P(void* p, size_t k, size_t plane) { return reinterpret_cast<T*>(p) + k * plane; }
 
+// FP32 <-> FP64 conversions on the integer pipe.  On this GPU the conversion
+// instructions issue on the FP64 pipe (2 per clock per SM), which the FP32 form
+// needs for its FP64 sums and relaxations; these rebuild the IEEE 754 binary64
+// (binary32) bit pattern with a few integer operations instead, with the same
+// result as the instruction (exact widening; narrowing rounded to nearest, ties
+// to even).  Normal numbers take the integer path; zeros, subnormals,
+// infinities and NaNs use the instruction.
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned u = __float_as_uint(x);
+  if (((u >> 23) & 0xffu) - 1u >= 254u) return double(x);
+  // exponent bias 127 -> 1023 (+896 in the exponent field), fraction 23 -> 52 bits
+  const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ float narrow_f64_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  if (((hi >> 20) & 0x7ffu) - 897u > 253u) return float(d);   // not a normal binary32 value
+  unsigned r = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+  r += ((lo & 0x1fffffffu) + 0x0fffffffu + (r & 1u)) >> 29;  // the 29 dropped bits: nearest, ties to even
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+// Conversions between the transport type T and the arithmetic type R of a closed form.
+template <typename R, typename T> __device__ __forceinline__ R widen(T x) { return R(x); }
+template <> __device__ __forceinline__ double widen<double, float>(float x) { return widen_f32(x); }
+template <typename T, typename R> __device__ __forceinline__ T narrow(R x) { return T(x); }
+template <> __device__ __forceinline__ float narrow<float, double>(double x) { return narrow_f64_rn(x); }
+
 // Periodic image of index g on a line of n cells, for g >= -n (any g a tile or
 // stencil reaches: at most a tile width plus the halo past the last cell).
 __device__ __forceinline__ int wrap_index(int g, int n) {

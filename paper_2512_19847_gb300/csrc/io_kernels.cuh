@@ -57,11 +57,11 @@ __device__ __forceinline__ void store_f32_state(const InstDev& I, size_t o, size
   double dd[6], m[6];
   for (int k = 0; k < 6; ++k) {
     I.dF[o + k * pl] = d[k];
-    dd[k] = double(d[k]);
+    dd[k] = widen_f32(d[k]);
   }
   pop_to_mom(dd, I, m);
   float* X = reinterpret_cast<float*>(I.X);
-  for (int k = 0; k < 6; ++k) X[o + k * pl] = float(m[k]);
+  for (int k = 0; k < 6; ++k) X[o + k * pl] = narrow_f64_rn(m[k]);
 }
 
 // ---- per-instance conversions (one instance, grid-stride over cells)
@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(TX* TY) k_stage1(const BatchDev* __restrict__ 
     const T* Xn = reinterpret_cast<const T*>(I.X);
     T* X1 = reinterpret_cast<T*>(I.Xs[1]);
     if (I.relax64) {
-      X1[o + 3 * pl] = T(I.k64.r_n[1] * double(Xn[o + 3 * pl]));
-      X1[o + 4 * pl] = T(I.k64.r_n[1] * double(Xn[o + 4 * pl]));
+      X1[o + 3 * pl] = narrow<T>(I.k64.r_n[1] * widen<double>(Xn[o + 3 * pl]));
+      X1[o + 4 * pl] = narrow<T>(I.k64.r_n[1] * widen<double>(Xn[o + 4 * pl]));
     } else {
       X1[o + 3 * pl] = coef<T>(I).r_n[1] * Xn[o + 3 * pl];
       X1[o + 4 * pl] = coef<T>(I).r_n[1] * Xn[o + 4 * pl];

@@ -190,3 +190,27 @@ def test_attach_rejects_longer_transforms():
     q.nx = 40
     with pytest.raises(api.ApDvmError):
         b.attach(0, q)
+
+
+def test_graph_rebuilt_when_a_new_transform_kind_attaches():
+    """A batch stepping through a captured CUDA graph with power-of-two solves only, then a
+    solve of another size attached: the graph is re-captured with the Bluestein launches and
+    every solve still equals itself alone."""
+    tmpl = api.default_params(96, 96, eps=1e-2, dt=0.01, tableau=tableaux.gsa2())
+    b = api.Batch(tmpl, capacity=2)
+    b.set_graph_steps(2)
+    q0 = tmpl.copy()
+    q0.nx, q0.ny = 64, 32
+    x0 = W.random_moment_state(64, 32, seed=50, amp=0.3)
+    b.attach(0, q0)
+    b.set_state(torch.from_numpy(x0).cuda(), slot=0)
+    b.step(2)
+    q1 = tmpl.copy()
+    q1.nx, q1.ny = 96, 40
+    x1 = W.random_moment_state(96, 40, seed=51, amp=0.3)
+    b.attach(1, q1)
+    b.set_state(torch.from_numpy(x1).cuda(), slot=1)
+    b.step(4)
+    b.sync_status()
+    assert np.array_equal(b.get_state(0).cpu().numpy(), run_gpu(q0, x0, 6, tile=b.tile))
+    assert np.array_equal(b.get_state(1).cpu().numpy(), run_gpu(q1, x1, 4, tile=b.tile))
