@@ -230,6 +230,15 @@ ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_state6, int 
  * any step since the last call produced a non-finite value; the flags are
  * then cleared. */
 ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h);
+/* Exercise the timeout path of the bounded device waits without a fault:
+ * enqueue on the handle's stream one kernel that waits, with the same bounded
+ * wait the stencil kernels use for their tile copies and a limit of wait_ns
+ * nanoseconds (in [1e3, 1e10]), on an mbarrier that nothing completes.  The
+ * wait expires, the kernel sets the handle's timeout flag and returns, so the
+ * next ap_dvm_sync_status returns AP_DVM_ERR_TIMEOUT and the context stays
+ * usable.  The paper has no counterpart: this checks the library's failure
+ * detection.  Returns AP_DVM_ERR_ARG for a limit out of range. */
+ap_dvm_status ap_dvm_check_wait_timeout(ap_dvm_handle* h, long long wait_ns);
 /* Message of the last error on this handle (never NULL). */
 const char* ap_dvm_last_error(const ap_dvm_handle* h);
 /* Release the handle (host memory and graphs); device workspaces stay with the caller. */

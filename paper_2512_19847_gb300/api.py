@@ -102,6 +102,7 @@ def lib():
         "ap_dvm_launches_per_step": (i32, [H]),
         "ap_dvm_run_host": (i32, [H, i32, vp, vp, vp, i32]),
         "ap_dvm_sync_status": (i32, [H]),
+        "ap_dvm_check_wait_timeout": (i32, [H, ctypes.c_longlong]),
         "ap_dvm_profile_enable": (i32, [H, i32]),
         "ap_dvm_profile_read": (i32, [H, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(f64),
                                       ctypes.POINTER(ctypes.c_long), i32]),
@@ -233,6 +234,11 @@ class _Handle:
 
     def sync_status(self):
         self._check(lib().ap_dvm_sync_status(self._h))
+
+    def check_wait_timeout(self, wait_ns: int):
+        """Enqueue one kernel whose bounded device wait expires after wait_ns (the next
+        sync_status raises AP_DVM_ERR_TIMEOUT)."""
+        self._check(lib().ap_dvm_check_wait_timeout(self._h, int(wait_ns)))
 
     def profile(self, enable: bool):
         """Per-kernel CUDA-event timing of the following ap_dvm_step calls."""

@@ -851,8 +851,15 @@ ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h) {
   unsigned flags = 0;
   CUDA_TRY(h, cudaMemcpy(&flags, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (flags) CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
-  if (flags & 2u) return fail(h, AP_DVM_ERR_TIMEOUT, "a bounded wait for a tile copy expired (results invalid)");
+  if (flags & 2u) return fail(h, AP_DVM_ERR_TIMEOUT, "a bounded device wait expired (results since the last check are invalid)");
   if (flags & 1u) return fail(h, AP_DVM_ERR_NONFINITE, "a step produced a non-finite value");
+  return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_check_wait_timeout(ap_dvm_handle* h, long long wait_ns) {
+  if (!h) return AP_DVM_ERR_ARG;
+  if (wait_ns < 1000 || wait_ns > 10000000000LL) return fail(h, AP_DVM_ERR_ARG, "wait_ns must be in [1e3, 1e10]");
+  CUDA_TRY(h, launch_wait_timeout(h->d_err, (unsigned long long)wait_ns, h->stream));
   return AP_DVM_OK;
 }
 

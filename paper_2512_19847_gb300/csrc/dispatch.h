@@ -1,6 +1,7 @@
 // Kernel tables shared between the instantiation units and the host API.
 #pragma once
 #include <cstddef>
+#include <cuda_runtime.h>
 
 namespace apd {
 
@@ -41,5 +42,7 @@ StencilSet stencil_f32_lf1(int tile);
 StencilSet stencil_f32_w3(int tile);
 StencilSet stencil_f32_w5(int tile);
 MiscSet misc_set(int f32form, int tile);
+// One kernel whose bounded wait expires after limit_ns (sets the timeout bit of err).
+cudaError_t launch_wait_timeout(unsigned* err, unsigned long long limit_ns, cudaStream_t stream);
 
 }  // namespace apd

@@ -2,8 +2,28 @@
 #include "dispatch.h"
 #include "fft_kernels.cuh"
 #include "io_kernels.cuh"
+#include "tma.cuh"
 
 namespace apd {
+
+// The timeout path of the bounded waits: thread 0 waits, with the stencil
+// kernels' bounded wait and the given limit, on an mbarrier that expects one
+// arrival that never comes; when the limit passes it sets the timeout bit of
+// the error flags and the kernel returns.  No copy is in flight.
+__global__ void k_wait_timeout(unsigned* err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit_ns)) atomicOr(err, 2u);
+}
+
+cudaError_t launch_wait_timeout(unsigned* err, unsigned long long limit_ns, cudaStream_t stream) {
+  k_wait_timeout<<<1, 32, 0, stream>>>(err, limit_ns);
+  return cudaGetLastError();
+}
 namespace {
 template <typename T, int TX, int TY>
 MiscSet make_misc() {

@@ -52,12 +52,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; false after the time limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Wait for the phase with the given parity to complete; false after the time
+// limit (limit_ns of the global timer).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns = kMbarWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kMbarWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 
