@@ -131,36 +131,13 @@ template <> __device__ __forceinline__ const Coef<double>& coef<double>(const In
 template <> __device__ __forceinline__ const Coef<float>& coef<float>(const InstDev& I) { return I.k32; }
 __device__ __forceinline__ bool has(unsigned mask, int j) { return (mask >> j) & 1u; }
 
-// Row-major tableau access, 1-based stage indices as in the paper.
-__device__ __forceinline__ double aex(const BatchDev& b, int i, int j) { return b.A_ex[(i - 1) * APD_MAXS + (j - 1)]; }
-__device__ __forceinline__ double aim(const BatchDev& b, int i, int j) { return b.A_im[(i - 1) * APD_MAXS + (j - 1)]; }
-
 // ---------------------------------------------------------------------------
-// Jiang-Shu WENO reconstructions at x_{i+1/2} from the left-biased stencil.
+// Jiang-Shu WENO3 reconstruction at x_{i+1/2} from the left-biased stencil.
 // The nonlinear weights alpha_k = d_k/(eps_W + beta_k)^2 are normalised with
-// a single division: multiplying every alpha_k by prod_m (eps_W + beta_m)^2
+// a single division: multiplying both alpha_k by prod_m (eps_W + beta_m)^2
 // gives alpha'_k = d_k prod_{m != k} (eps_W + beta_m)^2, the same weights.
+// (WENO5 is evaluated from per-point terms in the stencil kernels.)
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T ew) {
-  const T p0 = (T(2) * a - T(7) * b + T(11) * c) * T(1.0 / 6.0);
-  const T p1 = (-b + T(5) * c + T(2) * d) * T(1.0 / 6.0);
-  const T p2 = (T(2) * c + T(5) * d - e) * T(1.0 / 6.0);
-  const T c0 = a - T(2) * b + c, l0 = a - T(4) * b + T(3) * c;
-  const T c1 = b - T(2) * c + d, l1 = b - d;
-  const T c2 = c - T(2) * d + e, l2 = T(3) * c - T(4) * d + e;
-  const T b0 = T(13.0 / 12.0) * c0 * c0 + T(0.25) * l0 * l0;
-  const T b1 = T(13.0 / 12.0) * c1 * c1 + T(0.25) * l1 * l1;
-  const T b2 = T(13.0 / 12.0) * c2 * c2 + T(0.25) * l2 * l2;
-  T s0 = ew + b0; s0 *= s0;
-  T s1 = ew + b1; s1 *= s1;
-  T s2 = ew + b2; s2 *= s2;
-  const T w0 = T(0.1) * (s1 * s2);
-  const T w1 = T(0.6) * (s0 * s2);
-  const T w2 = T(0.3) * (s0 * s1);
-  return (w0 * p0 + w1 * p1 + w2 * p2) / (w0 + w1 + w2);
-}
-
 template <typename T>
 __device__ __forceinline__ T weno3(T a, T b, T c, T ew) {
   const T p0 = (T(3) * b - a) * T(0.5);
@@ -186,8 +163,6 @@ __device__ __forceinline__ T cdiff2(const T* f, int st, T inv_h2) {
   if (SCHEME == LF1_C2) return (f[st] - T(2) * f[0] + f[-st]) * inv_h2;
   return (-f[2 * st] + T(16) * f[st] - T(30) * f[0] + T(16) * f[-st] - f[-2 * st]) * (inv_h2 * T(1.0 / 12.0));
 }
-
-template <typename T> __device__ __forceinline__ T* P(void* p, size_t k, size_t plane) { return reinterpret_cast<T*>(p) + k * plane; }
 
 // FP32 <-> FP64 conversions on the integer pipe.  On this GPU the conversion
 // instructions issue on the FP64 pipe (2 per clock per SM), which the FP32 form

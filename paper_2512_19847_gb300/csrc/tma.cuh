@@ -62,10 +62,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
   return true;
 }
 
-__device__ __forceinline__ void tma_prefetch_map(const void* tmap) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
-}
-
 // Copy the box at (x, y, z) of the tensor described by tmap into dst, completing on bar.
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
   asm volatile(
