@@ -165,33 +165,49 @@ __device__ __forceinline__ T cdiff2(const T* f, int st, T inv_h2) {
 }
 
 // FP32 <-> FP64 conversions on the integer pipe.  On this GPU the conversion
-// instructions issue on the FP64 pipe (2 per clock per SM), which the FP32 form
-// needs for its FP64 sums and relaxations; these rebuild the IEEE 754 binary64
-// (binary32) bit pattern with a few integer operations instead, with the same
-// result as the instruction (exact widening; narrowing rounded to nearest, ties
-// to even).  Normal numbers take the integer path; zeros, subnormals,
-// infinities and NaNs use the instruction.
+// instructions issue on the FP64 pipe (2 per clock per SM); these rebuild the
+// IEEE 754 binary64 (binary32) bit pattern with integer operations and selects
+// only, for every class of input, with the instruction's result: exact
+// widening, narrowing rounded to nearest with ties to even (overflow to
+// infinity, subnormal results rounded likewise); a NaN stays a NaN.  The FP32
+// form's finish kernel, whose FP64 moment sums keep the FP64 pipe busy, uses
+// them; the stencil kernels, bound by latency rather than by that pipe, keep
+// the instructions (the integer form's extra instructions cost them more).
 __device__ __forceinline__ double widen_f32(float x) {
-  const unsigned u = __float_as_uint(x);
-  if (((u >> 23) & 0xffu) - 1u >= 254u) return double(x);
-  // exponent bias 127 -> 1023 (+896 in the exponent field), fraction 23 -> 52 bits
-  const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
-  return __hiloint2double((int)hi, (int)(u << 29));
+  const unsigned u = __float_as_uint(x), s = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  // normal: exponent bias 127 -> 1023 (+896 in the exponent field), fraction 23 -> 52 bits
+  unsigned hi = s | (((u & 0x7fffffffu) >> 3) + (896u << 20)), lo = u << 29;
+  // subnormal: m 2^-149 = 1.f 2^(p - 149), p the position of the leading bit of m
+  const unsigned p = 31u - (unsigned)__clz(m | 1u), f = (m << (23u - p)) & 0x7fffffu;
+  if (e == 0u) {
+    hi = m ? (s | ((p + 874u) << 20) | (f >> 3)) : s;
+    lo = m ? (f << 29) : 0u;
+  }
+  if (e == 0xffu) hi = s | 0x7ff00000u | (m >> 3);   // infinity or NaN (lo as above)
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ float narrow_f64_rn(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  if (((hi >> 20) & 0x7ffu) - 897u > 253u) return float(d);   // not a normal binary32 value
+  const unsigned s = hi & 0x80000000u, ea = (hi >> 20) & 0x7ffu;
+  // normal binary32 results (biased binary64 exponent 897 .. 1150): drop 29 fraction bits
   unsigned r = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
-  r += ((lo & 0x1fffffffu) + 0x0fffffffu + (r & 1u)) >> 29;  // the 29 dropped bits: nearest, ties to even
-  return __uint_as_float(r | (hi & 0x80000000u));
+  r += ((lo & 0x1fffffffu) + 0x0fffffffu + (r & 1u)) >> 29;   // nearest, ties to even (may carry to infinity)
+  // smaller: subnormal binary32 or zero, (2^52 + fraction) / 2^k rounded the same way, k = 926 - ea >= 30
+  const unsigned long long M = (1ull << 52) | ((unsigned long long)(hi & 0xfffffu) << 32) | lo;
+  const unsigned k = 926u - min(ea, 896u);
+  unsigned q = 0u;
+  if (k < 64u) {
+    const unsigned long long rem = M & ((1ull << k) - 1ull), half = 1ull << (k - 1u);
+    q = (unsigned)(M >> k);
+    q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+  }
+  unsigned out = ea >= 897u ? r : q;
+  if (ea > 1150u) out = 0x7f800000u;                                  // overflow
+  if (ea == 0x7ffu)
+    out = ((hi & 0xfffffu) | lo) ? (0x7fc00000u | ((hi & 0xfffffu) << 3) | (lo >> 29)) : 0x7f800000u;
+  return __uint_as_float(out | s);
 }
-
-// Conversions between the transport type T and the arithmetic type R of a closed form.
-template <typename R, typename T> __device__ __forceinline__ R widen(T x) { return R(x); }
-template <> __device__ __forceinline__ double widen<double, float>(float x) { return widen_f32(x); }
-template <typename T, typename R> __device__ __forceinline__ T narrow(R x) { return T(x); }
-template <> __device__ __forceinline__ float narrow<float, double>(double x) { return narrow_f64_rn(x); }
 
 // Periodic image of index g on a line of n cells, for g >= -n (any g a tile or
 // stencil reaches: at most a tile width plus the halo past the last cell).

@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(TX* TY) k_stage1(const BatchDev* __restrict__ 
     const T* Xn = reinterpret_cast<const T*>(I.X);
     T* X1 = reinterpret_cast<T*>(I.Xs[1]);
     if (I.relax64) {
-      X1[o + 3 * pl] = narrow<T>(I.k64.r_n[1] * widen<double>(Xn[o + 3 * pl]));
-      X1[o + 4 * pl] = narrow<T>(I.k64.r_n[1] * widen<double>(Xn[o + 4 * pl]));
+      X1[o + 3 * pl] = T(I.k64.r_n[1] * double(Xn[o + 3 * pl]));
+      X1[o + 4 * pl] = T(I.k64.r_n[1] * double(Xn[o + 4 * pl]));
     } else {
       X1[o + 3 * pl] = coef<T>(I).r_n[1] * Xn[o + 3 * pl];
       X1[o + 4 * pl] = coef<T>(I).r_n[1] * Xn[o + 4 * pl];

@@ -630,25 +630,25 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
                                              T ecur1, T ecur2, T vcur1, T vcur2, T& r1, T& r2) {
   const T* Xn = reinterpret_cast<const T*>(I.X);
   const Coef<R>& K = coef<R>(I);
-  R a1 = K.r_n[i] * widen<R>(Xn[o + 3 * pl]), a2 = K.r_n[i] * widen<R>(Xn[o + 4 * pl]);
+  R a1 = K.r_n[i] * R(Xn[o + 3 * pl]), a2 = K.r_n[i] * R(Xn[o + 4 * pl]);
   for (int jj = 1; jj < i; ++jj) {
     if (has(b.m_ex[i], jj)) {
       T e1, e2;
       if (jj == jcur) { e1 = ecur1; e2 = ecur2; }
       else { const T* e = reinterpret_cast<const T*>(I.E[jj]); e1 = e[o]; e2 = e[o + pl]; }
-      a1 = a1 + K.rv_e[i][jj] * widen<R>(e1);
-      a2 = a2 + K.rv_e[i][jj] * widen<R>(e2);
+      a1 = a1 + K.rv_e[i][jj] * R(e1);
+      a2 = a2 + K.rv_e[i][jj] * R(e2);
     }
     if (has(b.m_im[i], jj)) {
       T x1, x2;
       if (jj == jcur) { x1 = vcur1; x2 = vcur2; }
       else { const T* v = reinterpret_cast<const T*>(I.Xs[jj]); x1 = v[o + 3 * pl]; x2 = v[o + 4 * pl]; }
-      a1 = a1 + K.rv_v[i][jj] * widen<R>(x1);
-      a2 = a2 + K.rv_v[i][jj] * widen<R>(x2);
+      a1 = a1 + K.rv_v[i][jj] * R(x1);
+      a2 = a2 + K.rv_v[i][jj] * R(x2);
     }
   }
-  r1 = narrow<T>(a1);
-  r2 = narrow<T>(a2);
+  r1 = T(a1);
+  r2 = T(a2);
 }
 
 // ---------------------------------------------------------------------------
@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     }
     if (own) reinterpret_cast<T*>(I.R)[o] = R;
     if (first_stage) {
-      const double tsum = block_sum<double>(own ? widen<double>(thn) : 0.0, red, tid, TX * TY);
+      const double tsum = block_sum<double>(own ? double(thn) : 0.0, red, tid, TX * TY);
       if (tid == 0) I.th_part[t.tile] = tsum;
     }
   });
@@ -934,14 +934,14 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
     // step 4
     if (I.relax64) {
       const Coef<double>& K64 = I.k64;
-      double aq = K64.r_n[i] * widen<double>(Xn[o + 5 * pl]);
+      double aq = K64.r_n[i] * double(Xn[o + 5 * pl]);
       for (int jj = 1; jj <= i; ++jj) {
         if (!has(mim, jj)) continue;
-        const double dv = widen<double>((jj == i) ? dvi : reinterpret_cast<const T*>(I.Dv[jj])[o]);
+        const double dv = (jj == i) ? double(dvi) : double(reinterpret_cast<const T*>(I.Dv[jj])[o]);
         aq = aq + K64.rq_d[i][jj] * dv;
-        if (jj < i) aq = aq + K64.rv_v[i][jj] * widen<double>(reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl]);
+        if (jj < i) aq = aq + K64.rv_v[i][jj] * double(reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl]);
       }
-      out[o + 5 * pl] = narrow<T>(aq);
+      out[o + 5 * pl] = T(aq);
     } else {
       T aq = K.r_n[i] * Xn[o + 5 * pl];
       for (int jj = 1; jj <= i; ++jj) {
