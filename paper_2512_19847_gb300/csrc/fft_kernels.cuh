@@ -60,12 +60,28 @@ __device__ __forceinline__ C mul_j(C a, bool inv) {
   return r;
 }
 
+// Multiplication by the eighth roots W_8^1 = (1 - i)/sqrt2 and W_8^3 = W_8^1 W_8^2
+// (conjugated when inv), the constant twiddles inside a radix-2^3 step.
+template <typename C>
+__device__ __forceinline__ C mul_w8(C a, bool inv) {
+  using T = decltype(a.x);
+  const T r = T(0.70710678118654752440);
+  C b;
+  if (inv) { b.x = r * (a.x - a.y); b.y = r * (a.x + a.y); }
+  else { b.x = r * (a.x + a.y); b.y = r * (a.y - a.x); }
+  return b;
+}
+template <typename C>
+__device__ __forceinline__ C mul_w83(C a, bool inv) { return mul_j(mul_w8(a, inv), inv); }
+
 // ntr transforms of length n = 2^ln held back to back in x[], input in
 // bit-reversed order, output natural.  Twiddle W_m^p = tw[p * nmax/m].
-// Stages are taken two at a time (radix-2^2): each thread loads four
-// elements p0 + {0, h, 2h, 3h}, applies stage s (half h, twiddle W_{2h}^pos)
-// and stage s+1 (half 2h, twiddles W_{4h}^pos and W_{4h}^pos * W_{4h}^h) in
-// registers, and stores them; the first pair of stages has only trivial twiddles.
+// Stages are taken three at a time (radix-2^3): each thread loads eight
+// elements p0 + k h (k = 0..7, h = 2^(s-1)), applies stage s (half h, twiddle
+// W_{2h}^pos), stage s+1 (half 2h, W_{4h}^pos and W_{4h}^pos W_4) and stage s+2
+// (half 4h, W_{8h}^pos W_8^k) in registers, and stores them: one table twiddle
+// per stage, the rest constant roots.  One or two stages left over take a
+// radix-2^2 or radix-2 step; the first step has only constant twiddles.
 template <typename T>
 __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int ntr,
                                         const typename Cplx<T>::type* __restrict__ tw, int lnmax,
@@ -73,7 +89,42 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
   using C = typename Cplx<T>::type;
   const int n = 1 << ln;
   int s = 1;
-  for (; s + 1 <= ln; s += 2) {
+  for (; s + 2 <= ln; s += 3) {
+    const int h = 1 << (s - 1), ne = n >> 3, nb = ntr * ne;
+    for (int k = tid; k < nb; k += nthr) {
+      const int t = k >> (ln - 3), bi = k & (ne - 1);
+      const int pos = bi & (h - 1), grp = bi >> (s - 1);
+      C* q = x + t * n + grp * 8 * h + pos;
+      C v0 = q[0], v1 = q[h], v2 = q[2 * h], v3 = q[3 * h], v4 = q[4 * h], v5 = q[5 * h], v6 = q[6 * h], v7 = q[7 * h];
+      if (s > 1) {   // stage s: W_{2h}^pos on the odd elements
+        const C w1 = tw[pos << (lnmax - s)];
+        v1 = cmul_tw(w1, v1, inv); v3 = cmul_tw(w1, v3, inv); v5 = cmul_tw(w1, v5, inv); v7 = cmul_tw(w1, v7, inv);
+      }
+      C a0 = cadd(v0, v1), a1 = csub(v0, v1), a2 = cadd(v2, v3), a3 = csub(v2, v3);
+      C a4 = cadd(v4, v5), a5 = csub(v4, v5), a6 = cadd(v6, v7), a7 = csub(v6, v7);
+      if (s > 1) {   // stage s+1: W_{4h}^pos (and W_4 below)
+        const C w2 = tw[pos << (lnmax - s - 1)];
+        a2 = cmul_tw(w2, a2, inv); a3 = cmul_tw(w2, a3, inv); a6 = cmul_tw(w2, a6, inv); a7 = cmul_tw(w2, a7, inv);
+      }
+      a3 = mul_j(a3, inv);
+      a7 = mul_j(a7, inv);
+      C b0 = cadd(a0, a2), b2 = csub(a0, a2), b1 = cadd(a1, a3), b3 = csub(a1, a3);
+      C b4 = cadd(a4, a6), b6 = csub(a4, a6), b5 = cadd(a5, a7), b7 = csub(a5, a7);
+      if (s > 1) {   // stage s+2: W_{8h}^pos (and W_8^k below)
+        const C w3 = tw[pos << (lnmax - s - 2)];
+        b4 = cmul_tw(w3, b4, inv); b5 = cmul_tw(w3, b5, inv); b6 = cmul_tw(w3, b6, inv); b7 = cmul_tw(w3, b7, inv);
+      }
+      b5 = mul_w8(b5, inv);
+      b6 = mul_j(b6, inv);
+      b7 = mul_w83(b7, inv);
+      q[0] = cadd(b0, b4); q[4 * h] = csub(b0, b4);
+      q[h] = cadd(b1, b5); q[5 * h] = csub(b1, b5);
+      q[2 * h] = cadd(b2, b6); q[6 * h] = csub(b2, b6);
+      q[3 * h] = cadd(b3, b7); q[7 * h] = csub(b3, b7);
+    }
+    __syncthreads();
+  }
+  if (s + 1 == ln) {   // two stages left: radix-2^2
     const int h = 1 << (s - 1), nq = n >> 2, nb = ntr * nq;
     for (int k = tid; k < nb; k += nthr) {
       const int t = k >> (ln - 2), bi = k & (nq - 1);
@@ -99,8 +150,7 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
       x[p0 + 3 * h] = csub(a1, a3);
     }
     __syncthreads();
-  }
-  if (s == ln) {   // one radix-2 stage left (odd ln)
+  } else if (s == ln) {   // one stage left: radix-2
     const int half = 1 << (s - 1), sh = lnmax - s, nb = ntr * (n >> 1);
     for (int k = tid; k < nb; k += nthr) {
       const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
@@ -114,8 +164,10 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
   }
 }
 
-// Natural-order input, bit-reversed output (decimation in frequency), two
-// stages at a time as in fft_dit: stage s (half 2h) then stage s-1 (half h).
+// Natural-order input, bit-reversed output (decimation in frequency), three
+// stages at a time as in fft_dit, mirrored: stage s (half 4h, W_{8h}^pos W_8^k
+// on the differences), stage s-1 (half 2h, W_{4h}^pos and W_{4h}^pos W_4),
+// stage s-2 (half h, W_{2h}^pos), h = 2^(s-3); leftovers as radix-2^2 or radix-2.
 template <typename T>
 __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int ntr,
                                         const typename Cplx<T>::type* __restrict__ tw, int lnmax,
@@ -123,35 +175,59 @@ __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int n
   using C = typename Cplx<T>::type;
   const int n = 1 << ln;
   int s = ln;
-  for (; s >= 2; s -= 2) {
-    const int h = 1 << (s - 2), nq = n >> 2, nb = ntr * nq;
+  for (; s >= 3; s -= 3) {
+    const int h = 1 << (s - 3), ne = n >> 3, nb = ntr * ne;
     for (int k = tid; k < nb; k += nthr) {
-      const int t = k >> (ln - 2), bi = k & (nq - 1);
-      const int pos = bi & (h - 1), grp = bi >> (s - 2);
-      const int p0 = t * n + grp * 4 * h + pos;
-      const C x0 = x[p0], x1 = x[p0 + h], x2 = x[p0 + 2 * h], x3 = x[p0 + 3 * h];
-      const C b0 = cadd(x0, x2), b1 = cadd(x1, x3);
-      C b2 = csub(x0, x2), b3 = csub(x1, x3);
-      if (s > 2) {
-        const C w2 = tw[pos << (lnmax - s)];
-        b2 = cmul_tw(w2, b2, inv);
-        b3 = cmul_tw(w2, b3, inv);
+      const int t = k >> (ln - 3), bi = k & (ne - 1);
+      const int pos = bi & (h - 1), grp = bi >> (s - 3);
+      C* q = x + t * n + grp * 8 * h + pos;
+      const C v0 = q[0], v1 = q[h], v2 = q[2 * h], v3 = q[3 * h], v4 = q[4 * h], v5 = q[5 * h], v6 = q[6 * h], v7 = q[7 * h];
+      // stage s: pairs (k, k+4), differences times W_{8h}^pos W_8^k
+      C a0 = cadd(v0, v4), a1 = cadd(v1, v5), a2 = cadd(v2, v6), a3 = cadd(v3, v7);
+      C a4 = csub(v0, v4), a5 = csub(v1, v5), a6 = csub(v2, v6), a7 = csub(v3, v7);
+      a5 = mul_w8(a5, inv);
+      a6 = mul_j(a6, inv);
+      a7 = mul_w83(a7, inv);
+      if (s > 3) {
+        const C w3 = tw[pos << (lnmax - s)];
+        a4 = cmul_tw(w3, a4, inv); a5 = cmul_tw(w3, a5, inv); a6 = cmul_tw(w3, a6, inv); a7 = cmul_tw(w3, a7, inv);
       }
+      // stage s-1: pairs (k, k+2), differences times W_{4h}^pos (W_4 for the odd ones)
+      C b0 = cadd(a0, a2), b1 = cadd(a1, a3), b2 = csub(a0, a2), b3 = csub(a1, a3);
+      C b4 = cadd(a4, a6), b5 = cadd(a5, a7), b6 = csub(a4, a6), b7 = csub(a5, a7);
       b3 = mul_j(b3, inv);
-      C y1 = csub(b0, b1), y3 = csub(b2, b3);
-      if (s > 2) {
-        const C w1 = tw[pos << (lnmax - s + 1)];
-        y1 = cmul_tw(w1, y1, inv);
-        y3 = cmul_tw(w1, y3, inv);
+      b7 = mul_j(b7, inv);
+      if (s > 3) {
+        const C w2 = tw[pos << (lnmax - s + 1)];
+        b2 = cmul_tw(w2, b2, inv); b3 = cmul_tw(w2, b3, inv); b6 = cmul_tw(w2, b6, inv); b7 = cmul_tw(w2, b7, inv);
       }
-      x[p0] = cadd(b0, b1);
-      x[p0 + h] = y1;
-      x[p0 + 2 * h] = cadd(b2, b3);
-      x[p0 + 3 * h] = y3;
+      // stage s-2: pairs (k, k+1), differences times W_{2h}^pos
+      C c1 = csub(b0, b1), c3 = csub(b2, b3), c5 = csub(b4, b5), c7 = csub(b6, b7);
+      if (s > 3) {
+        const C w1 = tw[pos << (lnmax - s + 2)];
+        c1 = cmul_tw(w1, c1, inv); c3 = cmul_tw(w1, c3, inv); c5 = cmul_tw(w1, c5, inv); c7 = cmul_tw(w1, c7, inv);
+      }
+      q[0] = cadd(b0, b1); q[h] = c1;
+      q[2 * h] = cadd(b2, b3); q[3 * h] = c3;
+      q[4 * h] = cadd(b4, b5); q[5 * h] = c5;
+      q[6 * h] = cadd(b6, b7); q[7 * h] = c7;
     }
     __syncthreads();
   }
-  if (s == 1) {   // last radix-2 stage (odd ln): all twiddles are 1
+  if (s == 2) {   // two stages left: radix-2^2 with trivial table twiddles (h = 1)
+    const int nq = n >> 2, nb = ntr * nq;
+    for (int k = tid; k < nb; k += nthr) {
+      const int p0 = 4 * k;
+      const C x0 = x[p0], x1 = x[p0 + 1], x2 = x[p0 + 2], x3 = x[p0 + 3];
+      const C b0 = cadd(x0, x2), b1 = cadd(x1, x3), b2 = csub(x0, x2);
+      const C b3 = mul_j(csub(x1, x3), inv);
+      x[p0] = cadd(b0, b1);
+      x[p0 + 1] = csub(b0, b1);
+      x[p0 + 2] = cadd(b2, b3);
+      x[p0 + 3] = csub(b2, b3);
+    }
+    __syncthreads();
+  } else if (s == 1) {   // last radix-2 stage: all twiddles are 1
     const int nb = ntr * (n >> 1);
     for (int k = tid; k < nb; k += nthr) {
       const int i0 = 2 * k, i1 = i0 + 1;
@@ -200,7 +276,7 @@ __device__ __forceinline__ void theta_mean(const InstDev& I, double* red, double
 // ---- power-of-two axes
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
@@ -239,7 +315,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd(co
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 4) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
@@ -289,7 +365,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 4) k_fft_cols(const 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
@@ -338,7 +414,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_inv(co
 // sequences of length m = 2^ln (the convolution length) back to back
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd_bs(const BatchDev* __restrict__ bp) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd_bs(const BatchDev* __restrict__ bp) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
@@ -387,7 +463,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_fwd_bs
 // factor conj(w_ky), which the inverse transform's input chirp w_ky cancels,
 // so the division by the symbol applies to the convolution directly.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 4) k_fft_cols_bs(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols_bs(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
@@ -441,7 +517,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 4) k_fft_cols_bs(con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_fft_rows_inv_bs(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv_bs(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
