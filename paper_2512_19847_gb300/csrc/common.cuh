@@ -61,6 +61,7 @@ struct InstDev {
   int relax64;                  // FP32 form: closed-form relaxation in FP64
   int sstride;                  // complex elements per spectral row (>= nx/2 + 1)
   double dx, dy, dt, eps, tau, te2, rho0, amp;
+  float eps32, rho032, amp32;   // eps, rho0, amp rounded once (the FP32 form's repacking)
   double kappa[APD_MAXS + 1];   // kappa_i = 2 eps^2/(dt^2 a_ii^2), by stage i (1-based)
   double den[APD_MAXS + 1];     // tau eps^2 + dt a_ii
   double inv_den[APD_MAXS + 1]; // 1 / (tau eps^2 + dt a_ii)

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ 
     } else if (f32form) {
       float m[6], d[6];
       for (int k = 0; k < 6; ++k) m[k] = float(Y[o + k * pl]);
-      mom_to_pop<float>(m, float(I.eps), float(I.rho0), float(I.amp), d);
+      mom_to_pop<float>(m, I.eps32, I.rho032, I.amp32, d);
       for (int k = 0; k < 6; ++k) bad |= !isfinite(d[k]);
       store_f32_state(I, o, pl, d);
     } else {

@@ -206,6 +206,9 @@ inline void fill_constants(const ap_dvm_params& p, InstDev& d) {
   d.te2 = d.tau * p.eps * p.eps;
   d.rho0 = p.rho0;
   d.amp = p.mach;
+  d.eps32 = (float)p.eps;
+  d.rho032 = (float)p.rho0;
+  d.amp32 = (float)p.mach;
   for (int i = 1; i <= p.s; ++i) {
     const double a = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
     if (a == 0.0) continue;
