@@ -120,6 +120,23 @@ int fft_length(int n) {
   return m;
 }
 
+// Mixed-radix plan of an axis of n cells: the radices (4s first, then 2, 3, 5,
+// 7; 4 bits each, first pass in the low bits) when n is not a power of two and
+// has no prime factor above 7; false otherwise.
+bool mixed_radix_plan(int n, unsigned* plan, int* npass) {
+  if (is_pow2(n)) return false;
+  unsigned pl = 0;
+  int np = 0;
+  auto push = [&](int r) { pl |= (unsigned)r << (4 * np); ++np; };
+  while (n % 4 == 0) { push(4); n /= 4; }
+  for (int r : {2, 3, 5, 7})
+    while (n % r == 0) { push(r); n /= r; }
+  if (n != 1 || np > 8) return false;
+  *plan = pl;
+  *npass = np;
+  return true;
+}
+
 // Bluestein tables of an axis of n cells (n not a power of two) with
 // convolution length m: the chirp exp(-i pi k^2 / n), k < n (k^2 reduced
 // modulo 2n before the angle is formed), and the DFT of length m of the filter
@@ -237,10 +254,17 @@ size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
   I.lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
   // one partial sum per tile: at most ceil(nx/8) * ceil(ny/4) tiles (the smallest tile sides)
   I.th_part = reinterpret_cast<double*>(take((size_t)((p.nx + 7) / 8) * ((p.ny + 3) / 4) * sizeof(double)));
-  for (int a = 0; a < 2; ++a) {   // Bluestein chirp and filter of an axis that is not a power of two
+  for (int a = 0; a < 2; ++a) {   // tables of an axis that is not a power of two: mixed radix or Bluestein
     const int na = a ? p.ny : p.nx;
-    I.chirp[a] = is_pow2(na) ? nullptr : take((size_t)na * 2 * es);
-    I.filt[a] = is_pow2(na) ? nullptr : take((size_t)fft_length(na) * 2 * es);
+    unsigned plan = 0;
+    int npass = 0;
+    const bool mr = mixed_radix_plan(na, &plan, &npass);
+    I.mr_plan[a] = mr ? plan : 0u;
+    I.mr_npass[a] = mr ? npass : 0;
+    I.mr_tw[a] = mr ? take((size_t)na * 2 * es) : nullptr;
+    const bool bs = !is_pow2(na) && !mr;
+    I.chirp[a] = bs ? take((size_t)na * 2 * es) : nullptr;
+    I.filt[a] = bs ? take((size_t)fft_length(na) * 2 * es) : nullptr;
   }
   I.dF = p.precision == AP_DVM_FP32_DEV ? reinterpret_cast<float*>(take(6 * cells * sizeof(float))) : nullptr;
   I.tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1));
@@ -625,6 +649,19 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   for (int a = 0; a < 2; ++a) {
     const int na = a ? p->ny : p->nx;
     if (is_pow2(na)) continue;
+    if (d.mr_npass[a]) {   // mixed radix: W_n^q, q < n
+      const long double pi = 3.141592653589793238462643383279502884L;
+      for (int q = 0; q < na; ++q) {
+        const long double ang = -2.0L * pi * (long double)q / (long double)na;
+        tab64[a].push_back(make_double2((double)std::cos(ang), (double)std::sin(ang)));
+        tab32[a].push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+      }
+      if (h->f32)
+        CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.mr_tw[a]), tab32[a].data(), sizeof(float2) * na, cudaMemcpyHostToDevice, h->stream));
+      else
+        CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.mr_tw[a]), tab64[a].data(), sizeof(double2) * na, cudaMemcpyHostToDevice, h->stream));
+      continue;
+    }
     std::vector<std::complex<long double>> ch, fl;
     bluestein_tables(na, fft_length(na), ch, fl);
     for (const auto* v : {&ch, &fl}) {

@@ -88,8 +88,12 @@ struct InstDev {
   double* lamy;                 // 1D Laplacian symbol in y, ky = 0..ny-1
   double* th_part;              // per-tile partial sums of theta^n (ceil(nx/8) * ceil(ny/4) entries)
   float* dF;                    // FP32 form: deviation populations (6 planes)
-  const void* chirp[2];         // axes whose n is not a power of two (x, y): exp(-i pi m^2 / n), m < n,
-                                // complex T; null for a power of two
+  unsigned mr_plan[2];          // axes whose n is not a power of two but factors into 2, 3, 5, 7 (x, y):
+                                // the mixed-radix passes' radices, 4 bits each, first pass lowest
+  int mr_npass[2];              // ... their number (0: power of two, or Bluestein below)
+  const void* mr_tw[2];         // ... and W_n^q = exp(-2 pi i q / n), q < n, complex T
+  const void* chirp[2];         // other axes whose n is not a power of two: exp(-i pi m^2 / n), m < n,
+                                // complex T; null otherwise
   const void* filt[2];          // ... and the DFT of length M of the chirp filter exp(i pi m^2 / n),
                                 // |m| < n, in bit-reversed order and scaled by 1/M, complex T
   const void* tmap;             // tensor maps (128 B each) of the stage buffers Xs[j]

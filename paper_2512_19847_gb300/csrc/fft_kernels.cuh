@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd(co
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k_inst = find_inst(b.row_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
-    if (I.chirp[0]) continue;                       // a Bluestein item
+    if (I.chirp[0] || I.mr_npass[0]) continue;      // an item of another length
     const int n = I.nx, ny = I.ny, ln = I.lnx, ss = I.sstride;
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
     const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols(const 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k_inst = find_inst(b.col_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
-    if (I.chirp[1]) continue;                       // a Bluestein item
+    if (I.chirp[1] || I.mr_npass[1]) continue;      // an item of another length
     const int n = I.ny, ln = I.lny, ss = I.sstride, nh = (I.nx >> 1) + 1;
     const int col0 = (it - b.col_start[k_inst]) * I.col_group;
     const int ntr = min(I.col_group, nh - col0);
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv(co
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k_inst = find_inst(b.row_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
-    if (I.chirp[0]) continue;                       // a Bluestein item
+    if (I.chirp[0] || I.mr_npass[0]) continue;      // an item of another length
     const int n = I.nx, ny = I.ny, ln = I.lnx, ss = I.sstride;
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
     const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
@@ -410,8 +410,120 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv(co
   }
 }
 
-// ---- axes whose length is not a power of two (Bluestein); x holds ntr
-// sequences of length m = 2^ln (the convolution length) back to back
+// ---- mixed radix: lengths 2^a 3^b 5^c 7^d that are not powers of two, by
+// Stockham's self-sorting formulation (natural order in and out, ping-pong
+// between two buffers of n values).  With Ns the product of the radices of
+// the passes before, a pass of radix R takes, for each j < n/R with k = j mod Ns,
+// the R values src[j + r n/R] times W_{Ns R}^{k r}, transforms them with an
+// R-point DFT and writes them to dst[(j - k) R + k + r Ns].
+
+// cos and sin of 2 pi q / R, q = 1 .. (R-1)/2, for the odd radices.
+__device__ __forceinline__ constexpr double root_cos(int R, int q) {
+  return R == 3 ? -0.5
+       : R == 5 ? (q == 1 ? 0.3090169943749474241022934 : -0.8090169943749474241022934)
+       : (q == 1 ? 0.6234898018587335305250049 : q == 2 ? -0.2225209339563144042889026 : -0.9009688679024191262361023);
+}
+__device__ __forceinline__ constexpr double root_sin(int R, int q) {
+  return R == 3 ? 0.8660254037844386467637232
+       : R == 5 ? (q == 1 ? 0.9510565162951535721164393 : 0.5877852522924731291687060)
+       : (q == 1 ? 0.7818314824680298087084445 : q == 2 ? 0.9749279121818236070181317 : 0.4338837391175581204757683);
+}
+
+// R-point DFT of v in place (exp(-2 pi i ab/R); conjugate roots when inv).  Odd R:
+// opposite inputs are paired, y_a = v_0 + sum_b [(v_b + v_{R-b}) cos - i (v_b - v_{R-b}) sin](2 pi ab/R).
+template <int R, typename C>
+__device__ __forceinline__ void small_dft(C* v, bool inv) {
+  using T = decltype(v[0].x);
+  if constexpr (R == 2) {
+    const C a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  } else if constexpr (R == 4) {
+    const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]), t2 = cadd(v[1], v[3]), t3 = mul_j(csub(v[1], v[3]), inv);
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  } else {
+    constexpr int H = (R - 1) / 2;
+    C sp[H], dm[H], out[R];
+    C y0 = v[0];
+#pragma unroll
+    for (int b = 1; b <= H; ++b) {
+      sp[b - 1] = cadd(v[b], v[R - b]);
+      dm[b - 1] = csub(v[b], v[R - b]);
+      y0 = cadd(y0, sp[b - 1]);
+    }
+    out[0] = y0;
+#pragma unroll
+    for (int a = 1; a <= H; ++a) {
+      C re = v[0], im;
+      im.x = T(0); im.y = T(0);
+#pragma unroll
+      for (int b = 1; b <= H; ++b) {
+        const int q = (a * b) % R, qq = q <= H ? q : R - q;
+        const T c = T(root_cos(R, qq)), sn = q <= H ? T(root_sin(R, qq)) : -T(root_sin(R, qq));
+        re.x += c * sp[b - 1].x; re.y += c * sp[b - 1].y;
+        im.x += sn * dm[b - 1].x; im.y += sn * dm[b - 1].y;
+      }
+      C ya, yb;   // re -+ i im (forward), re +- i im (inverse)
+      if (!inv) { ya.x = re.x + im.y; ya.y = re.y - im.x; yb.x = re.x - im.y; yb.y = re.y + im.x; }
+      else { ya.x = re.x - im.y; ya.y = re.y + im.x; yb.x = re.x + im.y; yb.y = re.y - im.x; }
+      out[a] = ya;
+      out[R - a] = yb;
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) v[a] = out[a];
+  }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void stockham_pass(typename Cplx<T>::type* x, int m, int n, int ntr, int Ns, int src_off,
+                                              const typename Cplx<T>::type* __restrict__ tw, bool inv, int tid,
+                                              int nthr) {
+  using C = typename Cplx<T>::type;
+  const int nr = n / R, dst_off = n - src_off, tws = n / (Ns * R);
+  for (int e = tid; e < ntr * nr; e += nthr) {
+    const int p = e / nr, j = e - p * nr, k = j % Ns;
+    const C* src = x + p * m + src_off;
+    C* dst = x + p * m + dst_off;
+    C v[R];
+    v[0] = src[j];
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul_tw(tw[k * r * tws], src[j + r * nr], inv);
+    small_dft<R>(v, inv);
+    const int d0 = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[d0 + r * Ns] = v[r];
+  }
+  __syncthreads();
+}
+
+// ntr transforms of length n (plan: npass radices, 4 bits each, first pass in the
+// low bits), transform p in x + p m, starting in the buffer at offset off (0 or n);
+// returns the offset of the buffer that holds the result.  tw[q] = W_n^q, q < n.
+template <typename T>
+__device__ __forceinline__ int stockham(typename Cplx<T>::type* x, int m, int n, int ntr, unsigned plan, int npass,
+                                        const typename Cplx<T>::type* __restrict__ tw, bool inv, int off, int tid,
+                                        int nthr) {
+  int Ns = 1;
+  for (int q = 0; q < npass; ++q) {
+    const int R = (int)((plan >> (4 * q)) & 15u);
+    if (R == 4) stockham_pass<T, 4>(x, m, n, ntr, Ns, off, tw, inv, tid, nthr);
+    else if (R == 2) stockham_pass<T, 2>(x, m, n, ntr, Ns, off, tw, inv, tid, nthr);
+    else if (R == 3) stockham_pass<T, 3>(x, m, n, ntr, Ns, off, tw, inv, tid, nthr);
+    else if (R == 5) stockham_pass<T, 5>(x, m, n, ntr, Ns, off, tw, inv, tid, nthr);
+    else stockham_pass<T, 7>(x, m, n, ntr, Ns, off, tw, inv, tid, nthr);
+    off = n - off;
+    Ns *= R;
+  }
+  return off;
+}
+
+// ---- axes whose length is not a power of two: mixed radix where the length
+// factors into 2, 3, 5 and 7, else Bluestein; x holds ntr regions of m = 2^ln
+// values (the Bluestein convolution length, >= 2n: room for the two mixed-radix
+// buffers as well) back to back
 
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd_bs(const BatchDev* __restrict__ bp) {
@@ -424,11 +536,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd_bs
     const int k_inst = find_inst(b.row_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
     const C* ch = reinterpret_cast<const C*>(I.chirp[0]);
-    if (!ch) continue;                              // a power-of-two item
+    if (!ch && !I.mr_npass[0]) continue;            // a power-of-two item
     const int n = I.nx, ny = I.ny, ln = I.lnx, m = 1 << ln, ss = I.sstride;
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
     const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
     const T* R = reinterpret_cast<const T*>(I.R);
+    if (I.mr_npass[0]) {
+      for (int e = tid; e < ntr * n; e += nthr) {
+        const int p = e / n, k = e - p * n;
+        const size_t row = (size_t)(2 * (pair0 + p));
+        C z;
+        z.x = R[row * n + k];
+        z.y = row + 1 < (size_t)ny ? R[(row + 1) * n + k] : T(0);
+        x[p * m + k] = z;
+      }
+      __syncthreads();
+      const int off = stockham<T>(x, m, n, ntr, I.mr_plan[0], I.mr_npass[0], reinterpret_cast<const C*>(I.mr_tw[0]),
+                                  false, 0, tid, nthr);
+      C* S = reinterpret_cast<C*>(I.S);
+      const int nh = (n >> 1) + 1;
+      for (int e = tid; e < ntr * nh; e += nthr) {
+        const int p = e / nh, k = e - p * nh, km = k == 0 ? 0 : n - k;
+        const C zk = x[p * m + off + k], zm = x[p * m + off + km];
+        const size_t row = (size_t)(2 * (pair0 + p));
+        C A, B;
+        A.x = T(0.5) * (zk.x + zm.x); A.y = T(0.5) * (zk.y - zm.y);
+        B.x = T(0.5) * (zk.y + zm.y); B.y = T(-0.5) * (zk.x - zm.x);
+        S[row * ss + k] = A;
+        if (row + 1 < (size_t)ny) S[(row + 1) * ss + k] = B;
+      }
+      __syncthreads();
+      continue;
+    }
     for (int e = tid; e < ntr * m; e += nthr) {
       const int p = e >> ln, k = e & (m - 1);
       const size_t row = (size_t)(2 * (pair0 + p));
@@ -475,13 +614,43 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols_bs(con
     const int k_inst = find_inst(b.col_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
     const C* ch = reinterpret_cast<const C*>(I.chirp[1]);
-    if (!ch) continue;                              // a power-of-two item
+    if (!ch && !I.mr_npass[1]) continue;            // a power-of-two item
     const C* filt = reinterpret_cast<const C*>(I.filt[1]);
     const int n = I.ny, ln = I.lny, m = 1 << ln, ss = I.sstride, nh = (I.nx >> 1) + 1;
     const int col0 = (it - b.col_start[k_inst]) * I.col_group;
     const int ntr = min(I.col_group, nh - col0);
     if (col0 == 0) theta_mean(I, red, &s_mean, tid, nthr);
     C* S = reinterpret_cast<C*>(I.S);
+    if (I.mr_npass[1]) {
+      const C* tw = reinterpret_cast<const C*>(I.mr_tw[1]);
+      for (int e = tid; e < ntr * n; e += nthr) {
+        const int g = e / n, y = e - g * n;
+        x[g * m + y] = S[(size_t)y * ss + col0 + g];
+      }
+      __syncthreads();
+      const int off = stockham<T>(x, m, n, ntr, I.mr_plan[1], I.mr_npass[1], tw, false, 0, tid, nthr);
+      const double kap = I.kappa[i];
+      const double scale = 1.0 / ((double)I.nx * (double)I.ny);
+      for (int e = tid; e < ntr * n; e += nthr) {
+        const int g = e / n, ky = e - g * n, kx = col0 + g;
+        C v = x[g * m + off + ky];
+        if (kx == 0 && ky == 0) {
+          v.x = T(s_mean); v.y = T(0);
+        } else {
+          const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
+          v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
+        }
+        x[g * m + off + ky] = v;
+      }
+      __syncthreads();
+      const int off2 = stockham<T>(x, m, n, ntr, I.mr_plan[1], I.mr_npass[1], tw, true, off, tid, nthr);
+      for (int e = tid; e < ntr * n; e += nthr) {
+        const int g = e / n, y = e - g * n;
+        S[(size_t)y * ss + col0 + g] = x[g * m + off2 + y];
+      }
+      __syncthreads();
+      continue;
+    }
     for (int e = tid; e < ntr * m; e += nthr) {
       const int g = e >> ln, y = e & (m - 1);
       C z;
@@ -527,11 +696,39 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv_bs
     const int k_inst = find_inst(b.row_start, b.counts[3], it);
     const InstDev& I = b.inst[k_inst];
     const C* ch = reinterpret_cast<const C*>(I.chirp[0]);
-    if (!ch) continue;                              // a power-of-two item
+    if (!ch && !I.mr_npass[0]) continue;            // a power-of-two item
     const int n = I.nx, ny = I.ny, ln = I.lnx, m = 1 << ln, ss = I.sstride;
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
     const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
     const C* S = reinterpret_cast<const C*>(I.S);
+    if (I.mr_npass[0]) {
+      for (int e = tid; e < ntr * n; e += nthr) {
+        const int p = e / n, k = e - p * n;
+        const size_t row = (size_t)(2 * (pair0 + p));
+        const bool two = row + 1 < (size_t)ny;
+        const int kk = k <= (n >> 1) ? k : n - k;   // Hermitian symmetry of a real row
+        C A = S[row * ss + kk], B;
+        B.x = B.y = T(0);
+        if (two) B = S[(row + 1) * ss + kk];
+        if (kk != k) { A.y = -A.y; B.y = -B.y; }
+        C z;
+        z.x = A.x - B.y; z.y = A.y + B.x;
+        x[p * m + k] = z;
+      }
+      __syncthreads();
+      const int off = stockham<T>(x, m, n, ntr, I.mr_plan[0], I.mr_npass[0], reinterpret_cast<const C*>(I.mr_tw[0]),
+                                  true, 0, tid, nthr);
+      T* th = reinterpret_cast<T*>(I.Xs[i]) + 2 * (size_t)I.nx * I.ny;
+      for (int e = tid; e < ntr * n; e += nthr) {
+        const int p = e / n, mm = e - p * n;
+        const size_t row = (size_t)(2 * (pair0 + p));
+        const C z = x[p * m + off + mm];
+        th[row * n + mm] = z.x;
+        if (row + 1 < (size_t)ny) th[(row + 1) * n + mm] = z.y;
+      }
+      __syncthreads();
+      continue;
+    }
     for (int e = tid; e < ntr * m; e += nthr) {
       const int p = e >> ln, k = e & (m - 1);
       const size_t row = (size_t)(2 * (pair0 + p));

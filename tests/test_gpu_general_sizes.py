@@ -1,5 +1,6 @@
-"""Grids of any size in [8, 4096]: ragged stencil tiles at the high edges and
-Bluestein transforms for the axes whose length is not a power of two.
+"""Grids of any size in [8, 4096]: ragged stencil tiles at the high edges, and
+for the axes whose length is not a power of two mixed-radix transforms (lengths
+that factor into 2, 3, 5, 7) or Bluestein's (the others).
 
 FP64 parity with the oracle to 1e-12 (relative max-norm per moment plane) on
 odd, even and mixed sizes (both with TMA staging, rows a multiple of 16 bytes,
@@ -57,6 +58,31 @@ def test_sizes_match_oracle(nx, ny, scheme):
     got = run_gpu(p, X0, 2)
     ref = O.run(X0, o, 2)
     assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+# lengths that factor into 2, 3, 5 and 7 take the mixed-radix transform (every radix,
+# radix 7 repeated, long plans), the others Bluestein's
+@pytest.mark.parametrize("nx,ny", [(98, 49), (96, 45), (2000, 30), (343, 10), (27, 2187), (84, 63)])
+def test_mixed_radix_sizes(nx, ny):
+    X0 = W.random_moment_state(nx, ny, seed=nx + 7 * ny, amp=0.4)
+    p, o = _pair(nx, ny, "WENO5_C4", "gsa2", 1e-2, 0.05, 0.002)
+    got = run_gpu(p, X0, 2)
+    ref = O.run(X0, o, 2)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+def test_fp32_form_mixed_radix():
+    """FP32 form on a resolved flow, 100 x 96 (mixed radix on both axes)."""
+    nx, ny = 100, 96
+    u1, u2, pr = W.taylor_green(nx, ny)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    dt = W.stable_dt(u1, u2, 2 * math.pi / nx, 0.05)
+    p, o = _pair(nx, ny, "WENO5_C4", "gsa2", 1e-4, 0.05, dt, mach=1e-3)
+    p.precision = api.FP32_DEV
+    got = run_gpu(p, X0, 5)
+    ref = O.run(X0, o, 5)
+    err = np.max(np.hypot(got[0] - ref[0], got[1] - ref[1])) / np.max(np.hypot(ref[0], ref[1]))
+    assert err <= 1e-5, err
 
 
 @pytest.mark.parametrize("eps", [1.0, 1e-4, 0.0])
