@@ -56,9 +56,11 @@ enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1 };                   /* precision fo
 /* Parameters of one solve.
  *  nx, ny      cells per direction, in [8, 4096].  Any size: an axis whose
  *              length is not a power of two takes its Helmholtz transforms
- *              by Bluestein's chirp-z identity with a power-of-two length
- *              M >= 2n - 1, and the stencil tiles at the high edges of the
- *              grid may be ragged.  Grids whose rows are not a multiple of
+ *              by a mixed-radix FFT when the length factors into 2, 3, 5
+ *              and 7, else by Bluestein's chirp-z identity with a
+ *              power-of-two length M >= 2n - 1 (either way the transform
+ *              occupies M values of shared memory); the stencil tiles at
+ *              the high edges of the grid may be ragged.  Grids whose rows are not a multiple of
  *              16 bytes stage their tiles with plain loads instead of TMA.
  *  Lx, Ly      periodic domain [0,Lx) x [0,Ly), > 0 (the paper uses 2 pi).
  *  velocity_set  AP_DVM_D2V6 (the only set of Sec. 2.1).
