@@ -9,7 +9,8 @@
 // (i = 1..s for type A; i = 2..s for CK/ARS, whose stage 1 is X^n):
 //   k_explicit(i-1)  explicit terms and reusable operators of stage i-1, and step 1 (v^(i))
 //   k_rhs(i)         the Helmholtz right-hand side of step 2
-//   k_fft_rows_fwd, k_fft_cols(i), k_fft_rows_inv(i)   step 2 (theta^(i))
+//   k_fft_rows_fwd, k_fft_cols(i), k_fft_rows_inv(i)   step 2 (theta^(i)); the _bs kernels
+//                    of the same passes for axes whose length is not a power of two
 //   k_update(i)      steps 3 and 4 (u^(i), q^(i))
 // and finally k_finish (GSA: X^{n+1} = X^(s); FP32 form: repack populations).
 #include <cuda_runtime.h>
@@ -680,7 +681,7 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
       CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.filt[a]), tab64[a].data() + nc, sizeof(double2) * nf, cudaMemcpyHostToDevice, h->stream));
     }
   }
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));   // the symbol and Bluestein vectors are about to go out of scope
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));   // the symbol and transform-table vectors are about to go out of scope
   CUDA_TRY(h, cudaMemsetAsync(d.X, 0, (size_t)6 * p->nx * p->ny * (h->f32 ? 4 : 8), h->stream));
   if (d.dF) CUDA_TRY(h, cudaMemsetAsync(d.dF, 0, (size_t)6 * p->nx * p->ny * sizeof(float), h->stream));
   s.attached = true;

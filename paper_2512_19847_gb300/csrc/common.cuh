@@ -53,8 +53,9 @@ struct Coef {
 // FP64 form, float for the FP32-deviation form).
 struct InstDev {
   int nx, ny;                   // cells per direction (any sizes; tiles at the high edges may be ragged)
-  int lnx, lny;                 // log2 of the transform length per axis: n for a power of two,
-                                // else Bluestein's convolution length M (a power of two >= 2n - 1)
+  int lnx, lny;                 // log2 of the transform footprint per axis: n for a power of two,
+                                // else Bluestein's convolution length M (a power of two >= 2n - 1),
+                                // which the mixed-radix transform's two buffers of n also fit
   int tiles_x, tiles_y;         // tile grid for the batch's tile shape
   int row_pairs;                // row pairs per row-FFT work item
   int col_group;                // spectral columns per column-FFT work item

@@ -9,20 +9,23 @@
 //                    symbol (mode k = 0 set to mean(theta^n), reading G5),
 //                    inverse DFT along y, scaled by 1/(nx ny);
 //   k_fft_rows_inv : inverse real row DFTs into theta^(i).
-// Radix-2 in shared memory: decimation in time from bit-reversed order for
-// the forward transforms, decimation in frequency (natural in, bit-reversed
-// out) for the inverse ones, so no permutation pass is needed.  An axis whose
-// length n is not a power of two is transformed by Bluestein's chirp-z
-// identity (L. I. Bluestein, 1970): with w_m = exp(i pi m^2 / n) and
+// Power-of-two lengths: radix-2^3 passes in shared memory, decimation in time
+// from bit-reversed order for the forward transforms, decimation in frequency
+// (natural in, bit-reversed out) for the inverse ones, so no permutation pass
+// is needed.  Other lengths that factor into 2, 3, 5 and 7: a self-sorting
+// mixed-radix transform (below).  Any other length n is transformed by
+// Bluestein's chirp-z identity (L. I. Bluestein, 1970): with
+// w_m = exp(i pi m^2 / n) and
 // jk = (j^2 + k^2 - (k - j)^2) / 2,
 //     sum_j x_j exp(-2 pi i jk / n) = conj(w_k) sum_j (x_j conj(w_j)) w_{k-j},
 // a circular convolution of length M, the power of two >= 2n - 1, taken with
 // two radix-2 transforms of length M and the precomputed DFT of the filter
 // (w_m for |m| < n); the inverse transform conjugates chirp and filter.  A
 // row or spectral column then occupies M complex values in shared memory.
-// Each pass has a power-of-two kernel and a Bluestein kernel (suffix _bs);
-// each takes the work items of its kind and skips the others, and a step
-// launches only the kinds its batch holds.  When ny is odd, the last row pair
+// Each pass has a power-of-two kernel and a kernel for the other lengths
+// (suffix _bs: mixed radix or Bluestein); each takes the work items of its
+// kind and skips the others, and a step launches only the kinds its batch
+// holds.  When ny is odd, the last row pair
 // holds one row (its partner is zero).
 #pragma once
 #include "common.cuh"
