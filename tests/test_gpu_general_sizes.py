@@ -163,10 +163,10 @@ def test_thousand_squared():
     assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
 
 
-@pytest.mark.parametrize("nx", [60, 61])
-def test_fp32_form_ragged(nx):
-    """FP32 form on a resolved flow: 60 (16-byte rows, TMA) and 61 (plain loads) by 36."""
-    ny = 36
+@pytest.mark.parametrize("nx,ny", [(60, 36), (61, 36), (64, 37)])
+def test_fp32_form_ragged(nx, ny):
+    """FP32 form on a resolved flow: 60 x 36 (16-byte rows, TMA; mixed radix), 61 x 36 (plain
+    loads; Bluestein rows) and 64 x 37 (Bluestein columns)."""
     u1, u2, pr = W.taylor_green(nx, ny)
     X0 = O.equilibrium_state(u1, u2, pr)
     dt = W.stable_dt(u1, u2, 2 * math.pi / nx, 0.05)
