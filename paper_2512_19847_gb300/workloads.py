@@ -57,9 +57,11 @@ def double_shear_layer(nx: int, ny: int | None = None, inv_rho: float = 30.0, de
     Returns (u1, u2, p).
     """
     ny = nx if ny is None else ny
-    X, Y = cell_centres(nx, ny)
     if nodes:
-        X, Y = X - 0.5 * TWO_PI / nx, Y - 0.5 * TWO_PI / ny
+        X, Y = np.meshgrid(np.arange(nx, dtype=np.float64) * (TWO_PI / nx),
+                           np.arange(ny, dtype=np.float64) * (TWO_PI / ny), indexing="xy")
+    else:
+        X, Y = cell_centres(nx, ny)
     u1 = np.where(Y <= math.pi, np.tanh(inv_rho * (Y - math.pi / 2)), np.tanh(inv_rho * (1.5 * math.pi - Y)))
     u2 = delta * np.sin(X)
     p = np.zeros_like(u1)

@@ -31,3 +31,16 @@ def test_interpolation_keeps_the_mean_and_orientation():
     g = interpolate_periodic(f, n)
     xc = (np.arange(n) + 0.5) * 2 * math.pi / n
     assert np.max(np.abs(g - (2.5 + np.cos(2 * xc)[:, None]))) < 1e-12
+
+
+def test_node_sampled_grids_are_nested():
+    """Reading G14 of the Tables 1-2 grids: with nodes=True the double shear layer is sampled
+    at (i dx, j dy), so every point of an N - 1 = 2^k cell grid is a point of the finer ones
+    (injection compares the same physical points)."""
+    from paper_2512_19847_gb300 import workloads as W
+    coarse = W.double_shear_layer(32, inv_rho=15 / math.pi, nodes=True)
+    fine = W.double_shear_layer(512, inv_rho=15 / math.pi, nodes=True)
+    for c, f in zip(coarse, fine):
+        assert np.array_equal(c, f[::16, ::16])
+    centred = W.double_shear_layer(32, inv_rho=15 / math.pi)
+    assert not np.array_equal(centred[1], coarse[1])
