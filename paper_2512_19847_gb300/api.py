@@ -8,7 +8,6 @@ CPU path: if the library or a GPU is missing, every call raises.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import torch
