@@ -359,6 +359,7 @@ def test_g4_sign_from_the_stage_equations():
     assert res[+1.0] > 1e-3, res
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # the unstable cases overflow on purpose
 def test_g6_partner_reading_stability():
     """The explicit-weight dissipation partner stays bounded at CFL 0.5 on
     Taylor-Green with the second-order tableau; the lagged reading blows up."""
@@ -434,6 +435,7 @@ def test_temporal_order(tab, order):
         assert orders(scheme="LF1_C2", alpha=0.0) < 1.3
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # the unstable cases overflow on purpose
 def test_viscous_time_step_bound():
     """In the limit the viscous term is explicit (Sec. 3.1), so dt needs
     nu dt/dx^2 below ~0.5: 0.4 is stable over 150 steps, 0.7 is not; the
