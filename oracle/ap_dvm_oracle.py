@@ -85,6 +85,18 @@ def tableau_gsa2(c: float = 2.25):
     return A_ex, A_ex[-1].copy(), A_im, A_im[-1].copy()
 
 
+def tableau_ars4():
+    """A four-stage second-order GSA IMEX pair of ARS type (Sec. 3.1 definitions:
+    a_11 = 0 and a zero first implicit column, a_ii = 1/2 for i >= 2), with nodes
+    c = (0, 1/2, 3/2, 1) shared by both tableaux, weights equal to the last rows
+    (GSA), and sum w c = sum w~ c = 1/2.  Not one of the paper's pairs: it
+    exercises Algorithm 1 with s = 4, every explicit entry below the diagonal
+    nonzero, and every dissipation-partner weight atilde_ij - a_ij nonzero."""
+    A_ex = np.array([[0.0, 0.0, 0.0, 0.0], [0.5, 0.0, 0.0, 0.0], [0.75, 0.75, 0.0, 0.0], [0.5, 0.25, 0.25, 0.0]])
+    A_im = np.array([[0.0, 0.0, 0.0, 0.0], [0.0, 0.5, 0.0, 0.0], [0.0, 1.0, 0.5, 0.0], [0.0, 0.75, -0.25, 0.5]])
+    return A_ex, A_ex[-1].copy(), A_im, A_im[-1].copy()
+
+
 # ---------------------------------------------------------------------------
 # Parameters and state
 # ---------------------------------------------------------------------------

@@ -1,5 +1,6 @@
 """IMEX-RK tableaux as (A_ex, A_im) lists: the GSA schemes of Sec. 4.1 (type
-CK/ARS: a_11 = 0) and type-A GSA tableaux (a_ii != 0 for every i, Sec. 3.1)."""
+CK/ARS: a_11 = 0), a four-stage GSA pair of ARS type, and type-A GSA tableaux
+(a_ii != 0 for every i, Sec. 3.1)."""
 
 
 def euler():
@@ -12,6 +13,16 @@ def gsa2(c: float = 2.25):
     g = (c - 0.5) / (c - 1.0)
     A_ex = [[0.0, 0.0, 0.0], [c, 0.0, 0.0], [1.0 - 1.0 / (2.0 * c), 1.0 / (2.0 * c), 0.0]]
     A_im = [[0.0, 0.0, 0.0], [0.0, c, 0.0], [0.0, 1.0 - g, g]]
+    return A_ex, A_im
+
+
+def ars4():
+    """A four-stage second-order GSA pair of ARS type (a_11 = 0, zero first
+    implicit column, a_ii = 1/2 for i >= 2; nodes (0, 1/2, 3/2, 1)).  Not one
+    of the paper's pairs: the largest stage count the library takes, with
+    every explicit entry and every dissipation-partner weight nonzero."""
+    A_ex = [[0.0, 0.0, 0.0, 0.0], [0.5, 0.0, 0.0, 0.0], [0.75, 0.75, 0.0, 0.0], [0.5, 0.25, 0.25, 0.0]]
+    A_im = [[0.0, 0.0, 0.0, 0.0], [0.0, 0.5, 0.0, 0.0], [0.0, 1.0, 0.5, 0.0], [0.0, 0.75, -0.25, 0.5]]
     return A_ex, A_im
 
 

@@ -47,7 +47,7 @@ def run_gpu(p, X0, nsteps, graph=0, tile=-1):
 
 
 @pytest.mark.parametrize("scheme", ["LF1_C2", "WENO3_C4", "WENO5_C4"])
-@pytest.mark.parametrize("tab", ["euler", "gsa2"])
+@pytest.mark.parametrize("tab", ["euler", "gsa2", "ars4"])
 @pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-6])
 def test_one_step_random_state(scheme, tab, eps):
     nx, ny = 64, 32
@@ -293,6 +293,58 @@ def test_fp32_form_every_tile_shape(tile):
     p, o = _pair(n, n, "WENO5_C4", "gsa2", 1e-4, 0.05, dt, mach=1e-3)
     p.precision = api.FP32_DEV
     got = run_gpu(p, X0, 5, tile=tile)
+    ref = O.run(X0, o, 5)
+    err = np.max(np.hypot(got[0] - ref[0], got[1] - ref[1])) / np.max(np.hypot(ref[0], ref[1]))
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("scheme", ["WENO3_C4", "WENO5_C4"])
+def test_four_stages_every_tile_shape(tile, scheme):
+    """s = 4 (the largest stage count the library takes; the ARS-type pair
+    tableaux.ars4): the stage sums of Algorithm 1 over three earlier stages, the
+    dissipation partner over three earlier stages (reading G6) and the update's
+    largest staged plane set, on every tile shape, over 3 steps, on a grid with
+    ragged edge tiles in both directions."""
+    nx, ny = 72, 40
+    X0 = W.random_moment_state(nx, ny, seed=404, amp=0.4)
+    p, o = _pair(nx, ny, scheme, "ars4", 1e-2, 0.05, 0.01)
+    got = run_gpu(p, X0, 3, tile=tile)
+    ref = O.run(X0, o, 3)
+    assert np.all(rel_err(got, ref) <= TOL), rel_err(got, ref)
+
+
+def test_four_stages_batch_graph_and_fp32_form():
+    """s = 4 in the batched form (mixed sizes, CUDA graph: each solve bit for bit
+    its result alone, and the oracle's within 1e-12) and in the FP32 deviation
+    form (velocity within 1e-5 of the oracle on a resolved flow)."""
+    sizes = [(64, 64), (64, 32), (32, 64)]
+    eps = 1e-4
+    ps, refs, alone = [], [], []
+    for k, (nx, ny) in enumerate(sizes):
+        X0 = W.random_moment_state(nx, ny, seed=50 + k, amp=0.4)
+        p, o = _pair(nx, ny, "WENO5_C4", "ars4", eps, 0.05, 0.01, mach=1e-3)
+        ps.append((p, X0))
+        refs.append(O.run(X0, o, 4))
+        alone.append(run_gpu(p, X0, 4, tile=3))
+        assert np.all(rel_err(alone[-1], refs[-1]) <= TOL), rel_err(alone[-1], refs[-1])
+    b = api.Batch(ps[0][0], capacity=len(sizes))
+    for k, (p, X0) in enumerate(ps):
+        b.attach(k, p)
+        b.set_state(torch.from_numpy(X0).cuda(), slot=k)
+    b.set_tile(3)
+    b.set_graph_steps(2)
+    b.step(4)
+    b.sync_status()
+    for k in range(len(sizes)):
+        assert np.array_equal(b.get_state(k).cpu().numpy(), alone[k]), k
+    n = 64
+    u1, u2, pr = W.taylor_green(n)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    dt = W.stable_dt(u1, u2, 2 * math.pi / n, 0.05)
+    p, o = _pair(n, n, "WENO5_C4", "ars4", eps, 0.05, dt, mach=1e-3)
+    p.precision = api.FP32_DEV
+    got = run_gpu(p, X0, 5)
     ref = O.run(X0, o, 5)
     err = np.max(np.hypot(got[0] - ref[0], got[1] - ref[1])) / np.max(np.hypot(ref[0], ref[1]))
     assert err <= 1e-5, err

@@ -21,8 +21,11 @@ warnings.filterwarnings("ignore", category=RuntimeWarning)
 SCHEMES = ["LF1_C2", "WENO3_C4", "WENO5_C4"]
 
 
+TABLEAUX = {"euler": O.tableau_euler, "gsa2": O.tableau_gsa2, "ars4": O.tableau_ars4}
+
+
 def _params(n, scheme="WENO5_C4", eps=1e-2, tau=0.05, dt=None, tab="gsa2", **kw):
-    A_ex, _, A_im, _ = O.tableau_gsa2() if tab == "gsa2" else O.tableau_euler()
+    A_ex, _, A_im, _ = TABLEAUX[tab]()
     dx = 2 * math.pi / n
     return O.Params(n, n, eps, tau, 0.25 * dx if dt is None else dt, A_ex, A_im, scheme=scheme, **kw)
 
@@ -106,6 +109,55 @@ def test_equilibrium_moments():
     assert np.allclose(-M[3], f1, atol=1e-14) and np.allclose(M[4], f2, atol=1e-14)
 
 
+def test_outputs_are_the_moments_of_the_populations():
+    """outputs() against the definitions of Sec. 2.1 evaluated on the populations
+    F_i = rho0/6 + dF_i by scalar loops: the density is sum_i F_i, the momentum
+    sum_i c_i F_i = rho0 A u (A the storage amplitude, G10), and
+    theta = (sum_i F_i - rho0)/2 rescaled by rho0 A eps (G10); the pressure is
+    p = theta - |u|^2/2 with that theta and that u."""
+    X = W.random_moment_state(5, 4, seed=5, amp=0.7)
+    eps, rho0, amp = 0.02, 1.3, 2e-3
+    dF = O.populations_from_moments(X, eps, rho0=rho0, amp=amp)
+    rho, u1, u2, p = O.outputs(X, eps, rho0=rho0, amp=amp)
+    for j in range(4):
+        for i in range(5):
+            F = [rho0 / 6.0 + dF[k, j, i] for k in range(6)]
+            r = m1 = m2 = 0.0
+            for k in range(6):
+                r += F[k]
+                m1 += math.cos(math.pi * k / 3) * F[k]
+                m2 += math.sin(math.pi * k / 3) * F[k]
+            theta = 0.5 * (r - rho0) / (rho0 * amp * eps)
+            w1, w2 = m1 / (rho0 * amp), m2 / (rho0 * amp)
+            assert rho[j, i] == pytest.approx(r, rel=1e-14)
+            assert u1[j, i] == pytest.approx(w1, rel=1e-9, abs=1e-12)
+            assert u2[j, i] == pytest.approx(w2, rel=1e-9, abs=1e-12)
+            assert p[j, i] == pytest.approx(theta - 0.5 * (w1 * w1 + w2 * w2), rel=1e-8, abs=1e-10)
+
+
+@pytest.mark.parametrize("tab", ["gsa2", "ars4"])
+def test_pressure_output_in_the_limit(tab):
+    """eps -> 0: the pressure output follows the incompressible Taylor-Green
+    pressure (cos 2x + cos 2y)/4 exp(-4 nu t), nu = tau/4 (the limit scheme of
+    Theorem 3.4 carries p^(i) = theta^(i) - |u^(i)|^2/2 as its pressure), up to a
+    constant and converging with N; theta alone misses it by the kinetic part
+    |u|^2/2, so a dropped factor or a wrong sign in p fails."""
+    tau, T = 0.4, 0.5
+    nu = tau / 4
+    errs, th_errs = [], []
+    for n in (16, 32):
+        u1, u2, pr = W.taylor_green(n)
+        X = O.equilibrium_state(u1, u2, pr)
+        dt, ns = W.fixed_time_dt(T, 0.25 * 2 * math.pi / n)
+        Y = O.run(X, _params(n, "WENO5_C4", eps=1e-6, tau=tau, dt=dt, tab=tab), ns)
+        _, _, _, p = O.outputs(Y, 1e-6)
+        _, _, pe = W.taylor_green(n, t=T, nu=nu)
+        errs.append(np.max(np.abs((p - p.mean()) - (pe - pe.mean()))))
+        th_errs.append(np.max(np.abs((Y[2] - Y[2].mean()) - (pe - pe.mean()))))
+    assert errs[0] < 0.03 and errs[1] < 0.7 * errs[0], errs
+    assert min(th_errs) > 0.1, th_errs
+
+
 def _spec_d(f, axis, L=2 * math.pi):
     n = f.shape[axis]
     k = np.fft.fftfreq(n, d=1.0 / n) * (2 * math.pi / L)
@@ -154,9 +206,9 @@ def test_moment_system_follows_from_the_dvm():
 
 # ---------------------------------------------------------------- tableaux (Sec. 3.1, 4.1)
 
-@pytest.mark.parametrize("name", ["euler", "gsa2"])
+@pytest.mark.parametrize("name", ["euler", "gsa2", "ars4"])
 def test_tableau_properties(name):
-    A_ex, w_ex, A_im, w_im = O.tableau_euler() if name == "euler" else O.tableau_gsa2()
+    A_ex, w_ex, A_im, w_im = TABLEAUX[name]()
     s = A_ex.shape[0]
     assert np.allclose(np.triu(A_ex), 0.0)                 # explicit: strictly lower
     assert np.allclose(np.triu(A_im, 1), 0.0)              # implicit: DIRK
@@ -167,9 +219,23 @@ def test_tableau_properties(name):
     assert abs(w_ex.sum() - 1) < 1e-15 and abs(w_im.sum() - 1) < 1e-15
     if name == "gsa2":
         assert abs(A_im[2, 2] - 1.4) < 1e-15               # gamma = (c - 1/2)/(c - 1), c = 2.25
+    if name in ("gsa2", "ars4"):
         for w in (w_ex, w_im):
             for cc in (c_ex, c_im):
                 assert abs(w @ cc - 0.5) < 1e-14           # second-order and coupling conditions
+    if name == "ars4":
+        assert s == 4 and np.all(A_im[:, 0] == 0.0)        # ARS: zero first implicit column
+        # every dissipation-partner weight atilde_ij - a_ij (j < i, reading G6) is nonzero
+        assert all(A_ex[i, j] - A_im[i, j] != 0.0 for i in range(1, s) for j in range(i))
+
+
+def test_ars4_data_matches_the_package_tableau():
+    """The tests feed the CUDA path from paper_2512_19847_gb300.tableaux (data only):
+    its four-stage pair is the oracle's."""
+    from paper_2512_19847_gb300 import tableaux
+    A_ex, _, A_im, _ = O.tableau_ars4()
+    T_ex, T_im = tableaux.ars4()
+    assert np.array_equal(A_ex, np.array(T_ex)) and np.array_equal(A_im, np.array(T_im))
 
 
 # ---------------------------------------------------------------- stencils (Sec. 3.2, G7)
@@ -296,7 +362,7 @@ def test_helmholtz_against_dense_solve(scheme, n):
 
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("eps", [1.0, 1e-3, 0.0])
-@pytest.mark.parametrize("tab", ["euler", "gsa2"])
+@pytest.mark.parametrize("tab", ["euler", "gsa2", "ars4"])
 def test_uniform_equilibrium_is_fixed_point(scheme, eps, tab):
     n = 8
     u1 = np.full((n, n), 0.3)
@@ -307,10 +373,11 @@ def test_uniform_equilibrium_is_fixed_point(scheme, eps, tab):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_conservation_of_u_and_mean_theta(scheme):
+@pytest.mark.parametrize("tab", ["gsa2", "ars4"])
+def test_conservation_of_u_and_mean_theta(scheme, tab):
     n = 16
     X = W.random_moment_state(n, n, seed=21)
-    Y = O.step(X, _params(n, scheme, eps=0.05, tau=0.1))
+    Y = O.step(X, _params(n, scheme, eps=0.05, tau=0.1, tab=tab))
     assert abs(Y[0].sum() - X[0].sum()) < 1e-11 * np.abs(X[0]).sum()
     assert abs(Y[1].sum() - X[1].sum()) < 1e-11 * np.abs(X[1]).sum()
     assert abs(Y[2].mean() - X[2].mean()) < 1e-13 * np.abs(X[2]).max()
@@ -389,7 +456,8 @@ def test_exact_limit_eps_zero_runs():
 
 # ---------------------------------------------------------------- the incompressible limit
 
-def test_taylor_green_limit_decay():
+@pytest.mark.parametrize("tab", ["gsa2", "ars4"])
+def test_taylor_green_limit_decay(tab):
     """eps -> 0: u follows the INS Taylor-Green solution with nu = tau/4 and the
     kinetic energy decays like exp(-4 nu t) (Sec. 2.1 INS limit, Theorem 3.5)."""
     tau, T = 0.4, 0.5
@@ -399,7 +467,7 @@ def test_taylor_green_limit_decay():
         u1, u2, pr = W.taylor_green(n)
         X = O.equilibrium_state(u1, u2, pr)
         dt, ns = W.fixed_time_dt(T, 0.25 * 2 * math.pi / n)
-        Y = O.run(X, _params(n, "WENO5_C4", eps=1e-6, tau=tau, dt=dt), ns)
+        Y = O.run(X, _params(n, "WENO5_C4", eps=1e-6, tau=tau, dt=dt, tab=tab), ns)
         e1, e2, _ = W.taylor_green(n, t=T, nu=nu)
         errs.append(max(np.abs(Y[0] - e1).max(), np.abs(Y[1] - e2).max()))
         ke_ratio = np.mean(Y[0] ** 2 + Y[1] ** 2) / np.mean(X[0] ** 2 + X[1] ** 2)
@@ -407,7 +475,7 @@ def test_taylor_green_limit_decay():
     assert errs[1] < errs[0] / 8
 
 
-@pytest.mark.parametrize("tab,order", [("euler", 1.0), ("gsa2", 2.0)])
+@pytest.mark.parametrize("tab,order", [("euler", 1.0), ("gsa2", 2.0), ("ars4", 2.0)])
 def test_temporal_order(tab, order):
     """Self-convergence under dt halving at fixed N in the limit regime.
 
