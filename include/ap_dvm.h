@@ -216,15 +216,19 @@ ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, do
  *  cuda_stream  stream for the copies and kernels.
  * Returns AP_DVM_ERR_ARG for invalid parameters or a grid beyond the limit
  * above, AP_DVM_ERR_UNSUPPORTED for the FP32 form or a size that is not a
- * power of two, AP_DVM_ERR_CUDA if a CUDA
- * call fails.  The scratch is one 8 MiB file-scope device array that every
- * GPU which loads this library holds until the process exits.  The first
- * call on a device looks up that array's address (set-up), so make it before
- * any stream capture.  Each call synchronises the stream once after staging
- * its small descriptors, then enqueues the steps asynchronously.  All calls
- * share the one array and it keeps the last call's contents: calls whose
- * work overlaps on the GPU (other streams, other host threads) race and give
- * wrong results; serialise them. */
+ * power of two, AP_DVM_ERR_CUDA if a CUDA call fails, and, like
+ * ap_dvm_sync_status, AP_DVM_ERR_TIMEOUT if a kernel gave up a bounded wait
+ * for one of its tile copies (the state is then invalid) or
+ * AP_DVM_ERR_NONFINITE if a step produced a non-finite value (d_state6 then
+ * holds that state).  The scratch is one 8 MiB file-scope device array that
+ * every GPU which loads this library holds until the process exits; the
+ * first call on a device looks up that array's address.  Each call is
+ * synchronous: it synchronises the stream after staging its small
+ * descriptors from host memory, and again at the end to read the device
+ * error flags, so it cannot be called while the stream is being captured
+ * into a CUDA graph.  All calls share the one array and it keeps the last
+ * call's contents: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and give wrong results; serialise them. */
 ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_state6, int nsteps, void* cuda_stream);
 
 /* Synchronise the stream and return AP_DVM_ERR_TIMEOUT if a kernel gave up a
@@ -245,6 +249,21 @@ ap_dvm_status ap_dvm_check_wait_timeout(ap_dvm_handle* h, long long wait_ns);
 const char* ap_dvm_last_error(const ap_dvm_handle* h);
 /* Release the handle (host memory and graphs); device workspaces stay with the caller. */
 void ap_dvm_destroy(ap_dvm_handle* h);
+
+/* ---- measurement ---------------------------------------------------------------- */
+
+/* Arithmetic peak of the current GPU for the roofline of the FP64 form (the
+ * paper has no counterpart: it reports no hardware figures).  Launches a
+ * kernel whose threads run only independent fused multiply-add chains
+ * (FP64 for precision = AP_DVM_FP64, FP32 for AP_DVM_FP32_DEV), as many
+ * resident 256-thread blocks as fit on every SM, `iters` x 128 FMAs per
+ * thread, once to warm up and then `reps` times between CUDA events on
+ * cuda_stream; synchronises.  Writes the rate (2 flops per FMA) to *tflops
+ * and the mean launch time to *ms_per_launch.  Returns AP_DVM_ERR_ARG for
+ * null outputs, iters < 1, reps < 1 or another precision, AP_DVM_ERR_CUDA if
+ * a CUDA call fails. */
+ap_dvm_status ap_dvm_fma_peak(int precision, int iters, int reps, void* cuda_stream, double* tflops,
+                              double* ms_per_launch);
 
 /* Fill *p with defaults: 2 pi periodic square, D2V6, rho0 = 1, mach = 1e-2,
  * tau = 0.05, the second-order GSA tableau of Sec. 4.1 (c = 2.25), WENO5+C4,

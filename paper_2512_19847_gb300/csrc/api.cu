@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "dispatch.h"
 #include "step_plan.h"
+#include "workspace.h"
 
 using namespace apd;
 
@@ -108,36 +109,6 @@ ap_dvm_status fail(ap_dvm_handle* h, ap_dvm_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(h, AP_DVM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
   } while (0)
 
-bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
-int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-// Transform length of an axis of n cells: n for a power of two, else the
-// length of Bluestein's circular convolution, the power of two >= 2n - 1.
-int fft_length(int n) {
-  if (is_pow2(n)) return n;
-  int m = 1;
-  while (m < 2 * n - 1) m <<= 1;
-  return m;
-}
-
-// Mixed-radix plan of an axis of n cells: the radices (4s first, then 2, 3, 5,
-// 7; 4 bits each, first pass in the low bits) when n is not a power of two and
-// has no prime factor above 7; false otherwise.
-bool mixed_radix_plan(int n, unsigned* plan, int* npass) {
-  if (is_pow2(n)) return false;
-  unsigned pl = 0;
-  int np = 0;
-  auto push = [&](int r) { pl |= (unsigned)r << (4 * np); ++np; };
-  while (n % 4 == 0) { push(4); n /= 4; }
-  for (int r : {2, 3, 5, 7})
-    while (n % r == 0) { push(r); n /= r; }
-  if (n != 1 || np > 8) return false;
-  *plan = pl;
-  *npass = np;
-  return true;
-}
-
 // Bluestein tables of an axis of n cells (n not a power of two) with
 // convolution length m: the chirp exp(-i pi k^2 / n), k < n (k^2 reduced
 // modulo 2n before the angle is formed), and the DFT of length m of the filter
@@ -217,74 +188,6 @@ bool same_method(const ap_dvm_params& a, const ap_dvm_params& b) {
   for (int k = 0; k < AP_DVM_MAX_STAGES * AP_DVM_MAX_STAGES; ++k)
     if (a.A_ex[k] != b.A_ex[k] || a.A_im[k] != b.A_im[k]) return false;
   return true;
-}
-
-// Carves one instance's workspace (base == nullptr: size only).
-size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
-  const size_t es = p.precision == AP_DVM_FP64 ? 8 : 4;
-  const size_t cells = (size_t)p.nx * p.ny;
-  const size_t plane = cells * es;
-  size_t off = 0;
-  auto take = [&](size_t bytes) -> void* {
-    off = align_up(off, 256);
-    void* r = base ? base + off : nullptr;
-    off += bytes;
-    return r;
-  };
-  const int s = p.s;
-  InstDev tmp{};
-  InstDev& I = d ? *d : tmp;
-  const bool type_a = p.A_im[0] != 0.0;
-  I.X = take(6 * plane);
-  I.Xs[1] = type_a ? take(6 * plane) : I.X;           // stage 1: its own values (type A) or X^n
-  for (int j = 2; j <= s; ++j) I.Xs[j] = take(6 * plane);
-  for (int j = 1; j <= s; ++j) {
-    I.E[j] = take(2 * plane);
-    I.Du[j] = take(plane);
-    I.Lth[j] = take(plane);
-    I.Gth[j] = take(2 * plane);
-    I.DLFB[j] = take(2 * plane);
-    I.Dv[j] = take(plane);
-    I.DB[j] = take(plane);
-  }
-  I.Dun = type_a ? take(plane) : I.Du[1];
-  I.R = take(plane);
-  I.sstride = p.nx / 2 + 1;
-  I.S = take((size_t)p.ny * I.sstride * 2 * es);
-  I.lamx = reinterpret_cast<double*>(take((size_t)(p.nx / 2 + 1) * sizeof(double)));
-  I.lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
-  // one partial sum per tile: at most ceil(nx/8) * ceil(ny/4) tiles (the smallest tile sides)
-  I.th_part = reinterpret_cast<double*>(take((size_t)((p.nx + 7) / 8) * ((p.ny + 3) / 4) * sizeof(double)));
-  for (int a = 0; a < 2; ++a) {   // tables of an axis that is not a power of two: mixed radix or Bluestein
-    const int na = a ? p.ny : p.nx;
-    unsigned plan = 0;
-    int npass = 0;
-    const bool mr = mixed_radix_plan(na, &plan, &npass);
-    I.mr_plan[a] = mr ? plan : 0u;
-    I.mr_npass[a] = mr ? npass : 0;
-    I.mr_tw[a] = mr ? take((size_t)na * 2 * es) : nullptr;
-    const bool bs = !is_pow2(na) && !mr;
-    I.chirp[a] = bs ? take((size_t)na * 2 * es) : nullptr;
-    I.filt[a] = bs ? take((size_t)fft_length(na) * 2 * es) : nullptr;
-  }
-  I.dF = p.precision == AP_DVM_FP32_DEV ? reinterpret_cast<float*>(take(6 * cells * sizeof(float))) : nullptr;
-  I.tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1));
-  return align_up(off, 256);
-}
-
-// 1D symbol of the Laplacian stencil on DFT mode k (compact 3-point or 4th-order
-// 5-point second difference, Sec. 3.2), without cancellation for small k.
-void laplacian_symbol(int n, double h, int scheme, double* out, int count) {
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int k = 0; k < count; ++k) {
-    const long double phi = 2.0L * pi * (long double)k / (long double)n;
-    const long double s = std::sin(0.5L * phi);
-    const long double s2 = s * s;
-    long double v;
-    if (scheme == AP_DVM_LF1_C2) v = -4.0L * s2 / ((long double)h * h);
-    else v = 2.0L * s2 * (std::cos(phi) - 7.0L) / (3.0L * (long double)h * h);
-    out[k] = (double)v;
-  }
 }
 
 size_t batch_bytes(int capacity, int nmax) {

@@ -1,7 +1,8 @@
 // ap_dvm_step_noalloc: IMEX steps of one small FP64 solve with all scratch
 // in a file-scope device array, for callers that cannot allocate device
-// memory (see include/ap_dvm.h).  It reuses the library's kernels unchanged;
-// only the carving of the scratch and the launch sequence live here.
+// memory (see include/ap_dvm.h).  It reuses the library's kernels, the launch
+// sequence of one step (step_plan.h) and the workspace carving of the handle
+// path (workspace.h) unchanged; only the placement of the scratch lives here.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -12,6 +13,7 @@
 #include "common.cuh"
 #include "dispatch.h"
 #include "step_plan.h"
+#include "workspace.h"
 
 using namespace apd;
 
@@ -27,47 +29,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-size_t up(size_t x) { return (x + 255) / 256 * 256; }
-
 // Layout of the scratch: batch tables, then the instance's planes.
 struct Layout {
   size_t batch, inst, tile_start, row_start, col_start, counts, tw, err, ws;
   size_t total;
 };
 
-size_t instance_bytes(const ap_dvm_params& p, char* base, InstDev* I) {
-  const size_t plane = (size_t)p.nx * p.ny * sizeof(double);
-  size_t off = 0;
-  auto take = [&](size_t b) -> void* { off = up(off); void* r = base ? base + off : nullptr; off += b; return r; };
-  const bool type_a = p.A_im[0] != 0.0;
-  I->X = take(6 * plane);
-  I->Xs[1] = type_a ? take(6 * plane) : I->X;
-  for (int j = 2; j <= p.s; ++j) I->Xs[j] = take(6 * plane);
-  for (int j = 1; j <= p.s; ++j) {
-    I->E[j] = take(2 * plane);
-    I->Du[j] = take(plane);
-    I->Lth[j] = take(plane);
-    I->Gth[j] = take(2 * plane);
-    I->DLFB[j] = take(2 * plane);
-    I->Dv[j] = take(plane);
-    I->DB[j] = take(plane);
-  }
-  I->Dun = type_a ? take(plane) : I->Du[1];
-  I->R = take(plane);
-  I->sstride = p.nx / 2 + 1;
-  I->S = take((size_t)p.ny * I->sstride * 2 * sizeof(double));
-  I->lamx = reinterpret_cast<double*>(take((size_t)(p.nx / 2 + 1) * sizeof(double)));
-  I->lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
-  I->th_part = reinterpret_cast<double*>(take((size_t)p.nx * p.ny / 32 * sizeof(double)));
-  I->dF = nullptr;
-  I->tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1));
-  return up(off);
-}
-
 Layout layout(const ap_dvm_params& p, int nmax) {
   Layout L{};
   size_t off = 0;
-  auto take = [&](size_t b) { off = up(off); size_t r = off; off += b; return r; };
+  auto take = [&](size_t b) { off = align_up(off, 256); size_t r = off; off += b; return r; };
   L.batch = take(sizeof(BatchDev));
   L.inst = take(sizeof(InstDev));
   L.tile_start = take(2 * sizeof(int));
@@ -76,25 +47,10 @@ Layout layout(const ap_dvm_params& p, int nmax) {
   L.counts = take(4 * sizeof(int));
   L.tw = take(sizeof(double2) * (nmax / 2));
   L.err = take(4 * sizeof(unsigned));
-  InstDev dummy{};
-  L.ws = take(instance_bytes(p, nullptr, &dummy));
-  L.total = up(off);
+  L.ws = take(carve_instance(p, nullptr, nullptr));
+  L.total = align_up(off, 256);
   return L;
 }
-
-void symbol(int n, double h, int scheme, double* out, int count) {
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int k = 0; k < count; ++k) {
-    const long double phi = 2.0L * pi * (long double)k / (long double)n;
-    const long double s = std::sin(0.5L * phi);
-    const long double s2 = s * s;
-    const long double v = scheme == AP_DVM_LF1_C2 ? -4.0L * s2 / ((long double)h * h)
-                                                  : 2.0L * s2 * (std::cos(phi) - 7.0L) / (3.0L * (long double)h * h);
-    out[k] = (double)v;
-  }
-}
-
-int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 cudaError_t grid_of(const void* fn, int threads, size_t smem, int sms, int* grid) {
   cudaError_t e = cudaSuccess;
@@ -161,7 +117,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
 
   // descriptors, built on the host stack and copied into the scratch
   InstDev I{};
-  instance_bytes(*p, base + L.ws, &I);
+  carve_instance(*p, base + L.ws, &I);
   I.nx = p->nx; I.ny = p->ny; I.lnx = ilog2(p->nx); I.lny = ilog2(p->ny);
   I.tiles_x = p->nx / ks.tx; I.tiles_y = p->ny / ks.ty;
   I.row_pairs = std::max(1, std::min(eblk / p->nx, p->ny / 2));
@@ -193,8 +149,8 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
     tw[k].x = (double)std::cos(a);
     tw[k].y = (double)std::sin(a);
   }
-  symbol(p->nx, I.dx, p->space_scheme, lx, p->nx / 2 + 1);
-  symbol(p->ny, I.dy, p->space_scheme, ly, p->ny);
+  laplacian_symbol(p->nx, I.dx, p->space_scheme, lx, p->nx / 2 + 1);
+  laplacian_symbol(p->ny, I.dy, p->space_scheme, ly, p->ny);
   NA_TRY(cudaMemcpyAsync(base + L.batch, &B, sizeof(B), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(base + L.inst, &I, sizeof(I), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(B.tile_start, ts, sizeof(ts), cudaMemcpyHostToDevice, stream));
@@ -221,5 +177,13 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
     if (st) return (ap_dvm_status)st;
   }
   NA_TRY(cudaMemcpyAsync(d_state6, I.X, 6 * sizeof(double) * p->nx * p->ny, cudaMemcpyDeviceToDevice, stream));
+
+  // the device error flags of these steps (bit 1: a bounded tile-copy wait expired, bit 0:
+  // a non-finite state), read before the next call clears them
+  unsigned flags = 0;
+  NA_TRY(cudaMemcpyAsync(&flags, B.err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+  NA_TRY(cudaStreamSynchronize(stream));
+  if (flags & 2u) return AP_DVM_ERR_TIMEOUT;
+  if (flags & 1u) return AP_DVM_ERR_NONFINITE;
   return AP_DVM_OK;
 }
