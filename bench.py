@@ -220,7 +220,7 @@ def measured_traffic(kind: str, f32: bool, n: int):
     return None if v is None else float(v)
 
 
-def roofline(prof: dict, steps: int, cells: int, f32: bool, scheme: str, n: int, peaks: dict):
+def roofline(prof: dict, steps: int, cells: int, f32: bool, scheme: str, n: int, peaks: dict, fp64_peak: dict | None = None):
     flops = step_flops_per_cell(scheme, n)
     byts = step_bytes_per_cell(f32)
     kind, (tot_ms, launches) = max(prof.items(), key=lambda kv: kv[1][0])
@@ -236,20 +236,103 @@ def roofline(prof: dict, steps: int, cells: int, f32: bool, scheme: str, n: int,
                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
     alg = flops[kind] * cells / launches_per_step                # flops per launch
     achieved = alg / (per_launch_ms * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS
-    return kind, {"bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+    peak = fp64_peak["tflops_at_run_clock"]
+    return kind, {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                   "frac": round(achieved / peak, 4), "traffic": measured_traffic(kind, False, n), "kernel": kind,
                   "algorithmic_flops_per_launch": alg, "ms_per_launch": round(per_launch_ms, 4),
-                  "peak_source": "FP64 FMA pipe of this GPU model, measured with an FMA-chain microbenchmark: 0.505e12 DFMA/s x 2"}
+                  "peak_source": fp64_peak["source"]}
 
 
-# measured on this machine's GB300 (FMA-chain microbenchmark, 152 SMs x 8 blocks x 256 threads)
-FP64_PEAK_TFLOPS = 1.01
+def fma_peak_leg(local: int, precision: int, iters: int, reps: int = 60) -> dict:
+    """The measured FMA peak (ap_dvm_fma_peak: a kernel of independent FMA chains,
+    CUDA events on the launching stream) with the SM clock sampled while it runs."""
+    from paper_2512_19847_gb300 import api
+    api.fma_peak(precision, iters, 2)                   # warm-up (module load, clocks up)
+    with ClockSampler(local) as clk:
+        tf, ms = api.fma_peak(precision, iters, reps)
+    c = clk.summary()
+    return {"tflops": round(tf, 4), "ms_per_launch": round(ms, 3), "launches": reps, "clocks": c,
+            "dtype": "f64" if precision == api.FP64 else "f32"}
+
+
+def scaled_peak(leg: dict, run_clocks: dict) -> dict:
+    """The leg's peak scaled to the timed run's median SM clock (the FMA rate is
+    proportional to the clock)."""
+    f_leg, f_run = leg["clocks"].get("sm_mhz"), run_clocks.get("sm_mhz")
+    scale = (f_run / f_leg) if (f_leg and f_run) else 1.0
+    src = (f"bench.py FP64 FMA-chain leg (ap_dvm_fma_peak): {leg['tflops']} TFLOP/s at {f_leg} MHz median SM clock, "
+           f"scaled to the timed run's {f_run} MHz")
+    return {"tflops_at_run_clock": leg["tflops"] * scale, "source": src}
+
+
+# ----------------------------------------------------------------- the oracle on the host cores
+_ORACLE_STATE = {}
+
+
+def _oracle_init(n, eps, tau, dt):
+    """Worker set-up (spawned process): the workload's initial state and parameters."""
+    from oracle import ap_dvm_oracle as O
+    from paper_2512_19847_gb300 import workloads as W
+    A_ex, _, A_im, _ = O.tableau_gsa2()
+    _ORACLE_STATE["p"] = O.Params(n, n, eps, tau, dt, A_ex, A_im, scheme="WENO5_C4")
+    _ORACLE_STATE["X"] = O.equilibrium_state(*W.taylor_green(n))
+
+
+def _oracle_steps(nsteps):
+    """Advance this worker's replica by nsteps oracle IMEX steps; returns the seconds taken."""
+    from oracle import ap_dvm_oracle as O
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        _ORACLE_STATE["X"] = O.step(_ORACLE_STATE["X"], _ORACLE_STATE["p"])
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool_size(n: int, want: int) -> int:
+    """Workers for the all-core figure: every host core, capped so that the
+    replicas (about 80 planes of n^2 float64 each, stage caches included) fit in
+    half of the host memory."""
+    try:
+        mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError, AttributeError):
+        mem = 64e9
+    per = 80 * n * n * 8
+    return max(1, min(want, int(0.5 * mem // per)))
+
+
+class OraclePool:
+    """P spawned processes, each holding its own replica of the workload: one
+    'step' advances every replica by one oracle IMEX step (independent
+    replicas on the host cores, the oracle's all-core throughput).  Started
+    with 'spawn' so that no worker inherits a CUDA context."""
+
+    def __init__(self, procs: int, n, eps, tau, dt):
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(n, eps, tau, dt))
+
+    def step(self, nsteps: int = 1) -> float:
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_steps, [nsteps] * self.procs, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def cpu_baseline(n, eps, mach, tau, dt, fields, nsteps=1):
-    """The oracle as it stands, on the host, one full-size IMEX step."""
-    import numpy as np
+    """The oracle as it stands on the host: one IMEX step of the full-size
+    workload on one core, and one step on each of P independent replicas in P
+    processes (all host cores, memory permitting)."""
     from oracle import ap_dvm_oracle as O
     A_ex, _, A_im, _ = O.tableau_gsa2()
     X = O.equilibrium_state(*fields)
@@ -257,9 +340,22 @@ def cpu_baseline(n, eps, mach, tau, dt, fields, nsteps=1):
     t0 = time.perf_counter()
     for _ in range(nsteps):
         X = O.step(X, p)
-    el = time.perf_counter() - t0
-    return {"value": round(n * n * nsteps / el / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} IMEX step(s) of the {n}x{n} workload, numpy float64, 1 thread ({el:.1f} s)"}
+    el1 = time.perf_counter() - t0
+    v1 = n * n * nsteps / el1 / 1e6
+    ncores = host_cores()
+    procs = oracle_pool_size(n, ncores)
+    pool = OraclePool(procs, n, eps, tau, dt)
+    try:
+        pool.step(0)                     # workers up, state built
+        elp = pool.step(nsteps)
+    finally:
+        pool.close()
+    vp = procs * n * n * nsteps / elp / 1e6
+    return {"value": round(vp, 4), "unit": UNIT, "cores": procs, "kind": "oracle", "nproc": ncores,
+            "single_core_value": round(v1, 4),
+            "sample": (f"{nsteps} IMEX step(s) of the {n}x{n} workload (numpy float64): on {procs} independent "
+                       f"replicas in {procs} spawned processes, one thread each ({elp:.1f} s; value), and on one "
+                       f"core ({el1:.1f} s; single_core_value); host nproc = {ncores}")}
 
 
 def run_batched(torch, count=256, steps=200, seed=2512):
@@ -359,29 +455,33 @@ def load_peaks():
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (the only other implementation of the
+    method) as it stands, on the host cores, on the same 2048^2 workload.  A
+    step advances P independent replicas (P spawned processes, one per host
+    core, memory permitting) by one oracle IMEX step each."""
     if rank != 0:
         return
-    n = args.ref_n
-    fields, dt = workload(n, args.eps, args.mach, args.tau)
-    import numpy as np
-    from oracle import ap_dvm_oracle as O
-    A_ex, _, A_im, _ = O.tableau_gsa2()
-    p = O.Params(n, n, args.eps, args.tau, dt, A_ex, A_im, scheme="WENO5_C4")
-    X = O.equilibrium_state(*fields)
-    for _ in range(args.warmup):
-        X = O.step(X, p)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        X = O.step(X, p)
-    el = time.perf_counter() - t0
-    v = n * n * args.steps / el / 1e6
-    sample = (f"one IMEX step of the same scheme on a {n}x{n} Taylor-Green grid per step "
-              f"(the oracle's Mcell/s is size-independent within ~15% from 256^2 to 1024^2)")
+    n = args.n
+    _, dt = workload(n, args.eps, args.mach, args.tau)
+    ncores = host_cores()
+    procs = oracle_pool_size(n, ncores)
+    pool = OraclePool(procs, n, args.eps, args.tau, dt)
+    try:
+        pool.step(0)
+        for _ in range(args.warmup):
+            pool.step(1)
+        el = pool.step(args.steps)
+    finally:
+        pool.close()
+    v = procs * n * n * args.steps / el / 1e6
+    sample = (f"one IMEX step of the {n}x{n} workload on each of {procs} independent replicas per step "
+              f"({procs} spawned processes, one numpy thread each; host nproc = {ncores})")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args),
-            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": procs, "nproc": ncores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -404,11 +504,11 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--mach", type=float, default=1e-3)
     ap.add_argument("--tau", type=float, default=0.05)
-    ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--fp64-peak", action="store_true", help="print only the FMA-peak legs (FP64 and FP32) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -431,12 +531,20 @@ def main():
             dist.barrier()
 
     n, cells = args.n, args.n * args.n
+    from paper_2512_19847_gb300 import api
+    if args.fp64_peak:
+        legs = {"fp64": fma_peak_leg(local, api.FP64, 256), "fp32": fma_peak_leg(local, api.FP32_DEV, 16384)}
+        if rank == 0:
+            print(json.dumps({"fma_peak": legs}), flush=True)
+        return
     fields, dt = workload(n, args.eps, args.mach, args.tau)
     peaks = load_peaks()
 
     with ClockSampler(local) as clk:
         s64, ms64 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, False, args.steps, args.warmup, barrier)
     clocks = clk.summary()
+    fp64_leg = fma_peak_leg(local, api.FP64, 256)
+    fp64_peak = scaled_peak(fp64_leg, clocks)
     s32, ms32 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, True, args.steps, args.warmup, barrier)
 
     v64, ms64 = replica_rate(ms64, cells, args.steps, dist, "cuda")
@@ -454,7 +562,7 @@ def main():
     # per-kernel CUDA-event profile on the launching stream, dominant kernel roofline
     prof64 = profile_form(s64, args.profile_steps)
     prof32 = profile_form(s32, args.profile_steps)
-    k64, roof64 = roofline(prof64, args.profile_steps, cells, False, "WENO5_C4", n, peaks)
+    k64, roof64 = roofline(prof64, args.profile_steps, cells, False, "WENO5_C4", n, peaks, fp64_peak)
     k32, roof32 = roofline(prof32, args.profile_steps, cells, True, "WENO5_C4", n, peaks)
     launches64 = s64.launches_per_step * args.steps
 
@@ -498,6 +606,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches64,
         "clocks": clocks,
+        "fma_peak_fp64": fp64_leg,
         "fp32_dev": {"value": round(v32, 3), "unit": UNIT, "ms_per_step": round(ms32 / args.steps, 4),
                      "dtype": "f32 transport, f64 moment sums and relaxation (eps<=1e-4)",
                      "velocity_rel_err_vs_fp64": vel_err, "pressure_rel_err_vs_fp64": pr_err,

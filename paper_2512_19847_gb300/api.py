@@ -108,6 +108,8 @@ def lib():
         "ap_dvm_last_error": (ctypes.c_char_p, [H]),
         "ap_dvm_destroy": (None, [H]),
         "ap_dvm_default_params": (None, [P, i32, i32, f64, f64]),
+        "ap_dvm_step_noalloc": (i32, [P, vp, i32, vp]),
+        "ap_dvm_fma_peak": (i32, [i32, i32, i32, vp, ctypes.POINTER(f64), ctypes.POINTER(f64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -129,6 +131,16 @@ def default_params(nx: int, ny: int | None = None, eps: float = 1e-2, dt: float 
             continue
         setattr(p, k, v)
     return p
+
+
+def fma_peak(precision: int = FP64, iters: int = 256, reps: int = 50, stream=None) -> tuple[float, float]:
+    """ap_dvm_fma_peak: (TFLOP/s, ms per launch) of an FMA-chain kernel in FP64
+    (precision = FP64) or FP32 (FP32_DEV) on the current GPU."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib().ap_dvm_fma_peak(int(precision), int(iters), int(reps), _stream_ptr(stream), ctypes.byref(tf), ctypes.byref(ms))
+    if st != 0:
+        raise ApDvmError(st, "ap_dvm_fma_peak failed")
+    return tf.value, ms.value
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:

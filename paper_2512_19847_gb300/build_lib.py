@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libapdvm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["api", "noalloc", "k_misc", "k_f64_lf1", "k_f64_w3", "k_f64_w5", "k_f32_lf1", "k_f32_w3", "k_f32_w5"]
+UNITS = ["api", "noalloc", "k_misc", "k_peak", "k_f64_lf1", "k_f64_w3", "k_f64_w5", "k_f32_lf1", "k_f32_w3", "k_f32_w5"]
 
 
 def nvcc() -> str:
