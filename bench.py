@@ -64,7 +64,7 @@ def step_flops_per_cell(scheme: str, n: int) -> dict:
     cols = 2 * (5 * lg + 2.5)
     update = (6 + 4 * FP + 2 + 2 * c1 + (2 * c1 + 1) + 6 + 4 + 8) + (10 + 4 * FP + 2 + 2 * c1 + (2 * c1 + 1) + 12 + 4 + 13)
     return {"explicit": explicit, "rhs": rhs, "fft_rows_fwd": rows, "fft_cols": cols,
-            "fft_rows_inv": rows, "update": update, "finish": 0}
+            "fft_rows_inv": rows, "update": update}
 
 
 def step_bytes_per_cell(f32: bool) -> dict:
@@ -81,10 +81,10 @@ def step_bytes_per_cell(f32: bool) -> dict:
         # each pass reads and writes one plane-equivalent (real plane or half spectrum), two solves
         "fft_rows_fwd": 4, "fft_cols": 4, "fft_rows_inv": 4,
         # stage 2: read theta, v, u^(1), u^n, q^n (8), write u, q, D0.v (4);
-        # stage 3: read theta, v, u^(1), u^(2), u^n, q^n, D_LF.B(v)^(2), D0 theta^(2), D0.v^(2), q^(2) (16), write 4
-        "update": (8 + 4) + (16 + 4),
-        # FP64: X^(s) -> X; FP32: read X^(s), write the populations and the next step's FP64-summed moments
-        "finish": 18 if f32 else 12}
+        # stage 3: read theta, v, u^(1), u^(2), u^n, q^n, D_LF.B(v)^(2), D0 theta^(2), D0.v^(2), q^(2) (16),
+        # and close the step: write X^{n+1} (6; FP32 forms: the populations and the next step's
+        # FP64-summed moments, 12)
+        "update": (8 + 4) + (16 + (12 if f32 else 6))}
     return {k: v * e for k, v in planes.items()}
 
 
@@ -358,19 +358,52 @@ def cpu_baseline(n, eps, mach, tau, dt, fields, nsteps=1):
                        f"core ({el1:.1f} s; single_core_value); host nproc = {ncores}")}
 
 
-def run_batched(torch, count=256, steps=200, seed=2512):
+def fp32_errors(X32: np.ndarray, X64: np.ndarray) -> tuple[float, float]:
+    """Max relative velocity error and pressure error (p = theta - |u|^2/2, mean
+    removed, relative to the FP64 pressure's range) of an FP32-form state
+    against the FP64 form's state after the same steps."""
+    umax = float(np.max(np.hypot(X64[0], X64[1])))
+    vel = float(np.max(np.hypot(X32[0] - X64[0], X32[1] - X64[1])) / umax)
+    p64 = X64[2] - 0.5 * (X64[0] ** 2 + X64[1] ** 2)
+    p32 = X32[2] - 0.5 * (X32[0] ** 2 + X32[1] ** 2)
+    p64, p32 = p64 - p64.mean(), p32 - p32.mean()
+    return vel, float(np.max(np.abs(p32 - p64)) / max(float(np.max(np.abs(p64))), 1e-300))
+
+
+def _finite_slots(b, slots) -> list:
+    """Slots whose state is finite (the batch's non-finite flag is global)."""
+    import torch
+    return [k for k in slots if bool(torch.isfinite(b.get_state(k)).all())]
+
+
+def _sync_allow_nonfinite(b) -> bool:
+    """sync_status that reports a non-finite state instead of raising; other errors raise."""
+    from paper_2512_19847_gb300 import api
+    try:
+        b.sync_status()
+        return True
+    except api.ApDvmError as e:
+        if e.status != 5:
+            raise
+        return False
+
+
+def run_batched(torch, count=256, steps=200, seed=2512, sample=16):
     """Batched form: `count` seeded uneven instances (side uniform in
-    {64,128,256,512}, eps log-uniform [1e-6,0.5], Ma log-uniform [1e-3,1e-1],
+    {64,128,256,512}, eps log-uniform [1e-6,1], Ma log-uniform [1e-3,1e-1],
     random divergence-free fields, tau = 0.05), FP32 deviation storage, tile
-    chosen by the autotuner, all `steps` steps replayed as one CUDA graph."""
+    chosen by the autotuner, all `steps` steps replayed as one CUDA graph.  At
+    eps ~ 1 (far from the low-Mach regime) some random fields grow without bound
+    under the time-step rule: the oracle does the same at the same step
+    (tests/test_gpu_experiments.py), so they are counted, not removed.  The FP32
+    form's velocity and pressure errors are stated against the FP64 form on a
+    seeded sample of `sample` of the instances that stay finite."""
     from paper_2512_19847_gb300 import api, autotune, tableaux, workloads as W
-    # eps up to 0.5: at eps ~ 1 with O(1) velocities the 512^2 random fields blow up at a
-    # time that does not depend on dt (a property of the discrete model there, not of
-    # the time step)
-    draws = W.batched_draws(count, seed=seed, steps=steps, eps_range=(1e-6, 0.5))
+    draws = W.batched_draws(count, seed=seed, steps=steps, eps_range=(1e-6, 1.0))
     tmpl = api.default_params(512, 512, eps=1e-2, dt=1e-3, tau=0.05, tableau=tableaux.gsa2(), precision=api.FP32_DEV)
     b = api.Batch(tmpl, capacity=count)
     cells = 0
+    prms = []
     for k, d in enumerate(draws):
         u1, u2, p = W.random_divfree(d.n, d.seed)
         prm = tmpl.copy()
@@ -379,11 +412,12 @@ def run_batched(torch, count=256, steps=200, seed=2512):
         prm.dt = W.stable_dt(u1, u2, 2 * math.pi / d.n, prm.tau)
         b.attach(k, prm)
         b.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, p)], slot=k)
+        prms.append(prm)
         cells += d.n * d.n
     tuned = autotune.tune(b, steps=2, path=None)
     b.set_graph_steps(steps)
     b.step(steps)                          # warm-up (also builds the graph)
-    b.sync_status()
+    _sync_allow_nonfinite(b)
     torch.cuda.synchronize()
     for k, d in enumerate(draws):          # restart from the initial data
         u1, u2, p = W.random_divfree(d.n, d.seed)
@@ -394,19 +428,43 @@ def run_batched(torch, count=256, steps=200, seed=2512):
     b.step(steps)                          # one graph launch
     e1.record(st)
     e1.synchronize()
-    b.sync_status()
     ms = e0.elapsed_time(e1)
+    _sync_allow_nonfinite(b)
+    finite = _finite_slots(b, range(count))
+    blown = [{"n": draws[k].n, "eps": round(draws[k].eps, 4)} for k in range(count) if k not in set(finite)]
+    # FP32 error against the FP64 form on a seeded sample of the finite instances
+    rng = np.random.default_rng(seed + 1)
+    pick = sorted(rng.choice(finite, size=min(sample, len(finite)), replace=False).tolist())
+    t64 = tmpl.copy()
+    t64.precision = api.FP64
+    b64 = api.Batch(t64, capacity=len(pick))
+    for j, k in enumerate(pick):
+        q = prms[k].copy()
+        q.precision = api.FP64
+        b64.attach(j, q)
+        u1, u2, p = W.random_divfree(draws[k].n, draws[k].seed)
+        b64.set_equilibrium(*[torch.from_numpy(a).cuda() for a in (u1, u2, p)], slot=j)
+    b64.set_tile(3)
+    b64.step(steps)
+    b64.sync_status()
+    errs = [fp32_errors(b.get_state(k).cpu().numpy(), b64.get_state(j).cpu().numpy()) for j, k in enumerate(pick)]
     return {"value": round(cells * steps / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "instances": count,
             "cells": cells, "steps": steps, "ms": round(ms, 2), "graph_launches": 1,
             "kernel_launches": b.launches_per_step * steps, "tile": tuned["tile"],
-            "tile_ms_per_step": tuned["ms_per_step"], "dtype": "f32 deviation storage"}
+            "tile_ms_per_step": tuned["ms_per_step"], "dtype": "f32 deviation storage",
+            "eps_range": [1e-6, 1.0], "nonfinite_instances": blown,
+            "velocity_rel_err_vs_fp64": max(e[0] for e in errs), "pressure_rel_err_vs_fp64": max(e[1] for e in errs),
+            "error_sample": f"max over {len(pick)} seeded instances of the {len(finite)} finite ones (FP64 form, same draws)"}
 
 
-def run_served(torch, n_requests=48, budget=120e9, load=0.8, v_ref=None, seed=7):
+def run_served(torch, n_requests=500, budget=120e9, load=0.8, v_ref=None, seed=7, sample=8, alone=True):
     """Served form: open-loop Poisson stream (side uniform {128,256,512,1024},
-    eps log-uniform [1e-6,1e-1], 50-500 steps, tau = 0.05), admitted by an HBM
-    budget into one continuous batch (FP32 deviation form), against the same
-    stream served one solve at a time with the plain per-solve path."""
+    eps log-uniform [1e-6,1e-1], 50-500 steps, tau = 0.05) at `load` times the
+    stream rate the batched form sustains (v_ref Mcell-updates/s), admitted by an
+    HBM budget into one continuous batch (FP32 deviation form), against the same
+    stream served one solve at a time with the plain per-solve path.  The FP32
+    form's errors are stated against the FP64 form, each of a seeded sample of
+    `sample` requests re-run alone in FP64."""
     from paper_2512_19847_gb300 import api, serve, tableaux, workloads as W
     sides, steps_rng = (128, 256, 512, 1024), (50, 500)
     mean_work = np.mean([n * n for n in sides]) * np.mean(steps_rng)
@@ -425,10 +483,41 @@ def run_served(torch, n_requests=48, budget=120e9, load=0.8, v_ref=None, seed=7)
     tile = 2                                             # 16x8: the autotuner's pick for the FP32 form at 2048^2 and for the batched mix
     srv = serve.Server(tmpl, capacity=n_requests, hbm_budget=budget, chunk=10, tile=tile)
     mixed = srv.run(jobs).summary()
-    alone_jobs = serve.make_jobs(reqs, tmpl, fields)
-    alone = serve.run_alone(alone_jobs, tile=tile).summary()
-    mixed.update({"rate_hz": round(rate, 3), "hbm_budget_gb": budget / 1e9, "chunk_steps": 10, "tile": tile})
-    return {"continuous_batching": mixed, "alone_per_solve": alone}
+    mixed.update({"load": load, "rate_hz": round(rate, 3), "hbm_budget_gb": budget / 1e9, "chunk_steps": 10, "tile": tile})
+    # FP32 errors: a seeded sample of the served results against FP64 re-runs of the same requests
+    rng = np.random.default_rng(seed + 1)
+    errs = []
+    for k in sorted(rng.choice(len(jobs), size=min(sample, len(jobs)), replace=False).tolist()):
+        j = jobs[k]
+        q = j.params.copy()
+        q.precision = api.FP64
+        s64 = api.Solver(q)
+        s64.set_tile(3)
+        s64.set_graph_steps(1)
+        s64.set_equilibrium(*[t.to("cuda") for t in j.fields])
+        s64.step(j.steps)
+        s64.sync_status()
+        errs.append(fp32_errors(j.result.numpy(), s64.get_state().cpu().numpy()))
+    mixed.update({"velocity_rel_err_vs_fp64": max(e[0] for e in errs), "pressure_rel_err_vs_fp64": max(e[1] for e in errs),
+                  "error_sample": f"max over {len(errs)} seeded requests, each re-run alone in FP64"})
+    out = {"continuous_batching": mixed}
+    if alone:
+        alone_jobs = serve.make_jobs(reqs, tmpl, fields)
+        out["alone_per_solve"] = serve.run_alone(alone_jobs, tile=tile).summary()
+    return out
+
+
+def run_served_sweep(torch, v_ref, loads=(0.5, 0.7, 0.9), n_requests=500):
+    """p50/p99 and Mcell-updates/s of the served form and of the per-solve path at
+    several arrival rates (fractions of the batched form's sustained rate)."""
+    rows = []
+    for ld in loads:
+        r = run_served(torch, n_requests=n_requests, load=ld, v_ref=v_ref, sample=2)
+        c, a = r["continuous_batching"], r["alone_per_solve"]
+        rows.append({"load": ld, "rate_hz": c["rate_hz"], "batched_p50_ms": c["p50_ms"], "batched_p99_ms": c["p99_ms"],
+                     "batched_mcells": c["value"], "alone_p50_ms": a["p50_ms"], "alone_p99_ms": a["p99_ms"],
+                     "alone_mcells": a["value"], "max_resident": c["max_resident"]})
+    return rows
 
 
 def replica_rate(ms_local: float, cells: int, steps: int, dist=None, device: str = "cuda"):
@@ -509,6 +598,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--fp64-peak", action="store_true", help="print only the FMA-peak legs (FP64 and FP32) and exit")
+    ap.add_argument("--served-sweep", action="store_true", help="also sweep the served form's arrival rate")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -553,11 +643,7 @@ def main():
     # accuracy of the FP32 deviation form against the FP64 result after the same steps
     X64 = s64.get_state().cpu().numpy()
     X32 = s32.get_state().cpu().numpy()
-    ref_p = X64[2] - 0.5 * (X64[0] ** 2 + X64[1] ** 2)
-    p32 = X32[2] - 0.5 * (X32[0] ** 2 + X32[1] ** 2)
-    umax = float(np.max(np.hypot(X64[0], X64[1])))
-    vel_err = float(np.max(np.hypot(X32[0] - X64[0], X32[1] - X64[1])) / umax)
-    pr_err = float(np.max(np.abs((p32 - p32.mean()) - (ref_p - ref_p.mean()))) / float(np.max(np.abs(ref_p - ref_p.mean()))))
+    vel_err, pr_err = fp32_errors(X32, X64)
 
     # per-kernel CUDA-event profile on the launching stream, dominant kernel roofline
     prof64 = profile_form(s64, args.profile_steps)
@@ -589,7 +675,9 @@ def main():
             return {"error": f"{type(e).__name__}: {e}"[:300]}
 
     batched = None if args.no_batched else leg(run_batched, torch)
-    served = None if args.no_served else leg(run_served, torch, v_ref=(batched or {}).get("value", v32))
+    v_ref = (batched or {}).get("value", v32) if isinstance(batched, dict) and "value" in (batched or {}) else v32
+    served = None if args.no_served else leg(run_served, torch, v_ref=v_ref)
+    sweep = leg(run_served_sweep, torch, v_ref) if args.served_sweep else None
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -613,6 +701,7 @@ def main():
                      "roofline": roof32, "gpu_launches": s32.launches_per_step * args.steps},
         "batched": batched,
         "served": served,
+        "served_sweep": sweep,
         "kernels_fp64_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in prof64.items()},
         "kernels_fp32_ms_per_step": {k: round(v[0] / args.profile_steps, 4) for k, v in prof32.items()},
     }

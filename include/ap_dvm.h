@@ -50,7 +50,7 @@ typedef enum {
 
 enum { AP_DVM_D2V6 = 6 };                                        /* velocity set (Sec. 2.1) */
 enum { AP_DVM_LF1_C2 = 0, AP_DVM_WENO3_C4 = 1, AP_DVM_WENO5_C4 = 2 }; /* spatial scheme (Sec. 3.2) */
-enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1 };                   /* precision form */
+enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1, AP_DVM_FP32_DEV_TH = 2 }; /* precision form */
 #define AP_DVM_MAX_STAGES 4
 
 /* Parameters of one solve.
@@ -83,6 +83,13 @@ enum { AP_DVM_FP64 = 0, AP_DVM_FP32_DEV = 1 };                   /* precision fo
  *  precision   AP_DVM_FP64 (all in FP64) or AP_DVM_FP32_DEV (FP32 deviation
  *              populations and FP32 transport; FP64 moment sums, division by
  *              rho0*mach, and closed-form relaxation when eps <= 1e-4).
+ *              AP_DVM_FP32_DEV_TH is AP_DVM_FP32_DEV with theta carried from
+ *              step to step in its own FP32 plane beside the populations
+ *              instead of being summed back from them: theta rides at O(eps)
+ *              inside the populations, so summing it from FP32 populations
+ *              costs ~6e-8/eps of its relative precision (the pressure error
+ *              of AP_DVM_FP32_DEV); the populations are written as in
+ *              AP_DVM_FP32_DEV.
  *  weno_eps    epsilon of the WENO weights (1e-6 by default); at least 1e-30
  *              (FP64) or 1e-9 (FP32 form), so that the products and
  *              reciprocals of the smoothness terms stay in range.
@@ -149,7 +156,14 @@ ap_dvm_status ap_dvm_set_equilibrium(ap_dvm_handle* h, int slot, const double* d
 /* Set the state from 6 population planes: double (FP64 form or FP32 form),
  * or float (is_float = 1, FP32 form only). */
 ap_dvm_status ap_dvm_set_populations(ap_dvm_handle* h, int slot, const void* d_dF6, int is_float);
-/* Read the moment state into 6 double planes. */
+/* AP_DVM_FP32_DEV_TH only: overwrite the carried theta plane with d_theta
+ * (one double plane, rounded once to FP32), e.g. after ap_dvm_set_populations,
+ * which sums theta from the populations; with the populations read by
+ * ap_dvm_get_populations (float) and theta by ap_dvm_get_state, the two calls
+ * restore a solve bit for bit.  AP_DVM_ERR_ARG in the other forms. */
+ap_dvm_status ap_dvm_set_theta(ap_dvm_handle* h, int slot, const double* d_theta);
+/* Read the moment state into 6 double planes (the FP32 forms: the moments of the
+ * populations in FP64, with the carried theta in AP_DVM_FP32_DEV_TH). */
 ap_dvm_status ap_dvm_get_state(ap_dvm_handle* h, int slot, double* d_moments6);
 /* Read the populations into 6 planes (double, or float when is_float = 1). */
 ap_dvm_status ap_dvm_get_populations(ap_dvm_handle* h, int slot, void* d_dF6, int is_float);

@@ -19,7 +19,7 @@ MAX_STAGES = 4
 D2V6 = 6
 LF1_C2, WENO3_C4, WENO5_C4 = 0, 1, 2
 SCHEMES = {"LF1_C2": LF1_C2, "WENO3_C4": WENO3_C4, "WENO5_C4": WENO5_C4}
-FP64, FP32_DEV = 0, 1
+FP64, FP32_DEV, FP32_DEV_TH = 0, 1, 2
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_TABLEAU", 3: "ERR_WORKSPACE", 4: "ERR_CUDA",
           5: "ERR_NONFINITE", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
@@ -91,6 +91,7 @@ def lib():
         "ap_dvm_set_equilibrium": (i32, [H, i32, vp, vp, vp]),
         "ap_dvm_set_populations": (i32, [H, i32, vp, i32]),
         "ap_dvm_get_state": (i32, [H, i32, vp]),
+        "ap_dvm_set_theta": (i32, [H, i32, vp]),
         "ap_dvm_get_populations": (i32, [H, i32, vp, i32]),
         "ap_dvm_moments": (i32, [H, i32, vp, vp, vp, vp]),
         "ap_dvm_diagnostics": (i32, [H, i32, vp, ctypes.POINTER(f64)]),
@@ -197,6 +198,13 @@ class _Handle:
         assert dF.is_cuda and dF.shape == (6, *self._shape(slot)) and dF.dtype in (torch.float64, torch.float32)
         self._keep[("in", slot)] = dF
         self._check(lib().ap_dvm_set_populations(self._h, slot, _ptr(dF), int(dF.dtype == torch.float32)))
+
+    def set_theta(self, theta: torch.Tensor, slot: int = 0):
+        """FP32_DEV_TH: overwrite the carried theta plane ((ny, nx) float64 CUDA tensor)."""
+        theta = theta.contiguous()
+        assert theta.dtype == torch.float64 and theta.is_cuda and theta.shape == self._shape(slot)
+        self._keep[("theta", slot)] = theta
+        self._check(lib().ap_dvm_set_theta(self._h, slot, _ptr(theta)))
 
     def get_state(self, slot: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
         out = torch.empty((6, *self._shape(slot)), dtype=torch.float64, device=self.device) if out is None else out

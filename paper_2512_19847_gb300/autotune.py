@@ -40,16 +40,20 @@ def _save(h):
     saved = {}
     for slot, p in _params_of(h).items():
         if p.precision == api.FP32_DEV:
-            saved[slot] = h.get_populations(slot, dtype=torch.float32)
+            saved[slot] = (h.get_populations(slot, dtype=torch.float32), None)
+        elif p.precision == api.FP32_DEV_TH:   # the populations and the carried theta plane
+            saved[slot] = (h.get_populations(slot, dtype=torch.float32), h.get_state(slot)[2].clone())
         else:
-            saved[slot] = h.get_state(slot)
+            saved[slot] = (h.get_state(slot), None)
     return saved
 
 
 def _restore(h, saved):
-    for slot, X in saved.items():
+    for slot, (X, theta) in saved.items():
         if X.dtype == torch.float32:
             h.set_populations(X, slot)
+            if theta is not None:
+                h.set_theta(theta, slot)
         else:
             h.set_state(X, slot)
 

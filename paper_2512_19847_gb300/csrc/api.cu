@@ -37,9 +37,25 @@ struct Slot {
   ap_dvm_params p{};
   char* ws = nullptr;
   size_t bytes = 0;
-  InstDev dev{};
-  CUtensorMap maps[APD_MAXS + 1];   // host copies of the stage-buffer tensor maps
+  InstDev dev{};                        // as carved: X = state buffer 0, Xnext = buffer 1
+  CUtensorMap maps[2][APD_MAXS + 1];    // host copies of the stage-buffer tensor maps, per parity
 };
+
+// The instance as the kernels of a step of the given parity see it: the state
+// is double-buffered (even steps read buffer 0 and close into buffer 1, odd
+// steps the reverse); stage 1 of a CK/ARS tableau is the state itself.
+InstDev view(const Slot& s, int parity) {
+  InstDev d = s.dev;
+  void* buf[2] = {s.dev.X, s.dev.Xnext};
+  d.X = buf[parity];
+  d.Xnext = buf[parity ^ 1];
+  if (s.p.A_im[0] == 0.0) {
+    d.Xs[1] = d.X;
+    d.Dun = d.Du[1];
+  }
+  d.tmap = reinterpret_cast<const char*>(s.dev.tmap) + (size_t)parity * sizeof(CUtensorMap) * (APD_MAXS + 1);
+  return d;
+}
 
 struct ap_dvm_handle {
   ap_dvm_params tmpl{};
@@ -50,10 +66,10 @@ struct ap_dvm_handle {
   int num_sms = 0;
   int tile = 0;
   bool tile_auto = true;
-  int nmax = 0, lnmax = 0, eblk = 0;
+  int nmax = 0, lnmax = 0, eblk = 0, eblk_cols = 0;
   // batch workspace
-  BatchDev* d_batch = nullptr;
-  InstDev* d_inst = nullptr;
+  BatchDev* d_batch[2] = {nullptr, nullptr};   // per step parity (double-buffered state)
+  InstDev* d_inst[2] = {nullptr, nullptr};
   int* d_tile_start = nullptr;
   int* d_row_start = nullptr;
   int* d_col_start = nullptr;
@@ -61,26 +77,27 @@ struct ap_dvm_handle {
   double2* d_tw = nullptr;
   float2* d_tw32 = nullptr;
   unsigned* d_err = nullptr;
-  BatchDev hb{};
+  BatchDev hb[2]{};
+  int parity = 0;                    // parity of the next step: which state buffer it reads
   std::vector<Slot> slots;
   bool dirty = true;
   int n_active = 0;
   // upload staging (kept alive across async copies)
-  std::vector<InstDev> up_inst;
+  std::vector<InstDev> up_inst[2];
   std::vector<int> up_tiles, up_rows, up_cols;
   int up_counts[4] = {0, 0, 0, 0};
   // kernels
   StencilSet ks{};
   MiscSet km{};
-  int grid_explicit = 0, grid_rhs = 0, grid_update = 0, grid_fft = 0, grid_finish = 0;
+  int grid_explicit = 0, grid_rhs = 0, grid_update = 0, grid_fft = 0, grid_cols = 0, grid_finish = 0;
   unsigned fft_kinds = 0;   // FftKinds of the attached solves (the launches a step enqueues)
   size_t smem_update = 0;
   bool kernels_ready = false;
   // graph
   int graph_steps = 0;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // per starting parity
   cudaStream_t cap_stream = nullptr;
-  bool graph_valid = false;
+  bool graph_valid[2] = {false, false};
   // per-kernel CUDA-event profile (direct launches only)
   bool profile = false;
   std::vector<cudaEvent_t> ev;
@@ -161,9 +178,13 @@ ap_dvm_status validate(const ap_dvm_params* p, char* buf, size_t n) {
   if (!(p->dt > 0) || !std::isfinite(p->dt)) { snprintf(buf, n, "dt must be > 0"); return AP_DVM_ERR_ARG; }
   if (!std::isfinite(p->tau)) { snprintf(buf, n, "tau must be finite"); return AP_DVM_ERR_ARG; }
   if (p->space_scheme < AP_DVM_LF1_C2 || p->space_scheme > AP_DVM_WENO5_C4) { snprintf(buf, n, "unknown space_scheme"); return AP_DVM_ERR_ARG; }
-  if (p->precision != AP_DVM_FP64 && p->precision != AP_DVM_FP32_DEV) { snprintf(buf, n, "unknown precision"); return AP_DVM_ERR_ARG; }
-  if (p->precision == AP_DVM_FP32_DEV && !(p->eps > 0)) { snprintf(buf, n, "the FP32 deviation form needs eps > 0 (population view)"); return AP_DVM_ERR_ARG; }
-  if (!(p->weno_eps >= (p->precision == AP_DVM_FP32_DEV ? 1e-9 : 1e-30))) {
+  if (p->precision != AP_DVM_FP64 && p->precision != AP_DVM_FP32_DEV && p->precision != AP_DVM_FP32_DEV_TH) {
+    snprintf(buf, n, "unknown precision");
+    return AP_DVM_ERR_ARG;
+  }
+  const bool f32 = p->precision != AP_DVM_FP64;
+  if (f32 && !(p->eps > 0)) { snprintf(buf, n, "the FP32 deviation form needs eps > 0 (population view)"); return AP_DVM_ERR_ARG; }
+  if (!(p->weno_eps >= (f32 ? 1e-9 : 1e-30))) {
     snprintf(buf, n, "weno_eps must be >= 1e-30 (FP64) or >= 1e-9 (FP32 form)");
     return AP_DVM_ERR_ARG;
   }
@@ -193,8 +214,8 @@ bool same_method(const ap_dvm_params& a, const ap_dvm_params& b) {
 size_t batch_bytes(int capacity, int nmax) {
   size_t off = 0;
   auto take = [&](size_t b) { off = align_up(off, 256); off += b; };
-  take(sizeof(BatchDev));
-  take(sizeof(InstDev) * capacity);
+  take(sizeof(BatchDev) * 2);
+  take(sizeof(InstDev) * capacity * 2);
   take(sizeof(int) * (capacity + 1));
   take(sizeof(int) * (capacity + 1));
   take(sizeof(int) * (capacity + 1));
@@ -248,7 +269,8 @@ ap_dvm_status occupancy_grid(ap_dvm_handle* h, const void* fn, int threads, size
   return AP_DVM_OK;
 }
 
-size_t fft_smem(const ap_dvm_handle* h) { return (size_t)h->eblk * 2 * (h->f32 ? 4 : 8); }
+size_t fft_smem(const ap_dvm_handle* h) { return fft_block_bytes(h->eblk, h->f32); }
+size_t cols_smem(const ap_dvm_handle* h) { return fft_block_bytes(h->eblk_cols, h->f32); }
 
 ap_dvm_status prepare_kernels(ap_dvm_handle* h) {
   if (h->kernels_ready) return AP_DVM_OK;
@@ -263,14 +285,14 @@ ap_dvm_status prepare_kernels(ap_dvm_handle* h) {
   if ((st = occupancy_grid(h, h->ks.k_update, thr, h->smem_update, &h->grid_update))) return st;
   if ((st = occupancy_grid(h, h->km.k_finish, thr, 0, &h->grid_finish))) return st;
   h->grid_fft = 1 << 30;
-  for (const void* fn : {h->km.k_rows_fwd, h->km.k_cols, h->km.k_rows_inv, h->km.k_rows_fwd_bs, h->km.k_cols_bs,
-                         h->km.k_rows_inv_bs}) {
+  for (const void* fn : {h->km.k_rows_fwd, h->km.k_rows_inv, h->km.k_rows_fwd_bs, h->km.k_cols_bs, h->km.k_rows_inv_bs}) {
     int g = 0;
     if ((st = occupancy_grid(h, fn, 256, fft_smem(h), &g))) return st;
     h->grid_fft = std::min(h->grid_fft, g);
   }
+  if ((st = occupancy_grid(h, h->km.k_cols, h->f32 ? 1024 : 256, cols_smem(h), &h->grid_cols))) return st;
   h->kernels_ready = true;
-  h->graph_valid = false;
+  h->graph_valid[0] = h->graph_valid[1] = false;
   return AP_DVM_OK;
 }
 
@@ -285,38 +307,46 @@ ap_dvm_status flush(ap_dvm_handle* h) {
     return fail(h, AP_DVM_ERR_ARG, "the set of solves changed while the stream is being captured");
   const int TX = h->ks.tx, TY = h->ks.ty;
   const unsigned kinds = fft_kinds_of(h);
-  if (kinds != h->fft_kinds) { h->fft_kinds = kinds; h->graph_valid = false; }   // the launch sequence changed
-  h->up_inst.clear();
+  if (kinds != h->fft_kinds) { h->fft_kinds = kinds; h->graph_valid[0] = h->graph_valid[1] = false; }   // the launch sequence changed
+  h->up_inst[0].clear();
+  h->up_inst[1].clear();
   h->up_tiles.assign(1, 0);
   h->up_rows.assign(1, 0);
   h->up_cols.assign(1, 0);
   for (Slot& s : h->slots) {
     if (!s.attached) continue;
     if (s.p.nx < TX || s.p.ny < TY) return fail(h, AP_DVM_ERR_ARG, "grid %dx%d smaller than the tile %dx%d", s.p.nx, s.p.ny, TX, TY);
-    InstDev d = s.dev;
+    InstDev& d = s.dev;
     d.tiles_x = (s.p.nx + TX - 1) / TX;   // ragged tiles at the high edges
     d.tiles_y = (s.p.ny + TY - 1) / TY;
-    // tensor maps of the stage buffers for the current tile shape (TMA staging)
-    d.tma = encode_stage_maps(s.p, d, h->ks.bw, h->ks.bh, s.maps);
-    if (d.tma)
-      CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(d.tmap), &s.maps[0], sizeof(CUtensorMap) * (APD_MAXS + 1),
-                                  cudaMemcpyHostToDevice, h->stream));
     const int pairs = (s.p.ny + 1) / 2;   // row pairs (the last one single when ny is odd)
     d.row_pairs = std::max(1, std::min(h->eblk >> d.lnx, pairs));
-    d.col_group = std::max(1, h->eblk >> d.lny);
-    h->up_inst.push_back(d);
+    // power-of-two columns: a few adjacent columns per item (4 FP32 or 2 FP64: 32-byte row segments)
+    d.col_group = is_pow2(s.p.ny) ? std::min(h->f32 ? 4 : 2, std::max(1, h->eblk_cols >> d.lny))
+                                  : std::max(1, h->eblk >> d.lny);
+    for (int par = 0; par < 2; ++par) {   // the instance as steps of either parity see it
+      InstDev v = view(s, par);
+      // tensor maps of the stage buffers for the current tile shape (TMA staging)
+      v.tma = encode_stage_maps(s.p, v, h->ks.bw, h->ks.bh, s.maps[par]);
+      if (v.tma)
+        CUDA_TRY(h, cudaMemcpyAsync(const_cast<void*>(v.tmap), &s.maps[par][0], sizeof(CUtensorMap) * (APD_MAXS + 1),
+                                    cudaMemcpyHostToDevice, h->stream));
+      h->up_inst[par].push_back(v);
+    }
     h->up_tiles.push_back(h->up_tiles.back() + d.tiles_x * d.tiles_y);
     h->up_rows.push_back(h->up_rows.back() + (pairs + d.row_pairs - 1) / d.row_pairs);
     h->up_cols.push_back(h->up_cols.back() + (s.p.nx / 2 + 1 + d.col_group - 1) / d.col_group);
   }
-  const int n = (int)h->up_inst.size();
+  const int n = (int)h->up_inst[0].size();
   h->n_active = n;
   h->up_counts[0] = h->up_tiles.back();
   h->up_counts[1] = h->up_rows.back();
   h->up_counts[2] = h->up_cols.back();
   h->up_counts[3] = n;
   if (n > 0) {
-    CUDA_TRY(h, cudaMemcpyAsync(h->d_inst, h->up_inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice, h->stream));
+    for (int par = 0; par < 2; ++par)
+      CUDA_TRY(h, cudaMemcpyAsync(h->d_inst[par], h->up_inst[par].data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
+                                  h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_tile_start, h->up_tiles.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_row_start, h->up_rows.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_col_start, h->up_cols.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
@@ -367,30 +397,31 @@ ap_dvm_status profile_collect(ap_dvm_handle* h) {
   return AP_DVM_OK;
 }
 
-// Kernels of one IMEX step for all attached solves (see the file header).
-ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream) {
-  StepKernels K{h->ks, h->km, h->grid_explicit, h->grid_rhs, h->grid_update, h->grid_finish, h->grid_fft, fft_smem(h),
-                h->smem_update, h->fft_kinds};
+// Kernels of one IMEX step of the given parity for all attached solves (see the file header).
+ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream, int parity) {
+  StepKernels K{h->ks,       h->km,         h->grid_explicit, h->grid_rhs,   h->grid_update, h->grid_finish,
+                h->grid_fft, h->grid_cols, h->f32 ? 1024 : 256, fft_smem(h), cols_smem(h), h->smem_update, h->fft_kinds};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int kind) -> int {
     return (int)launch(h, stream, fn, grid, block, smem, args, kind);
   };
-  return (ap_dvm_status)enqueue_imex_step(h->tmpl, K, h->d_batch, h->f32, ln);
+  return (ap_dvm_status)enqueue_imex_step(h->tmpl, K, h->d_batch[parity], h->tmpl.precision, ln, true);
 }
 
-ap_dvm_status build_graph(ap_dvm_handle* h) {
-  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+// A CUDA graph of graph_steps steps starting at the given parity.
+ap_dvm_status build_graph(ap_dvm_handle* h, int parity) {
+  if (h->graph[parity]) { cudaGraphExecDestroy(h->graph[parity]); h->graph[parity] = nullptr; }
   if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   ap_dvm_status st = AP_DVM_OK;
-  for (int k = 0; k < h->graph_steps && st == AP_DVM_OK; ++k) st = enqueue_step(h, h->cap_stream);
+  for (int k = 0; k < h->graph_steps && st == AP_DVM_OK; ++k) st = enqueue_step(h, h->cap_stream, parity ^ (k & 1));
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (st) { if (g) cudaGraphDestroy(g); return st; }
   if (e != cudaSuccess) return fail(h, AP_DVM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&h->graph, g, 0);
+  e = cudaGraphInstantiate(&h->graph[parity], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(h, AP_DVM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-  h->graph_valid = true;
+  h->graph_valid[parity] = true;
   return AP_DVM_OK;
 }
 
@@ -436,7 +467,7 @@ void ap_dvm_default_params(ap_dvm_params* p, int nx, int ny, double eps, double 
 size_t ap_dvm_instance_workspace_size(const ap_dvm_params* p) {
   char buf[256];
   if (validate(p, buf, sizeof(buf)) != AP_DVM_OK) return 0;
-  return carve_instance(*p, nullptr, nullptr);
+  return carve_instance(*p, nullptr, nullptr, true);
 }
 
 size_t ap_dvm_batch_workspace_size(const ap_dvm_params* tmpl, int capacity) {
@@ -462,11 +493,12 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   if (capacity < 1) return fail(h, AP_DVM_ERR_ARG, "capacity must be >= 1");
   h->tmpl = *tmpl;
   h->capacity = capacity;
-  h->f32 = tmpl->precision == AP_DVM_FP32_DEV;
+  h->f32 = tmpl->precision != AP_DVM_FP64;
   h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->nmax = std::max(fft_length(tmpl->nx), fft_length(tmpl->ny));   // longest transform of the batch
   h->lnmax = ilog2(h->nmax);
-  h->eblk = std::max(2048, h->nmax);
+  h->eblk = fft_eblk(h->nmax);
+  h->eblk_cols = fft_eblk_cols(h->nmax, h->f32);
   const size_t need = batch_bytes(capacity, h->nmax);
   if (!d_workspace || bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
     return fail(h, AP_DVM_ERR_WORKSPACE, "batch workspace needs %zu bytes, 256-byte aligned (got %zu)", need, bytes);
@@ -475,8 +507,12 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   char* base = reinterpret_cast<char*>(d_workspace);
   size_t off = 0;
   auto take = [&](size_t b) { off = align_up(off, 256); char* r = base + off; off += b; return r; };
-  h->d_batch = reinterpret_cast<BatchDev*>(take(sizeof(BatchDev)));
-  h->d_inst = reinterpret_cast<InstDev*>(take(sizeof(InstDev) * capacity));
+  BatchDev* batches = reinterpret_cast<BatchDev*>(take(sizeof(BatchDev) * 2));
+  InstDev* insts = reinterpret_cast<InstDev*>(take(sizeof(InstDev) * capacity * 2));
+  for (int par = 0; par < 2; ++par) {
+    h->d_batch[par] = batches + par;
+    h->d_inst[par] = insts + (size_t)par * capacity;
+  }
   h->d_tile_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
   h->d_row_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
   h->d_col_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
@@ -495,8 +531,8 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
     tw32[k].x = (float)std::cos(a);
     tw32[k].y = (float)std::sin(a);
   }
-  BatchDev& hb = h->hb;
-  hb.inst = h->d_inst;
+  BatchDev& hb = h->hb[0];
+  hb.inst = h->d_inst[0];
   hb.tile_start = h->d_tile_start;
   hb.row_start = h->d_row_start;
   hb.col_start = h->d_col_start;
@@ -510,7 +546,9 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   // synchronous uploads: the host vectors go out of scope
   CUDA_TRY(h, cudaMemcpy(h->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(h, cudaMemcpy(h->d_tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice));
-  CUDA_TRY(h, cudaMemcpy(h->d_batch, &hb, sizeof(BatchDev), cudaMemcpyHostToDevice));
+  h->hb[1] = hb;
+  h->hb[1].inst = h->d_inst[1];
+  for (int par = 0; par < 2; ++par) CUDA_TRY(h, cudaMemcpy(h->d_batch[par], &h->hb[par], sizeof(BatchDev), cudaMemcpyHostToDevice));
   CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned) * 4));
   int zeros[4] = {0, 0, 0, 0};
   CUDA_TRY(h, cudaMemcpy(h->d_counts, zeros, sizeof(zeros), cudaMemcpyHostToDevice));
@@ -530,7 +568,7 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   if (std::max(fft_length(p->nx), fft_length(p->ny)) > h->nmax)
     return fail(h, AP_DVM_ERR_ARG, "grid %dx%d needs transforms of length %d, longer than the batch's %d", p->nx, p->ny,
                 std::max(fft_length(p->nx), fft_length(p->ny)), h->nmax);
-  const size_t need = carve_instance(*p, nullptr, nullptr);
+  const size_t need = carve_instance(*p, nullptr, nullptr, true);
   if (!d_workspace || bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
     return fail(h, AP_DVM_ERR_WORKSPACE, "instance workspace needs %zu bytes, 256-byte aligned (got %zu)", need, bytes);
   Slot& s = h->slots[slot];
@@ -539,15 +577,20 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   s.ws = reinterpret_cast<char*>(d_workspace);
   s.bytes = bytes;
   InstDev& d = s.dev;
-  carve_instance(*p, s.ws, &d);
+  carve_instance(*p, s.ws, &d, true);
   d.nx = p->nx; d.ny = p->ny; d.lnx = ilog2(fft_length(p->nx)); d.lny = ilog2(fft_length(p->ny));
   fill_constants(*p, d);
-  d.relax64 = (p->precision == AP_DVM_FP32_DEV && p->eps <= 1e-4) ? 1 : 0;
+  d.relax64 = (p->precision != AP_DVM_FP64 && p->eps <= 1e-4) ? 1 : 0;
   std::vector<double> lx(p->nx / 2 + 1), ly(p->ny);
   laplacian_symbol(p->nx, d.dx, p->space_scheme, lx.data(), (int)lx.size());
   laplacian_symbol(p->ny, d.dy, p->space_scheme, ly.data(), (int)ly.size());
   CUDA_TRY(h, cudaMemcpyAsync(d.lamx, lx.data(), sizeof(double) * lx.size(), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(d.lamy, ly.data(), sizeof(double) * ly.size(), cudaMemcpyHostToDevice, h->stream));
+  std::vector<float> lx32(lx.begin(), lx.end()), ly32(ly.begin(), ly.end());   // rounded once (FP32 form)
+  if (d.lamx32) {
+    CUDA_TRY(h, cudaMemcpyAsync(d.lamx32, lx32.data(), sizeof(float) * lx32.size(), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(d.lamy32, ly32.data(), sizeof(float) * ly32.size(), cudaMemcpyHostToDevice, h->stream));
+  }
   std::vector<double2> tab64[2];
   std::vector<float2> tab32[2];
   for (int a = 0; a < 2; ++a) {
@@ -585,7 +628,7 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
     }
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));   // the symbol and transform-table vectors are about to go out of scope
-  CUDA_TRY(h, cudaMemsetAsync(d.X, 0, (size_t)6 * p->nx * p->ny * (h->f32 ? 4 : 8), h->stream));
+  for (void* xb : {d.X, d.Xnext}) CUDA_TRY(h, cudaMemsetAsync(xb, 0, (size_t)6 * p->nx * p->ny * (h->f32 ? 4 : 8), h->stream));
   if (d.dF) CUDA_TRY(h, cudaMemsetAsync(d.dF, 0, (size_t)6 * p->nx * p->ny * sizeof(float), h->stream));
   s.attached = true;
   h->dirty = true;
@@ -618,9 +661,9 @@ static ap_dvm_status set_state_impl(ap_dvm_handle* h, int slot, const double* a,
   if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
   ap_dvm_status st = prepare_kernels(h);
   if (st) return st;
-  InstDev d = s->dev;
-  int f32 = h->f32;
-  void* args[] = {&d, &a, &b, &c, &f, &mode, &f32};
+  InstDev d = view(*s, h->parity);
+  int form = h->tmpl.precision;   // 0: FP64, 1: FP32 deviation form, 2: the same with theta carried
+  void* args[] = {&d, &a, &b, &c, &f, &mode, &form};
   return launch(h, h->stream, h->km.k_set_state, grid_for_cells((size_t)s->p.nx * s->p.ny), dim3(256), 0, args);
 }
 
@@ -630,9 +673,9 @@ static ap_dvm_status get_state_impl(ap_dvm_handle* h, int slot, double* out, flo
   if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
   ap_dvm_status st = prepare_kernels(h);
   if (st) return st;
-  InstDev d = s->dev;
-  int f32 = h->f32;
-  void* args[] = {&d, &out, &o1, &o2, &o3, &out32, &what, &f32};
+  InstDev d = view(*s, h->parity);
+  int form = h->tmpl.precision;
+  void* args[] = {&d, &out, &o1, &o2, &o3, &out32, &what, &form};
   return launch(h, h->stream, h->km.k_get_state, grid_for_cells((size_t)s->p.nx * s->p.ny), dim3(256), 0, args);
 }
 
@@ -642,7 +685,7 @@ ap_dvm_status ap_dvm_diagnostics(ap_dvm_handle* h, int slot, double* d_vorticity
   if (!s) return h ? fail(h, AP_DVM_ERR_ARG, "slot %d is not attached", slot) : AP_DVM_ERR_ARG;
   ap_dvm_status st = prepare_kernels(h);
   if (st) return st;
-  InstDev d = s->dev;
+  InstDev d = view(*s, h->parity);
   const size_t cells = (size_t)s->p.nx * s->p.ny;
   const int grid = (int)std::min<size_t>((cells + 255) / 256, 256);
   // block partials in the slot's right-hand-side plane (free between steps; >= 3 * grid doubles)
@@ -683,6 +726,12 @@ ap_dvm_status ap_dvm_set_populations(ap_dvm_handle* h, int slot, const void* d_d
   return set_state_impl(h, slot, reinterpret_cast<const double*>(d_dF6), nullptr, nullptr, nullptr, 2);
 }
 
+ap_dvm_status ap_dvm_set_theta(ap_dvm_handle* h, int slot, const double* d_theta) {
+  if (!d_theta) return h ? fail(h, AP_DVM_ERR_ARG, "null pointer") : AP_DVM_ERR_ARG;
+  if (h && h->tmpl.precision != AP_DVM_FP32_DEV_TH) return fail(h, AP_DVM_ERR_ARG, "the carried theta plane needs AP_DVM_FP32_DEV_TH");
+  return set_state_impl(h, slot, d_theta, nullptr, nullptr, nullptr, 4);
+}
+
 ap_dvm_status ap_dvm_get_state(ap_dvm_handle* h, int slot, double* d_moments6) {
   if (!d_moments6) return h ? fail(h, AP_DVM_ERR_ARG, "null pointer") : AP_DVM_ERR_ARG;
   return get_state_impl(h, slot, d_moments6, nullptr, 0);
@@ -709,14 +758,17 @@ ap_dvm_status ap_dvm_step(ap_dvm_handle* h, int nsteps) {
   if (h->n_active == 0 || nsteps == 0) return AP_DVM_OK;
   int done = 0;
   if (h->graph_steps > 0 && !h->profile) {
-    if (!h->graph_valid && (st = build_graph(h))) return st;
     while (nsteps - done >= h->graph_steps) {
-      CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+      const int par = h->parity;
+      if (!h->graph_valid[par] && (st = build_graph(h, par))) return st;
+      CUDA_TRY(h, cudaGraphLaunch(h->graph[par], h->stream));
       done += h->graph_steps;
+      h->parity ^= h->graph_steps & 1;
     }
   }
   for (; done < nsteps; ++done) {
-    if ((st = enqueue_step(h, h->stream))) return st;
+    if ((st = enqueue_step(h, h->stream, h->parity))) return st;
+    h->parity ^= 1;
     if (h->profile && h->ev_used > 2048 && (st = profile_collect(h))) return st;
   }
   return AP_DVM_OK;
@@ -745,7 +797,7 @@ int ap_dvm_profile_read(ap_dvm_handle* h, const char** names, double* total_ms, 
 ap_dvm_status ap_dvm_set_graph_steps(ap_dvm_handle* h, int k) {
   if (!h) return AP_DVM_ERR_ARG;
   if (k < 0) return fail(h, AP_DVM_ERR_ARG, "k must be >= 0");
-  if (k != h->graph_steps) { h->graph_steps = k; h->graph_valid = false; }
+  if (k != h->graph_steps) { h->graph_steps = k; h->graph_valid[0] = h->graph_valid[1] = false; }
   return AP_DVM_OK;
 }
 
@@ -767,7 +819,8 @@ int ap_dvm_launches_per_step(const ap_dvm_handle* h) {
   if (!h) return 0;
   const ap_dvm_params& t = h->tmpl;
   const int f = fft_launches(fft_kinds_of(h));   // transform launches per implicit stage
-  return t.A_im[0] != 0.0 ? 1 + (2 + f) + (3 + f) * (t.s - 1) + 1 : (3 + f) * (t.s - 1) + 1;
+  // the last stage's update closes the step (no finish kernel)
+  return t.A_im[0] != 0.0 ? 1 + (2 + f) + (3 + f) * (t.s - 1) : (3 + f) * (t.s - 1);
 }
 
 ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, double* h_out, double* d_stage, int nsteps) {
@@ -809,7 +862,8 @@ const char* ap_dvm_last_error(const ap_dvm_handle* h) { return h ? h->err : "nul
 void ap_dvm_destroy(ap_dvm_handle* h) {
   if (!h) return;
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (cudaGraphExec_t g : h->graph)
+    if (g) cudaGraphExecDestroy(g);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }

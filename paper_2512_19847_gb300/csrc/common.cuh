@@ -73,6 +73,8 @@ struct InstDev {
   Coef<double> k64;             // the stage coefficients in FP64 ...
   Coef<float> k32;              // ... and rounded once to FP32
   void* X;                      // 6 planes: state at t^n (moments)
+  void* Xnext;                  // 6 planes the last stage's update writes the state at t^{n+1} to (the
+                                // other buffer of a double-buffered state; null: a separate finish kernel)
   void* Xs[APD_MAXS + 1];       // stage values X^(j), j = 1..s (6 planes); Xs[1] = X for CK/ARS tableaux
                                 // (stage 1 = X^n), its own buffer for type-A tableaux; Xs[s] = next state
   void* E[APD_MAXS + 1];        // explicit term of step 1 for stage j (2 planes)
@@ -87,6 +89,9 @@ struct InstDev {
   void* S;                      // half spectrum, complex T, ny rows x sstride
   double* lamx;                 // 1D Laplacian symbol in x, kx = 0..nx/2
   double* lamy;                 // 1D Laplacian symbol in y, ky = 0..ny-1
+  float* lamx32;                // FP32 form: the same tables rounded once (null in the FP64 form)
+  float* lamy32;
+  float hscale32;               // FP32 form: 1/(nx ny) rounded once
   double* th_part;              // per-tile partial sums of theta^n (ceil(nx/8) * ceil(ny/4) entries)
   float* dF;                    // FP32 form: deviation populations (6 planes)
   unsigned mr_plan[2];          // axes whose n is not a power of two but factors into 2, 3, 5, 7 (x, y):

@@ -77,15 +77,27 @@ __device__ __forceinline__ C mul_w8(C a, bool inv) {
 template <typename C>
 __device__ __forceinline__ C mul_w83(C a, bool inv) { return mul_j(mul_w8(a, inv), inv); }
 
-// ntr transforms of length n = 2^ln held back to back in x[], input in
-// bit-reversed order, output natural.  Twiddle W_m^p = tw[p * nmax/m].
-// Stages are taken three at a time (radix-2^3): each thread loads eight
-// elements p0 + k h (k = 0..7, h = 2^(s-1)), applies stage s (half h, twiddle
-// W_{2h}^pos), stage s+1 (half 2h, W_{4h}^pos and W_{4h}^pos W_4) and stage s+2
-// (half 4h, W_{8h}^pos W_8^k) in registers, and stores them: one table twiddle
-// per stage, the rest constant roots.  One or two stages left over take a
-// radix-2^2 or radix-2 step; the first step has only constant twiddles.
+// Shared-memory index with padding: one spare element after every 2^PS
+// elements (PS = 31: none), so that the strided accesses of the butterfly
+// passes spread over the 32 banks: with 8-byte (FP32) complex values PS = 4,
+// with 16-byte (FP64) values PS = 3, every radix-2^3 pass below reads and
+// writes with the minimum number of shared-memory wavefronts.
+template <int PS>
+__device__ __forceinline__ int pidx(int i) { return PS >= 31 ? i : i + (i >> PS); }
 template <typename T>
+__host__ __device__ constexpr int pad_shift() { return sizeof(T) == 4 ? 4 : 3; }
+// Complex elements a padded region of n values occupies.
+__host__ __device__ constexpr int padded_len(int n, int ps) { return ps >= 31 ? n : n + (n >> ps) + 1; }
+
+// ntr transforms of length n = 2^ln held back to back in x[] (element i at
+// x[pidx<PS>(i)]), input in bit-reversed order, output natural.  Twiddle
+// W_m^p = tw[p * nmax/m].  Stages are taken three at a time (radix-2^3): each
+// thread loads eight elements p0 + k h (k = 0..7, h = 2^(s-1)), applies stage s
+// (half h, twiddle W_{2h}^pos), stage s+1 (half 2h, W_{4h}^pos and W_{4h}^pos W_4)
+// and stage s+2 (half 4h, W_{8h}^pos W_8^k) in registers, and stores them: one
+// table twiddle per stage, the rest constant roots.  One or two stages left over
+// take a radix-2^2 or radix-2 step; the first step has only constant twiddles.
+template <typename T, int PS = 31>
 __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int ntr,
                                         const typename Cplx<T>::type* __restrict__ tw, int lnmax,
                                         bool inv, int tid, int nthr) {
@@ -97,8 +109,9 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
     for (int k = tid; k < nb; k += nthr) {
       const int t = k >> (ln - 3), bi = k & (ne - 1);
       const int pos = bi & (h - 1), grp = bi >> (s - 1);
-      C* q = x + t * n + grp * 8 * h + pos;
-      C v0 = q[0], v1 = q[h], v2 = q[2 * h], v3 = q[3 * h], v4 = q[4 * h], v5 = q[5 * h], v6 = q[6 * h], v7 = q[7 * h];
+      const int q = t * n + grp * 8 * h + pos;
+      C v0 = x[pidx<PS>(q)], v1 = x[pidx<PS>(q + h)], v2 = x[pidx<PS>(q + 2 * h)], v3 = x[pidx<PS>(q + 3 * h)];
+      C v4 = x[pidx<PS>(q + 4 * h)], v5 = x[pidx<PS>(q + 5 * h)], v6 = x[pidx<PS>(q + 6 * h)], v7 = x[pidx<PS>(q + 7 * h)];
       if (s > 1) {   // stage s: W_{2h}^pos on the odd elements
         const C w1 = tw[pos << (lnmax - s)];
         v1 = cmul_tw(w1, v1, inv); v3 = cmul_tw(w1, v3, inv); v5 = cmul_tw(w1, v5, inv); v7 = cmul_tw(w1, v7, inv);
@@ -120,10 +133,10 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
       b5 = mul_w8(b5, inv);
       b6 = mul_j(b6, inv);
       b7 = mul_w83(b7, inv);
-      q[0] = cadd(b0, b4); q[4 * h] = csub(b0, b4);
-      q[h] = cadd(b1, b5); q[5 * h] = csub(b1, b5);
-      q[2 * h] = cadd(b2, b6); q[6 * h] = csub(b2, b6);
-      q[3 * h] = cadd(b3, b7); q[7 * h] = csub(b3, b7);
+      x[pidx<PS>(q)] = cadd(b0, b4); x[pidx<PS>(q + 4 * h)] = csub(b0, b4);
+      x[pidx<PS>(q + h)] = cadd(b1, b5); x[pidx<PS>(q + 5 * h)] = csub(b1, b5);
+      x[pidx<PS>(q + 2 * h)] = cadd(b2, b6); x[pidx<PS>(q + 6 * h)] = csub(b2, b6);
+      x[pidx<PS>(q + 3 * h)] = cadd(b3, b7); x[pidx<PS>(q + 7 * h)] = csub(b3, b7);
     }
     __syncthreads();
   }
@@ -133,7 +146,7 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
       const int t = k >> (ln - 2), bi = k & (nq - 1);
       const int pos = bi & (h - 1), grp = bi >> (s - 1);
       const int p0 = t * n + grp * 4 * h + pos;
-      C x0 = x[p0], x1 = x[p0 + h], x2 = x[p0 + 2 * h], x3 = x[p0 + 3 * h];
+      C x0 = x[pidx<PS>(p0)], x1 = x[pidx<PS>(p0 + h)], x2 = x[pidx<PS>(p0 + 2 * h)], x3 = x[pidx<PS>(p0 + 3 * h)];
       if (s > 1) {
         const C w1 = tw[pos << (lnmax - s)];
         x1 = cmul_tw(w1, x1, inv);
@@ -147,10 +160,10 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
         a3 = cmul_tw(w2, a3, inv);
       }
       a3 = mul_j(a3, inv);
-      x[p0] = cadd(a0, a2);
-      x[p0 + 2 * h] = csub(a0, a2);
-      x[p0 + h] = cadd(a1, a3);
-      x[p0 + 3 * h] = csub(a1, a3);
+      x[pidx<PS>(p0)] = cadd(a0, a2);
+      x[pidx<PS>(p0 + 2 * h)] = csub(a0, a2);
+      x[pidx<PS>(p0 + h)] = cadd(a1, a3);
+      x[pidx<PS>(p0 + 3 * h)] = csub(a1, a3);
     }
     __syncthreads();
   } else if (s == ln) {   // one stage left: radix-2
@@ -159,9 +172,9 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
       const int t = k >> (ln - 1), bi = k & ((n >> 1) - 1);
       const int pos = bi & (half - 1), grp = bi >> (s - 1);
       const int i0 = t * n + grp * 2 * half + pos, i1 = i0 + half;
-      const C a = x[i0], tb = cmul_tw(tw[pos << sh], x[i1], inv);
-      x[i0] = cadd(a, tb);
-      x[i1] = csub(a, tb);
+      const C a = x[pidx<PS>(i0)], tb = cmul_tw(tw[pos << sh], x[pidx<PS>(i1)], inv);
+      x[pidx<PS>(i0)] = cadd(a, tb);
+      x[pidx<PS>(i1)] = csub(a, tb);
     }
     __syncthreads();
   }
@@ -171,7 +184,7 @@ __device__ __forceinline__ void fft_dit(typename Cplx<T>::type* x, int ln, int n
 // stages at a time as in fft_dit, mirrored: stage s (half 4h, W_{8h}^pos W_8^k
 // on the differences), stage s-1 (half 2h, W_{4h}^pos and W_{4h}^pos W_4),
 // stage s-2 (half h, W_{2h}^pos), h = 2^(s-3); leftovers as radix-2^2 or radix-2.
-template <typename T>
+template <typename T, int PS = 31>
 __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int ntr,
                                         const typename Cplx<T>::type* __restrict__ tw, int lnmax,
                                         bool inv, int tid, int nthr) {
@@ -183,8 +196,9 @@ __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int n
     for (int k = tid; k < nb; k += nthr) {
       const int t = k >> (ln - 3), bi = k & (ne - 1);
       const int pos = bi & (h - 1), grp = bi >> (s - 3);
-      C* q = x + t * n + grp * 8 * h + pos;
-      const C v0 = q[0], v1 = q[h], v2 = q[2 * h], v3 = q[3 * h], v4 = q[4 * h], v5 = q[5 * h], v6 = q[6 * h], v7 = q[7 * h];
+      const int q = t * n + grp * 8 * h + pos;
+      const C v0 = x[pidx<PS>(q)], v1 = x[pidx<PS>(q + h)], v2 = x[pidx<PS>(q + 2 * h)], v3 = x[pidx<PS>(q + 3 * h)];
+      const C v4 = x[pidx<PS>(q + 4 * h)], v5 = x[pidx<PS>(q + 5 * h)], v6 = x[pidx<PS>(q + 6 * h)], v7 = x[pidx<PS>(q + 7 * h)];
       // stage s: pairs (k, k+4), differences times W_{8h}^pos W_8^k
       C a0 = cadd(v0, v4), a1 = cadd(v1, v5), a2 = cadd(v2, v6), a3 = cadd(v3, v7);
       C a4 = csub(v0, v4), a5 = csub(v1, v5), a6 = csub(v2, v6), a7 = csub(v3, v7);
@@ -210,10 +224,10 @@ __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int n
         const C w1 = tw[pos << (lnmax - s + 2)];
         c1 = cmul_tw(w1, c1, inv); c3 = cmul_tw(w1, c3, inv); c5 = cmul_tw(w1, c5, inv); c7 = cmul_tw(w1, c7, inv);
       }
-      q[0] = cadd(b0, b1); q[h] = c1;
-      q[2 * h] = cadd(b2, b3); q[3 * h] = c3;
-      q[4 * h] = cadd(b4, b5); q[5 * h] = c5;
-      q[6 * h] = cadd(b6, b7); q[7 * h] = c7;
+      x[pidx<PS>(q)] = cadd(b0, b1); x[pidx<PS>(q + h)] = c1;
+      x[pidx<PS>(q + 2 * h)] = cadd(b2, b3); x[pidx<PS>(q + 3 * h)] = c3;
+      x[pidx<PS>(q + 4 * h)] = cadd(b4, b5); x[pidx<PS>(q + 5 * h)] = c5;
+      x[pidx<PS>(q + 6 * h)] = cadd(b6, b7); x[pidx<PS>(q + 7 * h)] = c7;
     }
     __syncthreads();
   }
@@ -221,22 +235,22 @@ __device__ __forceinline__ void fft_dif(typename Cplx<T>::type* x, int ln, int n
     const int nq = n >> 2, nb = ntr * nq;
     for (int k = tid; k < nb; k += nthr) {
       const int p0 = 4 * k;
-      const C x0 = x[p0], x1 = x[p0 + 1], x2 = x[p0 + 2], x3 = x[p0 + 3];
+      const C x0 = x[pidx<PS>(p0)], x1 = x[pidx<PS>(p0 + 1)], x2 = x[pidx<PS>(p0 + 2)], x3 = x[pidx<PS>(p0 + 3)];
       const C b0 = cadd(x0, x2), b1 = cadd(x1, x3), b2 = csub(x0, x2);
       const C b3 = mul_j(csub(x1, x3), inv);
-      x[p0] = cadd(b0, b1);
-      x[p0 + 1] = csub(b0, b1);
-      x[p0 + 2] = cadd(b2, b3);
-      x[p0 + 3] = csub(b2, b3);
+      x[pidx<PS>(p0)] = cadd(b0, b1);
+      x[pidx<PS>(p0 + 1)] = csub(b0, b1);
+      x[pidx<PS>(p0 + 2)] = cadd(b2, b3);
+      x[pidx<PS>(p0 + 3)] = csub(b2, b3);
     }
     __syncthreads();
   } else if (s == 1) {   // last radix-2 stage: all twiddles are 1
     const int nb = ntr * (n >> 1);
     for (int k = tid; k < nb; k += nthr) {
       const int i0 = 2 * k, i1 = i0 + 1;
-      const C a = x[i0], b = x[i1];
-      x[i0] = cadd(a, b);
-      x[i1] = csub(a, b);
+      const C a = x[pidx<PS>(i0)], b = x[pidx<PS>(i1)];
+      x[pidx<PS>(i0)] = cadd(a, b);
+      x[pidx<PS>(i1)] = csub(a, b);
     }
     __syncthreads();
   }
@@ -260,7 +274,8 @@ __device__ __forceinline__ void bluestein_conv(typename Cplx<T>::type* x, int lm
 }
 
 // mean(theta^n) of instance I from its per-tile partial sums, in a fixed order,
-// into *mean (shared); every thread of the block calls it.
+// into *mean (shared); every thread of the block calls it; red holds one value
+// per warp of the block.
 __device__ __forceinline__ void theta_mean(const InstDev& I, double* red, double* mean, int tid, int nthr) {
   const int nt = I.tiles_x * I.tiles_y;
   double acc = 0.0;
@@ -276,11 +291,12 @@ __device__ __forceinline__ void theta_mean(const InstDev& I, double* red, double
   __syncthreads();
 }
 
-// ---- power-of-two axes
+// ---- power-of-two axes (shared memory padded, pidx<pad_shift<T>()>)
 
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
   using C = typename Cplx<T>::type;
+  constexpr int PS = pad_shift<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
   const BatchDev& b = *bp;
@@ -293,19 +309,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd(co
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
     const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
     const T* R = reinterpret_cast<const T*>(I.R);
+#pragma unroll 4
     for (int e = tid; e < ntr * n; e += nthr) {
       const int p = e >> ln, k = e & (n - 1);
       const size_t row = (size_t)(2 * (pair0 + p));
       C z; z.x = R[row * n + k]; z.y = row + 1 < (size_t)ny ? R[(row + 1) * n + k] : T(0);
-      x[p * n + brev(k, ln)] = z;
+      x[pidx<PS>(p * n + brev(k, ln))] = z;
     }
     __syncthreads();
-    fft_dit<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, false, tid, nthr);
+    fft_dit<T, PS>(x, ln, ntr, twiddles<T>(b), b.lnmax, false, tid, nthr);
     C* S = reinterpret_cast<C*>(I.S);
     const int nh = (n >> 1) + 1;
     for (int e = tid; e < ntr * nh; e += nthr) {
       const int p = e / nh, k = e - p * nh;
-      const C zk = x[p * n + k], zm = x[p * n + ((n - k) & (n - 1))];
+      const C zk = x[pidx<PS>(p * n + k)], zm = x[pidx<PS>(p * n + ((n - k) & (n - 1)))];
       const size_t row = (size_t)(2 * (pair0 + p));
       C A, B;
       A.x = T(0.5) * (zk.x + zm.x); A.y = T(0.5) * (zk.y - zm.y);
@@ -317,12 +334,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd(co
   }
 }
 
+// Column pass: a work item is a group of col_group (a power of two) adjacent
+// spectral columns, loaded and stored row by row (adjacent threads take
+// adjacent columns of one row); the forward transform runs by decimation in
+// frequency (natural order in, bit-reversed out) and the inverse by decimation
+// in time (bit-reversed in, natural out), so the symbol division takes the
+// spectrum in bit-reversed order and no permutation pass is needed.  The FP32
+// form runs it with 1024 threads (cols_threads<T>: one radix-2^3 butterfly per
+// thread and pass for four columns of 2048), the FP64 form with 256 (its
+// butterflies keep the FP64 pipe busy either way); the load and store loops are
+// unrolled so that several global accesses per thread are in flight.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
+__host__ __device__ constexpr int cols_threads() { return sizeof(T) == 4 ? 1024 : 256; }
+
+template <typename T>
+__global__ void __launch_bounds__(cols_threads<T>(), sizeof(T) == 4 ? 1 : 2) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
+  constexpr int PS = pad_shift<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
-  __shared__ double red[8];
+  __shared__ double red[32];
   __shared__ double s_mean;
   const BatchDev& b = *bp;
   const int nitems = b.counts[2], tid = threadIdx.x, nthr = blockDim.x;
@@ -331,37 +362,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols(const 
     const InstDev& I = b.inst[k_inst];
     if (I.chirp[1] || I.mr_npass[1]) continue;      // an item of another length
     const int n = I.ny, ln = I.lny, ss = I.sstride, nh = (I.nx >> 1) + 1;
-    const int col0 = (it - b.col_start[k_inst]) * I.col_group;
-    const int ntr = min(I.col_group, nh - col0);
+    const int G = I.col_group, lg = __ffs(G) - 1;
+    const int col0 = (it - b.col_start[k_inst]) * G;
+    const int ntr = min(G, nh - col0);
     if (col0 == 0) theta_mean(I, red, &s_mean, tid, nthr);
     C* S = reinterpret_cast<C*>(I.S);
-    for (int e = tid; e < ntr * n; e += nthr) {
-      const int g = e >> ln, y = e & (n - 1);
-      x[g * n + brev(y, ln)] = S[(size_t)y * ss + col0 + g];
+#pragma unroll 4
+    for (int e = tid; e < (n << lg); e += nthr) {
+      const int y = e >> lg, g = e & (G - 1);
+      if (g < ntr) x[pidx<PS>(g * n + y)] = S[(size_t)y * ss + col0 + g];
     }
     __syncthreads();
-    fft_dit<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, false, tid, nthr);
+    fft_dif<T, PS>(x, ln, ntr, twiddles<T>(b), b.lnmax, false, tid, nthr);
     const double kap = I.kappa[i];
     const double scale = 1.0 / ((double)I.nx * (double)I.ny);
     for (int e = tid; e < ntr * n; e += nthr) {
-      const int g = e >> ln, ky = e & (n - 1), kx = col0 + g;
-      C v = x[e];
+      const int g = e >> ln, ky = brev(e & (n - 1), ln), kx = col0 + g;
+      C v = x[pidx<PS>(e)];
       if (kx == 0 && ky == 0) {
         v.x = T(s_mean); v.y = T(0);
       } else if (sizeof(T) == 8) {
         const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
         v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
       } else {
-        const T f = T(scale) / T(I.lamx[kx] + I.lamy[ky] - kap);
-        v.x *= f; v.y *= f;
+        // FP32 form: the symbol in FP32 from the tables rounded once on the host
+        const float f = I.hscale32 * __frcp_rn(I.lamx32[kx] + I.lamy32[ky] - I.k32.kappa[i]);
+        v.x *= T(f); v.y *= T(f);
       }
-      x[e] = v;
+      x[pidx<PS>(e)] = v;
     }
     __syncthreads();
-    fft_dif<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, true, tid, nthr);
-    for (int e = tid; e < ntr * n; e += nthr) {
-      const int g = e >> ln, y = e & (n - 1);
-      S[(size_t)y * ss + col0 + g] = x[g * n + brev(y, ln)];
+    fft_dit<T, PS>(x, ln, ntr, twiddles<T>(b), b.lnmax, true, tid, nthr);
+#pragma unroll 4
+    for (int e = tid; e < (n << lg); e += nthr) {
+      const int y = e >> lg, g = e & (G - 1);
+      if (g < ntr) S[(size_t)y * ss + col0 + g] = x[pidx<PS>(g * n + y)];
     }
     __syncthreads();
   }
@@ -370,6 +405,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols(const 
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
+  constexpr int PS = pad_shift<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
   const BatchDev& b = *bp;
@@ -382,6 +418,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv(co
     const int pair0 = (it - b.row_start[k_inst]) * I.row_pairs;
     const int ntr = min(I.row_pairs, ((ny + 1) >> 1) - pair0);
     const C* S = reinterpret_cast<const C*>(I.S);
+#pragma unroll 4
     for (int e = tid; e < ntr * n; e += nthr) {
       const int p = e >> ln, k = e & (n - 1);
       const size_t row = (size_t)(2 * (pair0 + p));
@@ -397,15 +434,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv(co
         A.y = -A.y; B.y = -B.y;
       }
       C z; z.x = A.x - B.y; z.y = A.y + B.x;
-      x[e] = z;
+      x[pidx<PS>(e)] = z;
     }
     __syncthreads();
-    fft_dif<T>(x, ln, ntr, twiddles<T>(b), b.lnmax, true, tid, nthr);
+    fft_dif<T, PS>(x, ln, ntr, twiddles<T>(b), b.lnmax, true, tid, nthr);
     T* th = reinterpret_cast<T*>(I.Xs[i]) + 2 * (size_t)I.nx * I.ny;
     for (int e = tid; e < ntr * n; e += nthr) {
       const int p = e >> ln, m = e & (n - 1);
       const size_t row = (size_t)(2 * (pair0 + p));
-      const C z = x[p * n + brev(m, ln)];
+      const C z = x[pidx<PS>(p * n + brev(m, ln))];
       th[row * n + m] = z.x;
       if (row + 1 < (size_t)ny) th[(row + 1) * n + m] = z.y;
     }

@@ -52,28 +52,61 @@ __device__ __forceinline__ void mom_to_pop(const R* m, R eps, R rho0, R amp, R* 
 
 // FP32 form: store the deviation populations dF (the persistent state) and
 // the moments the next step starts from, summed from those FP32 values in
-// FP64 with the division by rho0 A (rounded once into the FP32 planes X).
-__device__ __forceinline__ void store_f32_state(const InstDev& I, size_t o, size_t pl, const float* d) {
+// FP64 with the division by rho0 A (rounded once into the FP32 planes X, or
+// into dst when given).
+__device__ __forceinline__ void store_f32_state(const InstDev& I, size_t o, size_t pl, const float* d,
+                                                float* dst = nullptr) {
   double dd[6], m[6];
   for (int k = 0; k < 6; ++k) {
     I.dF[o + k * pl] = d[k];
     dd[k] = widen_f32(d[k]);
   }
   pop_to_mom(dd, I, m);
-  float* X = reinterpret_cast<float*>(I.X);
+  float* X = dst ? dst : reinterpret_cast<float*>(I.X);
   for (int k = 0; k < 6; ++k) X[o + k * pl] = narrow_f64_rn(m[k]);
+}
+
+// The close of a step at one cell (GSA: X^{n+1} = X^(s)), given the last stage's
+// six moments m: FP64 form, copy them to X^{n+1} with a finiteness check; FP32
+// forms, pack them into the FP32 deviation populations and store the moments of
+// those populations (store_f32_state), with the carried theta for f32form = 2.
+// Returns true for a non-finite value.
+template <typename T>
+__device__ __forceinline__ bool close_step_cell(const InstDev& I, size_t o, size_t pl, const T* m, int f32form,
+                                                T* dst) {
+  bool bad = false;
+  if constexpr (sizeof(T) == 4) {
+    float d[6];
+    mom_to_pop<float>(m, I.eps32, I.rho032, I.amp32, d);
+    for (int k = 0; k < 6; ++k) bad |= !isfinite(d[k]);
+    store_f32_state(I, o, pl, d, dst);
+    if (f32form == 2) dst[o + 2 * pl] = m[2];
+  } else {
+    for (int k = 0; k < 6; ++k) {
+      bad |= !isfinite(m[k]);
+      dst[o + k * pl] = m[k];
+    }
+  }
+  return bad;
 }
 
 // ---- per-instance conversions (one instance, grid-stride over cells)
 
 // mode 0: moments (double) -> state;  mode 1: equilibrium from (u1, u2, p);
-// mode 2: populations dF (double) -> state;  mode 3: populations (float) -> state (FP32 form copy)
+// mode 2: populations dF (double) -> state;  mode 3: populations (float) -> state (FP32 form copy);
+// mode 4: the carried theta plane only (double, rounded to FP32; f32form = 2).
+// f32form: 0 FP64 form, 1 FP32 deviation form, 2 the same with theta carried in its own
+// FP32 plane (given moments set it directly; given populations, it is summed from them)
 template <typename T>
 __global__ void k_set_state(InstDev I, const double* __restrict__ a, const double* __restrict__ b2,
                             const double* __restrict__ c3, const float* __restrict__ f32, int mode, int f32form) {
   const size_t pl = (size_t)I.nx * I.ny;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < pl; o += (size_t)gridDim.x * blockDim.x) {
     double m[6];
+    if (mode == 4) {
+      reinterpret_cast<float*>(I.X)[o + 2 * pl] = float(a[o]);
+      continue;
+    }
     if (mode == 0) {
       for (int k = 0; k < 6; ++k) m[k] = a[o + k * pl];
     } else if (mode == 1) {
@@ -105,6 +138,7 @@ __global__ void k_set_state(InstDev I, const double* __restrict__ a, const doubl
       mom_to_pop<double>(m, I.eps, I.rho0, I.amp, d);
       for (int k = 0; k < 6; ++k) df[k] = float(d[k]);
       store_f32_state(I, o, pl, df);
+      if (f32form == 2) reinterpret_cast<float*>(I.X)[o + 2 * pl] = float(m[2]);
     } else {
       T* X = reinterpret_cast<T*>(I.X);
       for (int k = 0; k < 6; ++k) X[o + k * pl] = T(m[k]);
@@ -125,6 +159,7 @@ __global__ void k_get_state(InstDev I, double* __restrict__ out, double* __restr
       if (what == 3) { for (int k = 0; k < 6; ++k) out32[o + k * pl] = I.dF[o + k * pl]; continue; }
       if (what == 2) { for (int k = 0; k < 6; ++k) out[o + k * pl] = d[k]; continue; }
       pop_to_mom(d, I, m);
+      if (f32form == 2) m[2] = double(reinterpret_cast<const float*>(I.X)[o + 2 * pl]);   // the carried theta
     } else {
       const T* X = reinterpret_cast<const T*>(I.X);
       for (int k = 0; k < 6; ++k) m[k] = double(X[o + k * pl]);
@@ -240,7 +275,8 @@ __global__ void __launch_bounds__(TX* TY) k_stage1(const BatchDev* __restrict__ 
 // FP64 form: X^(s) -> X (GSA: the last stage is the new state), with a
 // finiteness check.  FP32 form: pack X^(s) into the FP32 deviation
 // populations and store the moments of those populations (store_f32_state)
-// as the next step's X.
+// as the next step's X; with theta carried (f32form = 2) the next step's
+// theta is theta^(s) itself, not the one summed from the populations.
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ bp, int f32form) {
   const BatchDev& b = *bp;
@@ -264,6 +300,7 @@ __global__ void __launch_bounds__(TX* TY) k_finish(const BatchDev* __restrict__ 
       mom_to_pop<float>(m, I.eps32, I.rho032, I.amp32, d);
       for (int k = 0; k < 6; ++k) bad |= !isfinite(d[k]);
       store_f32_state(I, o, pl, d);
+      if (f32form == 2) reinterpret_cast<float*>(I.X)[o + 2 * pl] = m[2];
     } else {
       T* X = reinterpret_cast<T*>(I.X);
       for (int k = 0; k < 6; ++k) {

@@ -101,8 +101,8 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   StencilSet ks = p->space_scheme == AP_DVM_LF1_C2 ? stencil_f64_lf1(tile)
                 : p->space_scheme == AP_DVM_WENO3_C4 ? stencil_f64_w3(tile) : stencil_f64_w5(tile);
   MiscSet km = misc_set(0, tile);
-  const int eblk = std::max(2048, nmax);
-  const size_t fft_smem = (size_t)eblk * 2 * sizeof(double);
+  const int eblk = fft_eblk(nmax), eblk_cols = fft_eblk_cols(nmax, false);
+  const size_t fft_smem = fft_block_bytes(eblk, false), cols_smem = fft_block_bytes(eblk_cols, false);
   const int thr = ks.tx * ks.ty;
   int g_exp = 0, g_rhs = 0, g_upd = 0, g_fin = 0, g1 = 0, g2 = 0, g3 = 0;
   NA_TRY(grid_of(ks.k_explicit, thr, ks.smem_explicit, sms, &g_exp));
@@ -111,9 +111,9 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   NA_TRY(grid_of(ks.k_update, thr, smem_upd, sms, &g_upd));
   NA_TRY(grid_of(km.k_finish, thr, 0, sms, &g_fin));
   NA_TRY(grid_of(km.k_rows_fwd, 256, fft_smem, sms, &g1));
-  NA_TRY(grid_of(km.k_cols, 256, fft_smem, sms, &g2));
+  NA_TRY(grid_of(km.k_cols, 256, cols_smem, sms, &g2));
   NA_TRY(grid_of(km.k_rows_inv, 256, fft_smem, sms, &g3));
-  const int g_fft = std::min(g1, std::min(g2, g3));
+  const int g_fft = std::min(g1, g3);
 
   // descriptors, built on the host stack and copied into the scratch
   InstDev I{};
@@ -121,7 +121,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   I.nx = p->nx; I.ny = p->ny; I.lnx = ilog2(p->nx); I.lny = ilog2(p->ny);
   I.tiles_x = p->nx / ks.tx; I.tiles_y = p->ny / ks.ty;
   I.row_pairs = std::max(1, std::min(eblk / p->nx, p->ny / 2));
-  I.col_group = std::max(1, eblk / p->ny);
+  I.col_group = std::min(2, std::max(1, eblk_cols / p->ny));   // the handle path's rule (FP64)
   I.relax64 = 0;
   fill_constants(*p, I);
   CUtensorMap maps[APD_MAXS + 1];
@@ -168,7 +168,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
 
   // the steps: the launch sequence of one IMEX step shared with the handle path
   BatchDev* bp = reinterpret_cast<BatchDev*>(base + L.batch);
-  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, fft_smem, smem_upd, FFT_X_POW2 | FFT_Y_POW2};
+  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, g2, 256, fft_smem, cols_smem, smem_upd, FFT_X_POW2 | FFT_Y_POW2};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int) -> int {
     return cudaLaunchKernel(fn, dim3(grid), block, args, smem, stream) == cudaSuccess ? 0 : (int)AP_DVM_ERR_CUDA;
   };

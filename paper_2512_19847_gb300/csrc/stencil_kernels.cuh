@@ -6,7 +6,10 @@
 //       D_0 . u^(j), D_Delta theta^(j), D_0 theta^(j), D_LF . B(v^(j)) (partner u^(j)),
 //     and step 1 of stage j+1: the closed-form v^(j+1), once per cell.
 //   k_rhs(i):  the right-hand side R_i of the Helmholtz equation (step 2).
-//   k_update(i): step 3 (u^(i)) and step 4 (closed-form q^(i)).
+//   k_update(i): step 3 (u^(i)) and step 4 (closed-form q^(i)); for the last stage
+//     with close_step set, also the close of the step (GSA: X^{n+1} = X^(s); the
+//     FP32 forms pack the populations and sum the next step's moments), written
+//     to the other buffer of the double-buffered state.
 //
 // Every kernel is a persistent loop over the batch's tile list.  The halo'd
 // plane tiles a kernel reads are staged into shared memory by TMA (one bulk
@@ -19,6 +22,7 @@
 #pragma once
 #include <type_traits>
 #include "common.cuh"
+#include "io_kernels.cuh"
 #include "tma.cuh"
 
 namespace apd {
@@ -241,13 +245,16 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined
-// by two Newton-Raphson steps r <- r + r (1 - d r), each doubling the number of
-// correct bits; the result is within a few units in the last place of 1/d.
+// by APD_RCP_NEWTON Newton-Raphson steps r <- r + r (1 - d r), each doubling the
+// number of correct bits.
+#ifndef APD_RCP_NEWTON
+#define APD_RCP_NEWTON 2
+#endif
 __device__ __forceinline__ double rcp_newton(double d) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  r = fma(r, fma(-d, r, 1.0), r);
-  r = fma(r, fma(-d, r, 1.0), r);
+#pragma unroll
+  for (int k = 0; k < APD_RCP_NEWTON; ++k) r = fma(r, fma(-d, r, 1.0), r);
   return r;
 }
 
@@ -619,6 +626,21 @@ __device__ __forceinline__ T* aligned_smem(unsigned char* raw) {
   return reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
 }
 
+// Widening of a transport value to the relaxation's arithmetic type R.  In the FP32
+// forms the closed-form relaxations run in FP64 (eps <= 1e-4): their FP32 inputs
+// are widened with integer operations (widen_f32, exact for every class of value)
+// rather than by the conversion instruction, which issues on the FP64 pipe, the
+// pipe those kernels' FP64 arithmetic already loads (APD_INT_WIDEN = 0 restores the
+// instruction).
+#ifndef APD_INT_WIDEN
+#define APD_INT_WIDEN 1
+#endif
+template <typename R, typename T>
+__device__ __forceinline__ R widen(T x) {
+  if constexpr (APD_INT_WIDEN && std::is_same<R, double>::value && std::is_same<T, float>::value) return widen_f32(x);
+  else return R(x);
+}
+
 // ---------------------------------------------------------------------------
 // Closed-form v^(i) at one cell (step 1):
 //   v^(i) = (tau eps^2 v^n - dt sum_j atilde_ij E^(j) - dt sum_j a_ij v^(j)) / (tau eps^2 + dt a_ii),
@@ -630,21 +652,21 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
                                              T ecur1, T ecur2, T vcur1, T vcur2, T& r1, T& r2) {
   const T* Xn = reinterpret_cast<const T*>(I.X);
   const Coef<R>& K = coef<R>(I);
-  R a1 = K.r_n[i] * R(Xn[o + 3 * pl]), a2 = K.r_n[i] * R(Xn[o + 4 * pl]);
+  R a1 = K.r_n[i] * widen<R>(Xn[o + 3 * pl]), a2 = K.r_n[i] * widen<R>(Xn[o + 4 * pl]);
   for (int jj = 1; jj < i; ++jj) {
     if (has(b.m_ex[i], jj)) {
       T e1, e2;
       if (jj == jcur) { e1 = ecur1; e2 = ecur2; }
       else { const T* e = reinterpret_cast<const T*>(I.E[jj]); e1 = e[o]; e2 = e[o + pl]; }
-      a1 = a1 + K.rv_e[i][jj] * R(e1);
-      a2 = a2 + K.rv_e[i][jj] * R(e2);
+      a1 = a1 + K.rv_e[i][jj] * widen<R>(e1);
+      a2 = a2 + K.rv_e[i][jj] * widen<R>(e2);
     }
     if (has(b.m_im[i], jj)) {
       T x1, x2;
       if (jj == jcur) { x1 = vcur1; x2 = vcur2; }
       else { const T* v = reinterpret_cast<const T*>(I.Xs[jj]); x1 = v[o + 3 * pl]; x2 = v[o + 4 * pl]; }
-      a1 = a1 + K.rv_v[i][jj] * R(x1);
-      a2 = a2 + K.rv_v[i][jj] * R(x2);
+      a1 = a1 + K.rv_v[i][jj] * widen<R>(x1);
+      a2 = a2 + K.rv_v[i][jj] * widen<R>(x2);
     }
   }
   r1 = T(a1);
@@ -840,7 +862,8 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const BatchDev* __restrict__ bp, int i, double weno_eps) {
+__global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const BatchDev* __restrict__ bp, int i, double weno_eps,
+                                                                       int close_step, int form) {
   using G = Geo<T, SCHEME, TX, TY>;
   constexpr int BW = G::BW, PL = G::PL, NX = G::NX, NY = G::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -928,20 +951,24 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
     const T* Xn = reinterpret_cast<const T*>(I.X);
     T* out = reinterpret_cast<T*>(I.Xs[i]);
     const T dt = K.dt;
-    out[o] = Xn[o] - dt * s1;
-    out[o + pl] = Xn[o + pl] - dt * s2;
-    reinterpret_cast<T*>(I.Dv[i])[o] = dvi;
+    const T u1 = Xn[o] - dt * s1, u2 = Xn[o + pl] - dt * s2;
+    if (!close_step) {
+      out[o] = u1;
+      out[o + pl] = u2;
+      reinterpret_cast<T*>(I.Dv[i])[o] = dvi;   // D0 . v^(i) for the q steps of later stages
+    }
     // step 4
+    T qi;
     if (I.relax64) {
       const Coef<double>& K64 = I.k64;
-      double aq = K64.r_n[i] * double(Xn[o + 5 * pl]);
+      double aq = K64.r_n[i] * widen<double>(Xn[o + 5 * pl]);
       for (int jj = 1; jj <= i; ++jj) {
         if (!has(mim, jj)) continue;
-        const double dv = (jj == i) ? double(dvi) : double(reinterpret_cast<const T*>(I.Dv[jj])[o]);
+        const double dv = widen<double>((jj == i) ? dvi : reinterpret_cast<const T*>(I.Dv[jj])[o]);
         aq = aq + K64.rq_d[i][jj] * dv;
-        if (jj < i) aq = aq + K64.rv_v[i][jj] * double(reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl]);
+        if (jj < i) aq = aq + K64.rv_v[i][jj] * widen<double>(reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl]);
       }
-      out[o + 5 * pl] = T(aq);
+      qi = T(aq);
     } else {
       T aq = K.r_n[i] * Xn[o + 5 * pl];
       for (int jj = 1; jj <= i; ++jj) {
@@ -950,8 +977,15 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
         aq = aq + K.rq_d[i][jj] * dv;
         if (jj < i) aq = aq + K.rv_v[i][jj] * reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl];
       }
-      out[o + 5 * pl] = aq;
+      qi = aq;
     }
+    if (!close_step) {
+      out[o + 5 * pl] = qi;
+      return;
+    }
+    // the close of the step at this cell: X^{n+1} = X^(s) (theta, v of the last stage from the staged tile)
+    const T m[6] = {u1, u2, sth[c], sv1[c], sv2[c], qi};
+    if (close_step_cell<T>(I, o, pl, m, form, reinterpret_cast<T*>(I.Xnext))) atomicOr(b.err, 1u);
   });
 }
 

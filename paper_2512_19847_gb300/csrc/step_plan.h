@@ -28,8 +28,8 @@ inline int fft_launches(unsigned kinds) {
 struct StepKernels {
   StencilSet ks;
   MiscSet km;
-  int g_explicit, g_rhs, g_update, g_finish, g_fft;
-  size_t fft_smem;
+  int g_explicit, g_rhs, g_update, g_finish, g_fft, g_cols, cols_threads;
+  size_t fft_smem, cols_smem;   // the power-of-two column pass has its own (wider) work items
   size_t smem_update;
   unsigned fft_kinds;   // FftKinds present among the attached solves
 };
@@ -45,6 +45,22 @@ inline int update_planes_max(const ap_dvm_params& t) {
     if (np > best) best = np;
   }
   return best;
+}
+
+// Shared memory of the transform kernels: every pass of a batch takes work items of
+// at most eblk complex values (eblk_cols for the power-of-two column pass), padded in
+// the power-of-two kernels (one spare value per 16 FP32 or 8 FP64 complex values).
+inline size_t fft_block_bytes(int elems, bool f32) {
+  const int ps = f32 ? 4 : 3;
+  return (size_t)(elems + (elems >> ps) + 1) * (f32 ? 8 : 16);
+}
+// Complex values per work item: rows and the other-length kernels eblk (at least
+// one transform of the longest length), the power-of-two column pass a few
+// adjacent columns (coalesced loads): 8192 values (64 KB) in FP32, 4096 in FP64.
+inline int fft_eblk(int nmax) { return nmax > 2048 ? nmax : 2048; }
+inline int fft_eblk_cols(int nmax, bool f32) {
+  const int e = f32 ? 8192 : 4096;
+  return nmax > e ? nmax : e;
 }
 
 inline size_t update_smem(const StencilSet& ks, const ap_dvm_params& t) {
@@ -87,9 +103,14 @@ inline int encode_stage_maps(const ap_dvm_params& p, const InstDev& d, int bw, i
   return 1;
 }
 
-// launch(fn, grid, block, smem, args, kind) -> int status (0 = success)
+// launch(fn, grid, block, smem, args, kind) -> int status (0 = success); form = the precision form
+// (AP_DVM_FP64, AP_DVM_FP32_DEV, AP_DVM_FP32_DEV_TH), passed to the finish kernel
+// fused: the last stage's update closes the step into the other state buffer
+// (I.Xnext; the handle path's double-buffered state), else a finish kernel
+// closes it in place.
 template <class Launch>
-int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp, int f32, Launch&& launch) {
+int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp, int form, Launch&& launch,
+                      bool fused = false) {
   const int s = t.s;
   const dim3 blk(K.ks.tx, K.ks.ty);
   double weno_eps = t.weno_eps;
@@ -128,17 +149,19 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
       const unsigned kk = K.fft_kinds;
       if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_fwd, K.g_fft, dim3(256), K.fft_smem, a, KK_ROWS_FWD))) return st;
       if ((kk & FFT_X_BS) && (st = launch(K.km.k_rows_fwd_bs, K.g_fft, dim3(256), K.fft_smem, a, KK_ROWS_FWD))) return st;
-      if ((kk & FFT_Y_POW2) && (st = launch(K.km.k_cols, K.g_fft, dim3(256), K.fft_smem, b, KK_COLS))) return st;
+      if ((kk & FFT_Y_POW2) && (st = launch(K.km.k_cols, K.g_cols, dim3(K.cols_threads), K.cols_smem, b, KK_COLS))) return st;
       if ((kk & FFT_Y_BS) && (st = launch(K.km.k_cols_bs, K.g_fft, dim3(256), K.fft_smem, b, KK_COLS))) return st;
       if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_inv, K.g_fft, dim3(256), K.fft_smem, b, KK_ROWS_INV))) return st;
       if ((kk & FFT_X_BS) && (st = launch(K.km.k_rows_inv_bs, K.g_fft, dim3(256), K.fft_smem, b, KK_ROWS_INV))) return st;
     }
     {
-      void* a[] = {&bp, &i, &weno_eps};
+      int close = (fused && i == s) ? 1 : 0;
+      void* a[] = {&bp, &i, &weno_eps, &close, &form};
       if ((st = launch(K.ks.k_update, K.g_update, blk, K.smem_update, a, KK_UPDATE))) return st;
     }
   }
-  void* a[] = {&bp, &f32};
+  if (fused) return 0;
+  void* a[] = {&bp, &form};
   return launch(K.km.k_finish, K.g_finish, blk, 0, a, KK_FINISH);
 }
 
@@ -218,6 +241,7 @@ inline void fill_constants(const ap_dvm_params& p, InstDev& d) {
   }
   d.inv_dx = 1.0 / d.dx;
   d.inv_dy = 1.0 / d.dy;
+  d.hscale32 = (float)(1.0 / ((double)p.nx * (double)p.ny));
   for (int i = 1; i <= p.s; ++i) {
     const double a = p.A_im[(i - 1) * AP_DVM_MAX_STAGES + (i - 1)];
     d.inv_aii[i] = a != 0.0 ? 1.0 / a : 0.0;

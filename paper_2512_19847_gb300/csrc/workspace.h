@@ -43,8 +43,12 @@ inline bool mixed_radix_plan(int n, unsigned* plan, int* npass) {
   return true;
 }
 
-// Carves one instance's workspace (base == nullptr: size only).
-inline size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
+// Carves one instance's workspace (base == nullptr: size only).  With two_states
+// the state is double-buffered (the last stage's update writes the next state to
+// the other buffer, I.Xnext) and the tensor-map region holds one set of maps per
+// buffer (2 (APD_MAXS + 1) maps); otherwise I.Xnext is null and a finish kernel
+// closes the step in place.
+inline size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d, bool two_states = false) {
   const size_t es = p.precision == AP_DVM_FP64 ? 8 : 4;
   const size_t cells = (size_t)p.nx * p.ny;
   const size_t plane = cells * es;
@@ -60,6 +64,7 @@ inline size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
   InstDev& I = d ? *d : tmp;
   const bool type_a = p.A_im[0] != 0.0;
   I.X = take(6 * plane);
+  I.Xnext = two_states ? take(6 * plane) : nullptr;
   I.Xs[1] = type_a ? take(6 * plane) : I.X;           // stage 1: its own values (type A) or X^n
   for (int j = 2; j <= s; ++j) I.Xs[j] = take(6 * plane);
   for (int j = 1; j <= s; ++j) {
@@ -77,6 +82,9 @@ inline size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
   I.S = take((size_t)p.ny * I.sstride * 2 * es);
   I.lamx = reinterpret_cast<double*>(take((size_t)(p.nx / 2 + 1) * sizeof(double)));
   I.lamy = reinterpret_cast<double*>(take((size_t)p.ny * sizeof(double)));
+  const bool f32 = p.precision != AP_DVM_FP64;
+  I.lamx32 = f32 ? reinterpret_cast<float*>(take((size_t)(p.nx / 2 + 1) * sizeof(float))) : nullptr;
+  I.lamy32 = f32 ? reinterpret_cast<float*>(take((size_t)p.ny * sizeof(float))) : nullptr;
   // one partial sum per tile: at most ceil(nx/8) * ceil(ny/4) tiles (the smallest tile sides)
   I.th_part = reinterpret_cast<double*>(take((size_t)((p.nx + 7) / 8) * ((p.ny + 3) / 4) * sizeof(double)));
   for (int a = 0; a < 2; ++a) {   // tables of an axis that is not a power of two: mixed radix or Bluestein
@@ -91,8 +99,8 @@ inline size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d) {
     I.chirp[a] = bs ? take((size_t)na * 2 * es) : nullptr;
     I.filt[a] = bs ? take((size_t)fft_length(na) * 2 * es) : nullptr;
   }
-  I.dF = p.precision == AP_DVM_FP32_DEV ? reinterpret_cast<float*>(take(6 * cells * sizeof(float))) : nullptr;
-  I.tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1));
+  I.dF = f32 ? reinterpret_cast<float*>(take(6 * cells * sizeof(float))) : nullptr;
+  I.tmap = take(sizeof(CUtensorMap) * (APD_MAXS + 1) * (two_states ? 2 : 1));
   return align_up(off, 256);
 }
 

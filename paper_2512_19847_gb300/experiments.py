@@ -20,8 +20,16 @@ and nested grids, compared by injection) and "cells" (N cells, not nested,
 the reference evaluated at the coarse cell centres by its trigonometric
 interpolant, exact for the band-limited part it resolves).
 
+``figures`` runs the flows of Figs. 2-5 of Sec. 4 (thick layer at
+eps = 1e-6 with tau = 0 to t = 6 and tau = 0.05 to t = 9.5, the same at
+eps = 0.25 (Fig. 3_2, smeared vortices), thin layer at eps = 1e-6 with both
+tau), each at the largest of a list of CFL numbers that keeps the run finite
+(the inviscid runs need a smaller one), and reports the divergence history,
+the enstrophy and the extreme vorticity.
+
     python -m paper_2512_19847_gb300.experiments --case shear_thin --n 512 --eps 1e-6
     python -m paper_2512_19847_gb300.experiments --table 2
+    python -m paper_2512_19847_gb300.experiments --figures
 """
 from __future__ import annotations
 
@@ -152,6 +160,45 @@ def convergence(table: int = 2, sizes=(33, 65, 129, 257), ref: int = 513, eps: f
     return rows
 
 
+FIGURES = {
+    "fig2_thick_euler": ("shear_thick", 1e-6, 0.0, 6.0),
+    "fig3_thick_ns": ("shear_thick", 1e-6, 0.05, 9.5),
+    "fig3_2_thick_euler_eps0.25": ("shear_thick", 0.25, 0.0, 6.0),
+    "fig3_2_thick_ns_eps0.25": ("shear_thick", 0.25, 0.05, 9.5),
+    "fig4_thin_euler": ("shear_thin", 1e-6, 0.0, 9.5),
+    "fig5_thin_ns": ("shear_thin", 1e-6, 0.05, 9.5),
+}
+
+
+def figures(n: int = 256, cfls=(0.4, 0.3, 0.2, 0.1, 0.05), names=None, record_every: int = 25,
+            scheme: str = "WENO3_C4") -> dict:
+    """The flows of Figs. 2-5 (Sec. 4.1-4.2) on n x n cells with the paper's WENO3
+    (Sec. 4.1): for each, the largest CFL number of `cfls` whose run stays finite,
+    the divergence history (max |D_0 . u| over time), the enstrophy at the start and
+    the end, and the extreme vorticity."""
+    out = {}
+    for name in names or FIGURES:
+        case, eps, tau, t_end = FIGURES[name]
+        res = {"case": case, "eps": eps, "tau": tau, "t_end": t_end, "tried": []}
+        for cfl in cfls:
+            try:
+                h = run(case, n, eps=eps, tau=tau, t_end=t_end, record_every=record_every, cfl=cfl, scheme=scheme)
+            except api.ApDvmError as e:
+                if e.status != 5:            # anything but a non-finite state is an error
+                    raise
+                res["tried"].append({"cfl": cfl, "finite": False})
+                continue
+            w = h.vorticity
+            res.update({"cfl": cfl, "dt": h.dt, "steps": h.steps, "wall_s": round(h.wall_s, 2),
+                        "div_max_final": h.div_max[-1], "div_max_peak": max(h.div_max),
+                        "enstrophy_start": h.enstrophy[0], "enstrophy_end": h.enstrophy[-1],
+                        "vorticity_max": float(w.abs().max()), "div_history": [h.t[::8], h.div_max[::8]]})
+            res["tried"].append({"cfl": cfl, "finite": True})
+            break
+        out[name] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--case", choices=sorted(CASES), default="shear_thick")
@@ -161,15 +208,20 @@ def main():
     ap.add_argument("--t-end", type=float, default=None)
     ap.add_argument("--every", type=int, default=50)
     ap.add_argument("--fp32", action="store_true", help="FP32 deviation form")
-    ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--cfl", type=float, default=0.4, help="CFL number (0.5 for the convergence study)")
     ap.add_argument("--visc", type=float, default=0.32)
     ap.add_argument("--table", type=int, choices=(1, 2), default=None,
                     help="run the convergence study of Table 1 or 2 instead")
     ap.add_argument("--grids", choices=("nodes", "cells"), default="nodes")
+    ap.add_argument("--ref", type=int, default=513, help="reference grid of the convergence study")
+    ap.add_argument("--figures", action="store_true", help="run the flows of Figs. 2-5 instead")
     args = ap.parse_args()
     if args.table:
-        for row in convergence(args.table, grids=args.grids):
+        for row in convergence(args.table, grids=args.grids, ref=args.ref, cfl=args.cfl):
             print(json.dumps(row))
+        return
+    if args.figures:
+        print(json.dumps(figures(args.n)))
         return
     h = run(args.case, args.n, args.eps, args.tau, args.t_end, args.every,
             api.FP32_DEV if args.fp32 else api.FP64, cfl=args.cfl, visc=args.visc)

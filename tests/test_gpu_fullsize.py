@@ -47,22 +47,29 @@ def test_precision_workload_2048_fp64_parity(field):
     assert np.all(_rel(got, ref) <= 1e-12), _rel(got, ref)
 
 
-def test_precision_workload_2048_fp32_error():
+# bounds at about twice the measured errors (GB300): AP_DVM_FP32_DEV sums theta from the FP32
+# populations, where it rides at O(eps); AP_DVM_FP32_DEV_TH carries it in its own FP32 plane
+FP32_BOUNDS = {api.FP32_DEV: (5e-6, 2.5e-3), api.FP32_DEV_TH: (5e-6, 2.5e-3)}
+
+
+@pytest.mark.parametrize("prec", [api.FP32_DEV, api.FP32_DEV_TH])
+def test_precision_workload_2048_fp32_error(prec):
     """FP32 deviation storage vs all-FP64 on the 2048^2 random divergence-free field,
-    eps = 1e-4, Ma = 1e-3, 10 steps: velocity within 1e-5 of max |u|; the
-    pressure error (theta rides at O(eps) inside the FP32 populations) is stated."""
+    eps = 1e-4, Ma = 1e-3, 10 steps: velocity within 1e-5 of max |u| (the stated
+    target), velocity and pressure errors within about twice their measured values."""
     n = 2048
     f = W.random_divfree(n, seed=2048)
     dt = W.stable_dt(f[0], f[1], 2 * math.pi / n, 0.05)
     a = _gpu(n, f, 1e-4, 1e-3, 0.05, dt, 10)
-    b = _gpu(n, f, 1e-4, 1e-3, 0.05, dt, 10, prec=api.FP32_DEV)
+    b = _gpu(n, f, 1e-4, 1e-3, 0.05, dt, 10, prec=prec)
     vel = np.max(np.hypot(a[0] - b[0], a[1] - b[1])) / np.max(np.hypot(a[0], a[1]))
     pa = a[2] - 0.5 * (a[0] ** 2 + a[1] ** 2)
     pb = b[2] - 0.5 * (b[0] ** 2 + b[1] ** 2)
     pr = np.max(np.abs((pb - pb.mean()) - (pa - pa.mean()))) / np.max(np.abs(pa - pa.mean()))
-    print(f"FP32 deviation form, 2048^2 random field, 10 steps: velocity {vel:.2e}, pressure {pr:.2e}")
-    assert vel <= 1e-5
-    assert pr <= 1e-2
+    print(f"FP32 form {prec}, 2048^2 random field, 10 steps: velocity {vel:.2e}, pressure {pr:.2e}")
+    vb, pbnd = FP32_BOUNDS[prec]
+    assert vel <= min(vb, 1e-5), vel
+    assert pr <= pbnd, pr
 
 
 @pytest.mark.parametrize("n", [4096, 4095])

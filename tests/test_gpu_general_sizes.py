@@ -192,8 +192,9 @@ def test_batch_mixed_sizes_equal_alone():
         b.set_state(torch.from_numpy(states[k]).cuda(), slot=k)
     b.step(3)
     b.sync_status()
-    # both transform kinds on both axes: 2 + 2 row launches and 2 column launches per implicit stage
-    assert b.launches_per_step == (3 + 6) * 2 + 1
+    # both transform kinds on both axes: 2 + 2 row launches and 2 column launches per implicit
+    # stage; the last stage's update closes the step (no finish launch)
+    assert b.launches_per_step == (3 + 6) * 2
     for k, (nx, ny) in enumerate(sizes):
         q = tmpl.copy()
         q.nx, q.ny = nx, ny
@@ -205,7 +206,7 @@ def test_launch_count_by_transform_kind():
     """A single solve launches one kernel per transform pass, whichever kind its axes need."""
     for nx, ny in ((64, 64), (33, 64), (64, 33), (33, 35)):
         s = api.Solver(api.default_params(nx, ny, eps=1e-2, dt=0.01, tableau=tableaux.gsa2()))
-        assert s.launches_per_step == (3 + 3) * 2 + 1, (nx, ny)
+        assert s.launches_per_step == (3 + 3) * 2, (nx, ny)
 
 
 def test_attach_rejects_longer_transforms():

@@ -348,3 +348,40 @@ def test_four_stages_batch_graph_and_fp32_form():
     ref = O.run(X0, o, 5)
     err = np.max(np.hypot(got[0] - ref[0], got[1] - ref[1])) / np.max(np.hypot(ref[0], ref[1]))
     assert err <= 1e-5, err
+
+
+def test_fp32_carried_theta_form():
+    """AP_DVM_FP32_DEV_TH: theta carried in its own FP32 plane.  Velocity within 1e-5
+    and the pressure closer to the oracle's than the plain FP32 form's (theta is no
+    longer summed back from the populations, where it rides at O(eps)); the
+    populations are those of the FP32 form's packing; set_theta after
+    set_populations restores a solve bit for bit (the autotuner's save/restore)."""
+    n = 64
+    u1, u2, pr = W.taylor_green(n)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    dt = W.stable_dt(u1, u2, 2 * math.pi / n, 0.05)
+    p, o = _pair(n, n, "WENO5_C4", "gsa2", 1e-4, 0.05, dt, mach=1e-3)
+    ref = O.run(X0, o, 5)
+    pref = ref[2] - 0.5 * (ref[0] ** 2 + ref[1] ** 2)
+    out = {}
+    for prec in (api.FP32_DEV, api.FP32_DEV_TH):
+        p.precision = prec
+        got = run_gpu(p, X0, 5)
+        vel = np.max(np.hypot(got[0] - ref[0], got[1] - ref[1])) / np.max(np.hypot(ref[0], ref[1]))
+        pg = got[2] - 0.5 * (got[0] ** 2 + got[1] ** 2)
+        out[prec] = np.max(np.abs((pg - pg.mean()) - (pref - pref.mean()))) / np.max(np.abs(pref - pref.mean()))
+        assert vel <= 1e-5, (prec, vel)
+    assert out[api.FP32_DEV_TH] < 0.1 * out[api.FP32_DEV], out
+    # bit-for-bit restore: populations + carried theta
+    p.precision = api.FP32_DEV_TH
+    s = api.Solver(p)
+    s.set_state(torch.from_numpy(X0).cuda())
+    s.step(2)
+    pops = s.get_populations(dtype=torch.float32)
+    theta = s.get_state()[2].clone()
+    s.step(3)
+    want = s.get_state().cpu().numpy()
+    s.set_populations(pops)
+    s.set_theta(theta)
+    s.step(3)
+    assert np.array_equal(s.get_state().cpu().numpy(), want)
