@@ -73,18 +73,18 @@ def step_bytes_per_cell(f32: bool) -> dict:
     e = 4 if f32 else 8
     planes = {
         # stage 1: read u, v, q (5), write E, D0.u, v^(2) (5);
-        # stage 2: read X^(2) (6), E^(1), v^n (4), write E, D0.u, D_Delta theta, D0 theta, D_LF.B(v), v^(3) (10)
-        "explicit": (5 + 5) + (10 + 10),
+        # stage 2: read X^(2) (6), E^(1), v^n (4), write E, D0.u, D_Delta theta, D_LF.B(v) + D0 theta, v^(3) (8)
+        "explicit": (5 + 5) + (10 + 8),
         # stage 2: read v^(2), theta^n, D0.u^n (4), write DB, R (2);
         # stage 3: read v^(3), theta^n, D0.u^n, D0.u^(2), DB^(2), D_Delta theta^(2) (7), write 2
         "rhs": (4 + 2) + (7 + 2),
         # each pass reads and writes one plane-equivalent (real plane or half spectrum), two solves
         "fft_rows_fwd": 4, "fft_cols": 4, "fft_rows_inv": 4,
         # stage 2: read theta, v, u^(1), u^n, q^n (8), write u, q, D0.v (4);
-        # stage 3: read theta, v, u^(1), u^(2), u^n, q^n, D_LF.B(v)^(2), D0 theta^(2), D0.v^(2), q^(2) (16),
+        # stage 3: read theta, v, u^(1), u^(2), u^n, q^n, D_LF.B(v)^(2) + D0 theta^(2), D0.v^(2), q^(2) (14),
         # and close the step: write X^{n+1} (6; FP32 forms: the populations and the next step's
         # FP64-summed moments, 12)
-        "update": (8 + 4) + (16 + (12 if f32 else 6))}
+        "update": (8 + 4) + (14 + (12 if f32 else 6))}
     return {k: v * e for k, v in planes.items()}
 
 

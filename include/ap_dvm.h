@@ -223,8 +223,8 @@ ap_dvm_status ap_dvm_run_host(ap_dvm_handle* h, int slot, const double* h_in, do
  * real-time loops that forbid allocation after start-up, or plugins loaded
  * into a process whose allocator they may not touch.
  *  p          parameters (FP64 form only; nx, ny powers of two <= 128 and
- *             the whole scratch of the solve <= 8 MiB: up to 3 stages at
- *             128 x 128).
+ *             the whole scratch of the solve <= 8 MiB: at 128 x 128, CK/ARS
+ *             tableaux up to 4 stages, type-A tableaux up to 3).
  *  d_state6   device moment state, 6 double planes (u1, u2, theta, v1, v2, q):
  *             read at the start, overwritten with the state after nsteps.
  *  cuda_stream  stream for the copies and kernels.

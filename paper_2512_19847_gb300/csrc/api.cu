@@ -543,15 +543,17 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   hb.s = tmpl->s;
   fill_tableau(*tmpl, hb);
   hb.err = h->d_err;
-  // synchronous uploads: the host vectors go out of scope
-  CUDA_TRY(h, cudaMemcpy(h->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice));
-  CUDA_TRY(h, cudaMemcpy(h->d_tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice));
+  // uploads on the handle's stream (no legacy-stream serialisation against the caller's other
+  // streams), synchronised below: the host vectors go out of scope
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_tw32, tw32.data(), sizeof(float2) * tw32.size(), cudaMemcpyHostToDevice, h->stream));
   h->hb[1] = hb;
   h->hb[1].inst = h->d_inst[1];
-  for (int par = 0; par < 2; ++par) CUDA_TRY(h, cudaMemcpy(h->d_batch[par], &h->hb[par], sizeof(BatchDev), cudaMemcpyHostToDevice));
-  CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned) * 4));
-  int zeros[4] = {0, 0, 0, 0};
-  CUDA_TRY(h, cudaMemcpy(h->d_counts, zeros, sizeof(zeros), cudaMemcpyHostToDevice));
+  for (int par = 0; par < 2; ++par)
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_batch[par], &h->hb[par], sizeof(BatchDev), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned) * 4, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_counts, 0, sizeof(int) * 4, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->slots.resize(capacity);
   h->dirty = true;
   return AP_DVM_OK;
@@ -843,8 +845,9 @@ ap_dvm_status ap_dvm_sync_status(ap_dvm_handle* h) {
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   CUDA_TRY(h, cudaGetLastError());
   unsigned flags = 0;
-  CUDA_TRY(h, cudaMemcpy(&flags, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  if (flags) CUDA_TRY(h, cudaMemset(h->d_err, 0, sizeof(unsigned)));
+  CUDA_TRY(h, cudaMemcpyAsync(&flags, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (flags) CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
   if (flags & 2u) return fail(h, AP_DVM_ERR_TIMEOUT, "a bounded device wait expired (results since the last check are invalid)");
   if (flags & 1u) return fail(h, AP_DVM_ERR_NONFINITE, "a step produced a non-finite value");
   return AP_DVM_OK;

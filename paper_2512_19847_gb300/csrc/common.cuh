@@ -81,8 +81,8 @@ struct InstDev {
   void* Du[APD_MAXS + 1];       // D_0 . u^(j)
   void* Dun;                    // D_0 . u^n (= Du[1] when stage 1 is X^n)
   void* Lth[APD_MAXS + 1];      // D_Delta theta^(j)
-  void* Gth[APD_MAXS + 1];      // D_0 theta^(j) (2 planes)
-  void* DLFB[APD_MAXS + 1];     // D_LF . B(v^(j)) with partner u^(j) (2 planes)
+  void* DLFB[APD_MAXS + 1];     // D_LF . B(v^(j)) with partner u^(j), plus D_0 theta^(j) (2 planes):
+                                // step 3 of later stages uses the two only as this sum
   void* Dv[APD_MAXS + 1];       // D0_LF . v^(j)
   void* DB[APD_MAXS + 1];       // D_0^2 : B(v^(j))
   void* R;                      // Helmholtz right-hand side

@@ -3,7 +3,7 @@
 //   k_explicit(j): explicit term of step 1 for stage j,
 //       E^(j) = (tau/4) D0_LF . B(u^(j)) + tau eps^2 D_LF q^(j) - F(u^(j)),
 //     the derived operators of stage j that later stages reuse
-//       D_0 . u^(j), D_Delta theta^(j), D_0 theta^(j), D_LF . B(v^(j)) (partner u^(j)),
+//       D_0 . u^(j), D_Delta theta^(j), D_LF . B(v^(j)) (partner u^(j)) + D_0 theta^(j),
 //     and step 1 of stage j+1: the closed-form v^(j+1), once per cell.
 //   k_rhs(i):  the right-hand side R_i of the Helmholtz equation (step 2).
 //   k_update(i): step 3 (u^(i)) and step 4 (closed-form q^(i)); for the last stage
@@ -18,7 +18,11 @@
 // Upwind fluxes are then computed one axis at a time: for every flux/partner
 // pair the Lax-Friedrichs splitting g+- = (g +- U)/2 and the curvature part
 // of the WENO5 smoothness indicators are evaluated once per point, then each
-// interface flux once, then differenced.
+// interface flux once, then differenced.  The WENO fluxes take the split without
+// its factor 1/2 (g +- U, with eps_W scaled by 4): every operation of a WENO
+// reconstruction is homogeneous under a power-of-two scaling of its inputs once
+// eps_W scales with the indicators, so the interface flux comes out exactly twice
+// the one of (g +- U)/2, and the 1/2 joins 1/dx in the flux difference (flux_scale).
 #pragma once
 #include <type_traits>
 #include "common.cuh"
@@ -27,7 +31,7 @@
 
 namespace apd {
 
-enum NeedBits { NEED_E = 1, NEED_DU = 2, NEED_LTH = 4, NEED_GTH = 8, NEED_DLFB = 16, NEED_V = 32 };
+enum NeedBits { NEED_E = 1, NEED_DU = 2, NEED_LTH = 4, NEED_DLFB = 16, NEED_V = 32 };
 
 // Geometry of a staged plane tile: rows y0-H .. y0+TY+H-1, columns
 // x0-4 .. x0+TX+3 (row stride BW); logical tile column 0 (x = x0-H) sits at
@@ -329,9 +333,8 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
     const T* gp = pick<NP>(g, pr);
     const T gv = ((NEG >> pr) & 1u) ? -gp[o] : gp[o];
     const T uv = pick<NP>(U, pr)[o];
-    const T hg = T(0.5) * gv;
-    split[(4 * pr + 0) * LS + r] = hg + T(0.5) * uv;
-    split[(4 * pr + 1) * LS + r] = hg - T(0.5) * uv;
+    split[(4 * pr + 0) * LS + r] = gv + uv;   // 2 g+ and 2 g- (the flux comes out doubled)
+    split[(4 * pr + 1) * LS + r] = gv - uv;
   }
   __syncthreads();
   if (SCHEME == WENO3_C4) {
@@ -343,12 +346,12 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
       const T* Pp = split + (4 * pr + 0) * LS + c;
       const T* Mm = split + (4 * pr + 1) * LS + c;
       out[pr * NL * NI + out_off(line, m)] =
-          weno3<T>(Pp[-PS], Pp[0], Pp[PS], ew) + weno3<T>(Mm[2 * PS], Mm[PS], Mm[0], ew);
+          weno3<T>(Pp[-PS], Pp[0], Pp[PS], T(4) * ew) + weno3<T>(Mm[2 * PS], Mm[PS], Mm[0], T(4) * ew);
     }
     return;
   }
-  // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W
-  const T ew4 = T(4) * ew;
+  // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W (x 4 for the doubled split)
+  const T ew4 = T(16) * ew;
   for (int k = tid; k < 2 * NP * LS; k += NT) {
     const int q = k / LS, r = k - q * LS;
     int line, pt;
@@ -434,17 +437,16 @@ __device__ __forceinline__ void w5_runs_item(const float* g, const UF& U, bool n
   constexpr int RUNS = (NI + KR - 1) / KR;
   constexpr bool CLAMP = RUNS * KR + 4 > (AX == 0 ? TX + 6 : LL - 1);
   const int m0 = run * KR;
-  const float hs = neg ? -0.5f : 0.5f;
-  float Pp[NPT], Pm[NPT];   // g+ and g- at points m0 .. m0 + KR + 4 of the line (interface m has centre point m + 2)
+  float Pp[NPT], Pm[NPT];   // 2 g+ and 2 g- at points m0 .. m0 + KR + 4 of the line (interface m has centre point m + 2)
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
     const int pt = CLAMP ? min(m0 + j, LL - 1) : m0 + j;
     const int o = AX == 0 ? (H + line) * SW + XO + pt : pt * SW + XO + H + line;
-    const float hg = hs * g[o], hu = 0.5f * U(o);
-    Pp[j] = hg + hu;
-    Pm[j] = hg - hu;
+    const float gv = neg ? -g[o] : g[o], uv = U(o);
+    Pp[j] = gv + uv;
+    Pm[j] = gv - uv;
   }
-  float Cp[NPT], Cm[NPT];   // (13/3) (f_{j-1} - 2 f_j + f_{j+1})^2 + 4 eps_W
+  float Cp[NPT], Cm[NPT];   // (13/3) (f_{j-1} - 2 f_j + f_{j+1})^2 + 16 eps_W (indicators x 4, doubled split)
 #pragma unroll
   for (int j = 1; j <= KR + 3; ++j) {
     const float cp = fmaf(-2.f, Pp[j], Pp[j - 1]) + Pp[j + 1];
@@ -469,7 +471,7 @@ __device__ __forceinline__ void w5_runs_both_axes(const float* const* gx, const 
   constexpr int RX = (TX + 1 + KR - 1) / KR, RY = (TY + 1 + KR - 1) / KR;
   constexpr int IX = NP * TY * RX, IY = NP * TX * RY;
   constexpr int NXI = TY * (TX + 1), NYI = (TY + 1) * TX;
-  const float ew4 = 4.f * ew;
+  const float ew4 = 16.f * ew;   // 4 eps_W, x 4 for the doubled split
   for (int k = tid; k < IX + IY; k += NT) {
     if (k < IX) {
       const int pr = k / (TY * RX), r = k - pr * (TY * RX), run = r / TY, line = r - run * TY;
@@ -504,9 +506,8 @@ __device__ __forceinline__ void w5_fluxes_xy(const T* const* gx, const T* const*
       const T* gp = pick<NP>(gx, pr);
       const T gv = ((NEGX >> pr) & 1u) ? -gp[o] : gp[o];
       const T uv = pick<NP>(ux, pr)[o];
-      const T hg = T(0.5) * gv;
-      spx[(4 * pr + 0) * LSX + r] = hg + T(0.5) * uv;
-      spx[(4 * pr + 1) * LSX + r] = hg - T(0.5) * uv;
+      spx[(4 * pr + 0) * LSX + r] = gv + uv;   // doubled split, as in axis_fluxes
+      spx[(4 * pr + 1) * LSX + r] = gv - uv;
     } else {
       const int kk = k - NP * LSX;
       const int pr = kk / LSY, r = kk - pr * LSY, pt = r / TX, line = r - pt * TX;
@@ -514,14 +515,13 @@ __device__ __forceinline__ void w5_fluxes_xy(const T* const* gx, const T* const*
       const T* gp = pick<NP>(gy, pr);
       const T gv = ((NEGY >> pr) & 1u) ? -gp[o] : gp[o];
       const T uv = pick<NP>(uy, pr)[o];
-      const T hg = T(0.5) * gv;
-      spy[(4 * pr + 0) * LSY + r] = hg + T(0.5) * uv;
-      spy[(4 * pr + 1) * LSY + r] = hg - T(0.5) * uv;
+      spy[(4 * pr + 0) * LSY + r] = gv + uv;
+      spy[(4 * pr + 1) * LSY + r] = gv - uv;
     }
   }
   __syncthreads();
-  // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W
-  const T ew4 = T(4) * ew;
+  // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W (x 4 for the doubled split)
+  const T ew4 = T(16) * ew;
   for (int k = tid; k < 2 * NP * (LSX + LSY); k += NT) {
     if (k < 2 * NP * LSX) {
       const int q = k / LSX, r = k - q * LSX, line = r / W, pt = r - line * W;
@@ -673,6 +673,11 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
   r2 = T(a2);
 }
 
+// Factor of 1/h in the difference of interface fluxes: the WENO fluxes come out
+// doubled (the split without its 1/2), the LF1 flux of Sec. 3.2 does not.
+template <typename T, int SCHEME>
+__device__ __forceinline__ T flux_scale(T inv_h) { return SCHEME == LF1_C2 ? inv_h : T(0.5) * inv_h; }
+
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const BatchDev* __restrict__ bp, int j, unsigned need, double weno_eps) {
@@ -723,14 +728,15 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const 
     if (t.x0 + tx >= nx || t.y0 + ty >= I.ny) return;   // beyond the grid (ragged edge tile)
     const Coef<T>& K = coef<T>(I);
     const T idx = K.inv_dx, idy = K.inv_dy;
+    const T fidx = flux_scale<T, SCHEME>(idx), fidy = flux_scale<T, SCHEME>(idy);
     const int c = G::C00 + ty * BW + tx;
     const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
     T e1 = T(0), e2 = T(0);
     if (needE) {
       const T b1 = cdiff<T, SCHEME>(su2 + c, BW, idy) - cdiff<T, SCHEME>(su1 + c, 1, idx);
       const T b2 = cdiff<T, SCHEME>(su2 + c, 1, idx) + cdiff<T, SCHEME>(su1 + c, BW, idy);
-      const T g1 = (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * idx;
-      const T g2 = (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * idy;
+      const T g1 = (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * fidx;
+      const T g2 = (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * fidy;
       const T a1 = su1[c], a2 = su2[c];
       const T f1 = T(0.5) * (a2 * a2 - a1 * a1), f2 = a1 * a2;
       const T qt = K.qtau, te2 = K.te2;
@@ -746,21 +752,18 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const 
     if (need & NEED_LTH) {
       reinterpret_cast<T*>(I.Lth[j])[o] = cdiff2<T, SCHEME>(sth + c, 1, idx * idx) + cdiff2<T, SCHEME>(sth + c, BW, idy * idy);
     }
-    if (need & NEED_GTH) {
-      T* gt = reinterpret_cast<T*>(I.Gth[j]);
-      gt[o] = cdiff<T, SCHEME>(sth + c, 1, idx);
-      gt[o + pl] = cdiff<T, SCHEME>(sth + c, BW, idy);
-    }
     if (needB) {
+      // step 3 of every later stage uses D_LF . B(v^(j)) and D_0 theta^(j) only as their
+      // sum (times a_ij): one 2-plane field, summed here as it was summed there
       const T* fxb = fx + NX;
       const T* fyb = fy + NY;
-      const T d1 = (fxb[ty * (TX + 1) + tx + 1] - fxb[ty * (TX + 1) + tx]) * idx +
-                   (fyb[(ty + 1) * TX + tx] - fyb[ty * TX + tx]) * idy;
-      const T d2 = (fxb[NX + ty * (TX + 1) + tx + 1] - fxb[NX + ty * (TX + 1) + tx]) * idx +
-                   (fyb[NY + (ty + 1) * TX + tx] - fyb[NY + ty * TX + tx]) * idy;
+      const T d1 = (fxb[ty * (TX + 1) + tx + 1] - fxb[ty * (TX + 1) + tx]) * fidx +
+                   (fyb[(ty + 1) * TX + tx] - fyb[ty * TX + tx]) * fidy;
+      const T d2 = (fxb[NX + ty * (TX + 1) + tx + 1] - fxb[NX + ty * (TX + 1) + tx]) * fidx +
+                   (fyb[NY + (ty + 1) * TX + tx] - fyb[NY + ty * TX + tx]) * fidy;
       T* db = reinterpret_cast<T*>(I.DLFB[j]);
-      db[o] = d1;
-      db[o + pl] = d2;
+      db[o] = d1 + cdiff<T, SCHEME>(sth + c, 1, idx);
+      db[o + pl] = d2 + cdiff<T, SCHEME>(sth + c, BW, idy);
     }
     if (need & NEED_V) {
       // step 1 of stage i = j + 1 at this cell
@@ -929,21 +932,21 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
     __syncthreads();
     if (t.x0 + tx >= nx || t.y0 + ty >= I.ny) return;   // beyond the grid (ragged edge tile)
     const T idx = K.inv_dx, idy = K.inv_dy;
+    const T fidx = flux_scale<T, SCHEME>(idx), fidy = flux_scale<T, SCHEME>(idy);
     const int c = G::C00 + ty * BW + tx;
     const size_t o = (size_t)(t.y0 + ty) * nx + (t.x0 + tx);
-    const T d1 = (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * idx + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * idy;
-    const T d2 = (fx[NX + ty * (TX + 1) + tx + 1] - fx[NX + ty * (TX + 1) + tx]) * idx +
-                 (fy[NY + (ty + 1) * TX + tx] - fy[NY + ty * TX + tx]) * idy;
+    const T d1 = (fx[ty * (TX + 1) + tx + 1] - fx[ty * (TX + 1) + tx]) * fidx + (fy[(ty + 1) * TX + tx] - fy[ty * TX + tx]) * fidy;
+    const T d2 = (fx[NX + ty * (TX + 1) + tx + 1] - fx[NX + ty * (TX + 1) + tx]) * fidx +
+                 (fy[NY + (ty + 1) * TX + tx] - fy[NY + ty * TX + tx]) * fidy;
     const T g1 = cdiff<T, SCHEME>(sth + c, 1, idx), g2 = cdiff<T, SCHEME>(sth + c, BW, idy);
     const T dvi = cdiff<T, SCHEME>(sv1 + c, 1, idx) + cdiff<T, SCHEME>(sv2 + c, BW, idy);
     // step 3
     T s1 = T(0), s2 = T(0);
     for (int jj = 1; jj < i; ++jj) {
       if (has(mim, jj)) {
-        const T* db = reinterpret_cast<const T*>(I.DLFB[jj]);
-        const T* gt = reinterpret_cast<const T*>(I.Gth[jj]);
-        s1 = s1 + K.aim[i][jj] * (db[o] + gt[o]);
-        s2 = s2 + K.aim[i][jj] * (db[o + pl] + gt[o + pl]);
+        const T* bg = reinterpret_cast<const T*>(I.DLFB[jj]);   // D_LF . B(v^(jj)) + D_0 theta^(jj)
+        s1 = s1 + K.aim[i][jj] * bg[o];
+        s2 = s2 + K.aim[i][jj] * bg[o + pl];
       }
     }
     s1 = s1 + K.aim[i][i] * (d1 + g1);

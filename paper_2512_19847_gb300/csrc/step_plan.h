@@ -129,7 +129,7 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
     unsigned need = 32u;                                   // v^(i), step 1 of stage i
     for (int k = j + 1; k <= s; ++k) {
       if (AEX(k, j) != 0.0) need |= 1u;                    // E^(j)
-      if (AIM(k, j) != 0.0) need |= 2u | 4u | 8u | 16u;    // D0.u, D_Delta theta, D0 theta, D_LF.B(v) of stage j
+      if (AIM(k, j) != 0.0) need |= 2u | 4u | 16u;        // D0.u, D_Delta theta, D_LF.B(v) + D0 theta of stage j
     }
     if (j == 1 && !type_a) need |= 2u;                     // D0 . u^n (= D0 . u^(1)) enters every right-hand side
     if (j >= 1) {

@@ -71,7 +71,6 @@ inline size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d, boo
     I.E[j] = take(2 * plane);
     I.Du[j] = take(plane);
     I.Lth[j] = take(plane);
-    I.Gth[j] = take(2 * plane);
     I.DLFB[j] = take(2 * plane);
     I.Dv[j] = take(plane);
     I.DB[j] = take(plane);

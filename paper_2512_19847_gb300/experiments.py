@@ -20,6 +20,9 @@ and nested grids, compared by injection) and "cells" (N cells, not nested,
 the reference evaluated at the coarse cell centres by its trigonometric
 interpolant, exact for the band-limited part it resolves).
 
+``uniform_in_eps`` repeats the Table 2 study for several eps at tau = 0 and
+0.05 (Fig. 1: the error at fixed N and dt stays bounded as eps varies).
+
 ``figures`` runs the flows of Figs. 2-5 of Sec. 4 (thick layer at
 eps = 1e-6 with tau = 0 to t = 6 and tau = 0.05 to t = 9.5, the same at
 eps = 0.25 (Fig. 3_2, smeared vortices), thin layer at eps = 1e-6 with both
@@ -30,6 +33,7 @@ the enstrophy and the extreme vorticity.
     python -m paper_2512_19847_gb300.experiments --case shear_thin --n 512 --eps 1e-6
     python -m paper_2512_19847_gb300.experiments --table 2
     python -m paper_2512_19847_gb300.experiments --figures
+    python -m paper_2512_19847_gb300.experiments --uniform
 """
 from __future__ import annotations
 
@@ -160,6 +164,18 @@ def convergence(table: int = 2, sizes=(33, 65, 129, 257), ref: int = 513, eps: f
     return rows
 
 
+def uniform_in_eps(eps_values=(1e-6, 1e-4, 1e-2, 0.25), taus=(0.0, 0.05), sizes=(33, 65, 129), ref: int = 257,
+                   cfl: float = 0.5) -> dict:
+    """Fig. 1 of Sec. 4.1: the Table 2 study (second-order tableau, WENO3, thick layer,
+    t = 1) repeated for several eps at tau = 0 and tau = 0.05; the scheme is uniformly
+    accurate in eps when the errors at fixed (N, dt) stay bounded as eps varies."""
+    out = {}
+    for tau in taus:
+        for eps in eps_values:
+            out[f"tau{tau:g}_eps{eps:g}"] = convergence(2, sizes=sizes, ref=ref, eps=eps, tau=tau, cfl=cfl)
+    return out
+
+
 FIGURES = {
     "fig2_thick_euler": ("shear_thick", 1e-6, 0.0, 6.0),
     "fig3_thick_ns": ("shear_thick", 1e-6, 0.05, 9.5),
@@ -215,6 +231,7 @@ def main():
     ap.add_argument("--grids", choices=("nodes", "cells"), default="nodes")
     ap.add_argument("--ref", type=int, default=513, help="reference grid of the convergence study")
     ap.add_argument("--figures", action="store_true", help="run the flows of Figs. 2-5 instead")
+    ap.add_argument("--uniform", action="store_true", help="run the eps-uniformity study of Fig. 1 instead")
     args = ap.parse_args()
     if args.table:
         for row in convergence(args.table, grids=args.grids, ref=args.ref, cfl=args.cfl):
@@ -222,6 +239,9 @@ def main():
         return
     if args.figures:
         print(json.dumps(figures(args.n)))
+        return
+    if args.uniform:
+        print(json.dumps(uniform_in_eps()))
         return
     h = run(args.case, args.n, args.eps, args.tau, args.t_end, args.every,
             api.FP32_DEV if args.fp32 else api.FP64, cfl=args.cfl, visc=args.visc)

@@ -49,7 +49,8 @@ def test_precision_workload_2048_fp64_parity(field):
 
 # bounds at about twice the measured errors (GB300): AP_DVM_FP32_DEV sums theta from the FP32
 # populations, where it rides at O(eps); AP_DVM_FP32_DEV_TH carries it in its own FP32 plane
-FP32_BOUNDS = {api.FP32_DEV: (5e-6, 2.5e-3), api.FP32_DEV_TH: (5e-6, 2.5e-3)}
+# measured (GB300, this workload, 10 steps): velocity 7.6e-7 for both, pressure 8.4e-4 and 7.0e-5
+FP32_BOUNDS = {api.FP32_DEV: (1.6e-6, 1.7e-3), api.FP32_DEV_TH: (1.6e-6, 1.5e-4)}
 
 
 @pytest.mark.parametrize("prec", [api.FP32_DEV, api.FP32_DEV_TH])

@@ -35,11 +35,11 @@ def _rel(a, b):
     return np.max(np.abs(a - b), axis=(1, 2)) / np.maximum(np.max(np.abs(b), axis=(1, 2)), 1e-300)
 
 
-# ("WENO5_C4", 128, 128, "type_a3") is the largest layout the 8 MiB scratch takes:
-# three stages and type A's own stage-1 buffer at 128 x 128
+# the largest layouts the 8 MiB scratch takes at 128 x 128: four stages of a CK/ARS tableau
+# (ars4), three stages of a type-A tableau (type_a3, with its own stage-1 buffer)
 @pytest.mark.parametrize("scheme,nx,ny,tab", [("WENO5_C4", 64, 64, "gsa2"), ("LF1_C2", 128, 128, "gsa2"),
                                               ("WENO3_C4", 16, 16, "gsa2"), ("WENO5_C4", 64, 64, "type_a3"),
-                                              ("WENO5_C4", 128, 128, "type_a3"), ("WENO5_C4", 64, 64, "ars4")])
+                                              ("WENO5_C4", 128, 128, "type_a3"), ("WENO5_C4", 128, 128, "ars4")])
 def test_noalloc_matches_handle_path_two_calls(scheme, nx, ny, tab):
     fn = _noalloc()
     X0 = W.random_moment_state(nx, ny, seed=404, amp=0.4)
@@ -103,9 +103,12 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     d = torch.zeros((6, 256, 256), dtype=torch.float64, device="cuda")
     p = api.default_params(256, 256, eps=1e-2, dt=0.01)
     assert fn(ctypes.byref(p), d.data_ptr(), 1, stream) == 1          # AP_DVM_ERR_ARG
-    p4 = api.default_params(128, 128, eps=1e-2, dt=0.01, tableau=tableaux.ars4())
+    # a four-stage type-A tableau (its own stage-1 buffer) at 128^2 exceeds the 8 MiB
+    A_ex = [[0, 0, 0, 0], [0.5, 0, 0, 0], [0.25, 0.25, 0, 0], [0.2, 0.3, 0.5, 0]]
+    A_im = [[0.5, 0, 0, 0], [0, 0.5, 0, 0], [0, 0.25, 0.5, 0], [0, 0.25, 0.25, 0.5]]
+    p4 = api.default_params(128, 128, eps=1e-2, dt=0.01, tableau=(A_ex, A_im))
     d4 = torch.zeros((6, 128, 128), dtype=torch.float64, device="cuda")
-    assert fn(ctypes.byref(p4), d4.data_ptr(), 1, stream) == 1        # 4 stages at 128^2 exceed 8 MiB
+    assert fn(ctypes.byref(p4), d4.data_ptr(), 1, stream) == 1
     p5 = api.default_params(96, 64, eps=1e-2, dt=0.01)                 # not a power of two
     d5 = torch.zeros((6, 64, 96), dtype=torch.float64, device="cuda")
     assert fn(ctypes.byref(p5), d5.data_ptr(), 1, stream) == 7         # AP_DVM_ERR_UNSUPPORTED
