@@ -157,12 +157,15 @@ def make_solver(n, eps, mach, tau, dt, f32: bool, scheme="WENO5_C4"):
     return api.Solver(p)
 
 
-def time_form(torch, fields, n, eps, mach, tau, dt, f32, steps, warmup, barrier, graph_steps=1):
+def time_form(torch, fields, n, eps, mach, tau, dt, f32, steps, warmup, barrier, graph_steps=1, tile=None):
     s = make_solver(n, eps, mach, tau, dt, f32)
     s.set_equilibrium(*[torch.from_numpy(a).cuda() for a in fields])
-    # tile shape from the autotuner (state saved and restored bit for bit)
-    from paper_2512_19847_gb300 import autotune
-    s.tuned = autotune.tune(s, steps=2, path=None)
+    if tile is not None:                                 # a fixed tile shape (profiling runs)
+        s.set_tile(tile)
+        s.tuned = {"tile": tile, "ms_per_step": {}, "cached": False, "fixed": True}
+    else:                                                # the autotuner (state saved and restored bit for bit)
+        from paper_2512_19847_gb300 import autotune
+        s.tuned = autotune.tune(s, steps=2, path=None)
     s.set_graph_steps(graph_steps)
     s.step(warmup)
     s.sync_status()
@@ -599,6 +602,9 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--fp64-peak", action="store_true", help="print only the FMA-peak legs (FP64 and FP32) and exit")
     ap.add_argument("--served-sweep", action="store_true", help="also sweep the served form's arrival rate")
+    ap.add_argument("--tiles", default=None,
+                    help="FP64,FP32 tile indices (autotune.TILES) instead of the autotuner, e.g. 5,2 for profiling "
+                         "runs, whose perturbed timings would make the autotuner pick other shapes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -629,13 +635,16 @@ def main():
         return
     fields, dt = workload(n, args.eps, args.mach, args.tau)
     peaks = load_peaks()
+    tile64, tile32 = (int(t) for t in args.tiles.split(",")) if args.tiles else (None, None)
 
     with ClockSampler(local) as clk:
-        s64, ms64 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, False, args.steps, args.warmup, barrier)
+        s64, ms64 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, False, args.steps, args.warmup, barrier,
+                              tile=tile64)
     clocks = clk.summary()
     fp64_leg = fma_peak_leg(local, api.FP64, 256)
     fp64_peak = scaled_peak(fp64_leg, clocks)
-    s32, ms32 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, True, args.steps, args.warmup, barrier)
+    s32, ms32 = time_form(torch, fields, n, args.eps, args.mach, args.tau, dt, True, args.steps, args.warmup, barrier,
+                          tile=tile32)
 
     v64, ms64 = replica_rate(ms64, cells, args.steps, dist, "cuda")
     v32, ms32 = replica_rate(ms32, cells, args.steps, dist, "cuda")
