@@ -189,6 +189,18 @@ ap_dvm_status ap_dvm_diagnostics(ap_dvm_handle* h, int slot, double* d_vorticity
  * graph steps k > 0 (ap_dvm_set_graph_steps) the steps are replayed from a
  * CUDA graph of k steps. */
 ap_dvm_status ap_dvm_step(ap_dvm_handle* h, int nsteps);
+/* Advance the attached solves by different numbers of steps in one call: the
+ * solve in slot k by steps_per_slot[k] steps (host array of capacity entries,
+ * read for attached slots only, each in [0, nsteps]; else AP_DVM_ERR_ARG and
+ * nothing runs).  The call runs nsteps steps at most, as ap_dvm_step does, in
+ * segments between the counts at which solves drop out: a solve whose count is
+ * reached sits out the remaining steps (it leaves the kernels' work lists and
+ * its state stays as it is), so a short request does not shorten the others'
+ * share of the call.  Each solve ends exactly where ap_dvm_step would leave it
+ * after its own count of steps.  Asynchronous; the work lists are re-uploaded
+ * at each change of the stepping set (stream-ordered copies), so the call may
+ * not run inside a stream capture when the counts differ. */
+ap_dvm_status ap_dvm_step_slots(ap_dvm_handle* h, int nsteps, const int* steps_per_slot);
 /* Use a captured CUDA graph of k steps for ap_dvm_step (k = 0: direct launches). */
 ap_dvm_status ap_dvm_set_graph_steps(ap_dvm_handle* h, int k);
 /* Tile shape of the stencil kernels: 0 = 32x8, 1 = 32x4, 2 = 16x8, 3 = 8x8,

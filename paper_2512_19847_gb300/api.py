@@ -96,6 +96,7 @@ def lib():
         "ap_dvm_moments": (i32, [H, i32, vp, vp, vp, vp]),
         "ap_dvm_diagnostics": (i32, [H, i32, vp, ctypes.POINTER(f64)]),
         "ap_dvm_step": (i32, [H, i32]),
+        "ap_dvm_step_slots": (i32, [H, i32, ctypes.POINTER(i32)]),
         "ap_dvm_set_graph_steps": (i32, [H, i32]),
         "ap_dvm_set_tile": (i32, [H, i32]),
         "ap_dvm_get_tile": (i32, [H]),
@@ -341,3 +342,11 @@ class Batch(_Handle):
     @property
     def slots(self):
         return sorted(self._params)
+
+    def step_slots(self, nsteps: int, steps: dict):
+        """ap_dvm_step_slots: advance the solve in slot k by steps[k] of at most nsteps
+        steps (attached slots missing from steps advance by nsteps)."""
+        arr = (ctypes.c_int * self.capacity)(*([0] * self.capacity))
+        for k in self.slots:
+            arr[k] = int(steps.get(k, nsteps))
+        self._check(lib().ap_dvm_step_slots(self._h, int(nsteps), arr))

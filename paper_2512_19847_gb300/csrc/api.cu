@@ -39,21 +39,25 @@ struct Slot {
   size_t bytes = 0;
   InstDev dev{};                        // as carved: X = state buffer 0, Xnext = buffer 1
   CUtensorMap maps[2][APD_MAXS + 1];    // host copies of the stage-buffer tensor maps, per parity
+  int flip = 0;                         // the state is in buffer (handle parity) ^ flip
+  bool paused = false;                  // left out of the steps (ap_dvm_step_slots)
 };
 
 // The instance as the kernels of a step of the given parity see it: the state
-// is double-buffered (even steps read buffer 0 and close into buffer 1, odd
-// steps the reverse); stage 1 of a CK/ARS tableau is the state itself.
+// is double-buffered (a step reads buffer q = parity ^ flip and closes into
+// buffer q ^ 1; flip changes only while the slot sits out steps of
+// ap_dvm_step_slots); stage 1 of a CK/ARS tableau is the state itself.
 InstDev view(const Slot& s, int parity) {
   InstDev d = s.dev;
+  const int q = parity ^ s.flip;
   void* buf[2] = {s.dev.X, s.dev.Xnext};
-  d.X = buf[parity];
-  d.Xnext = buf[parity ^ 1];
+  d.X = buf[q];
+  d.Xnext = buf[q ^ 1];
   if (s.p.A_im[0] == 0.0) {
     d.Xs[1] = d.X;
     d.Dun = d.Du[1];
   }
-  d.tmap = reinterpret_cast<const char*>(s.dev.tmap) + (size_t)parity * sizeof(CUtensorMap) * (APD_MAXS + 1);
+  d.tmap = reinterpret_cast<const char*>(s.dev.tmap) + (size_t)q * sizeof(CUtensorMap) * (APD_MAXS + 1);
   return d;
 }
 
@@ -314,7 +318,7 @@ ap_dvm_status flush(ap_dvm_handle* h) {
   h->up_rows.assign(1, 0);
   h->up_cols.assign(1, 0);
   for (Slot& s : h->slots) {
-    if (!s.attached) continue;
+    if (!s.attached || s.paused) continue;
     if (s.p.nx < TX || s.p.ny < TY) return fail(h, AP_DVM_ERR_ARG, "grid %dx%d smaller than the tile %dx%d", s.p.nx, s.p.ny, TX, TY);
     InstDev& d = s.dev;
     d.tiles_x = (s.p.nx + TX - 1) / TX;   // ragged tiles at the high edges
@@ -632,6 +636,8 @@ ap_dvm_status ap_dvm_attach(ap_dvm_handle* h, int slot, const ap_dvm_params* p, 
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));   // the symbol and transform-table vectors are about to go out of scope
   for (void* xb : {d.X, d.Xnext}) CUDA_TRY(h, cudaMemsetAsync(xb, 0, (size_t)6 * p->nx * p->ny * (h->f32 ? 4 : 8), h->stream));
   if (d.dF) CUDA_TRY(h, cudaMemsetAsync(d.dF, 0, (size_t)6 * p->nx * p->ny * sizeof(float), h->stream));
+  s.flip = 0;
+  s.paused = false;
   s.attached = true;
   h->dirty = true;
   if (h->tile_auto) {
@@ -774,6 +780,44 @@ ap_dvm_status ap_dvm_step(ap_dvm_handle* h, int nsteps) {
     if (h->profile && h->ev_used > 2048 && (st = profile_collect(h))) return st;
   }
   return AP_DVM_OK;
+}
+
+ap_dvm_status ap_dvm_step_slots(ap_dvm_handle* h, int nsteps, const int* steps_per_slot) {
+  if (!h) return AP_DVM_ERR_ARG;
+  if (nsteps < 0 || !steps_per_slot) return fail(h, AP_DVM_ERR_ARG, "nsteps must be >= 0 and steps_per_slot given");
+  std::vector<int> ends;
+  for (int k = 0; k < h->capacity; ++k) {
+    if (!h->slots[k].attached) continue;
+    const int c = steps_per_slot[k];
+    if (c < 0 || c > nsteps) return fail(h, AP_DVM_ERR_ARG, "slot %d: %d steps, outside [0, %d]", k, c, nsteps);
+    ends.push_back(c);
+  }
+  std::sort(ends.begin(), ends.end());
+  ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
+  // segments between the step counts at which slots drop out: the slots that are done
+  // sit out the rest (left out of the work lists; their state stays where it is, so
+  // their buffer offset absorbs the parity the handle moves through)
+  ap_dvm_status st = AP_DVM_OK;
+  int t = 0;
+  for (int e : ends) {
+    if (e <= t) continue;
+    for (int k = 0; k < h->capacity; ++k) {
+      Slot& s = h->slots[k];
+      if (!s.attached) continue;
+      const bool p = steps_per_slot[k] <= t;
+      if (p != s.paused) { s.paused = p; h->dirty = true; }
+    }
+    const int par0 = h->parity;
+    st = ap_dvm_step(h, e - t);
+    const int moved = h->parity ^ par0;
+    for (Slot& s : h->slots)
+      if (s.attached && s.paused) s.flip ^= moved;
+    if (st) break;
+    t = e;
+  }
+  for (Slot& s : h->slots)
+    if (s.attached && s.paused) { s.paused = false; h->dirty = true; }
+  return st;
 }
 
 ap_dvm_status ap_dvm_profile_enable(ap_dvm_handle* h, int enable) {

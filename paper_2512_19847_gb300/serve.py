@@ -6,9 +6,10 @@ batch handle; each round it
 
   1. admits arrived requests in arrival order while a slot is free and the
      resident workspaces stay within the HBM budget,
-  2. advances every resident solve by the same number of IMEX steps (never
-     more than the fewest steps any of them still needs, and at most
-     `chunk`), all solves in each kernel launch, replayed from a CUDA graph,
+  2. advances every resident solve by up to `chunk` IMEX steps, each by no
+     more than it still needs (ap_dvm_step_slots: a solve that is done sits
+     out the round's remaining steps), all solves in each kernel launch,
+     replayed from a CUDA graph,
   3. retires the solves that are done: their state is copied to pinned host
      memory asynchronously, the slot and the workspace are released.
 
@@ -138,10 +139,11 @@ class Server:
             stats.max_resident = max(stats.max_resident, len(self.resident))
             stats.max_bytes = max(stats.max_bytes, int(self.bytes))
             if self.resident:
-                c = min(self.chunk, min(r[1] for r in self.resident.values()))
-                self.batch.step(c)
+                c = min(self.chunk, max(r[1] for r in self.resident.values()))
+                counts = {slot: min(c, r[1]) for slot, r in self.resident.items()}
+                self.batch.step_slots(c, counts)
                 for slot in list(self.resident):
-                    self.resident[slot][1] -= c
+                    self.resident[slot][1] -= counts[slot]
                     if self.resident[slot][1] == 0:
                         self._retire(slot)
             elif not self.inflight and pending:

@@ -44,6 +44,45 @@ def test_mix_equals_alone_bitwise(prec, tile):
         assert torch.equal(b.get_state(k), s.get_state()), k
 
 
+@pytest.mark.parametrize("prec,graph", [(api.FP64, 1), (api.FP32_DEV, 1), (api.FP32_DEV_TH, 0), (api.FP64, 2)])
+def test_step_slots_equals_alone(prec, graph):
+    """ap_dvm_step_slots: each solve advances by its own count (some sit out part of
+    the call, one all of it); over two such calls and a plain step every solve equals
+    the same solve run alone for its total number of steps, bit for bit."""
+    insts = [_inst(*m, prec) for m in MIX]
+    tmpl = insts[-1][0].copy()
+    b = api.Batch(tmpl, capacity=8)
+    b.set_graph_steps(graph)
+    for k, (prm, f) in enumerate(insts):
+        b.attach(k, prm)
+        b.set_equilibrium(*[torch.from_numpy(a).cuda() for a in f], slot=k)
+    b.set_tile(3)
+    b.step_slots(5, {0: 5, 1: 2, 2: 0, 3: 3, 4: 5})
+    b.step_slots(4, {0: 1, 1: 4, 2: 4, 3: 0, 4: 3})
+    b.step(1)
+    b.sync_status()
+    total = {0: 7, 1: 7, 2: 5, 3: 4, 4: 9}
+    for k, (prm, f) in enumerate(insts):
+        s = api.Solver(prm)
+        s.set_tile(3)
+        s.set_equilibrium(*[torch.from_numpy(a).cuda() for a in f])
+        s.step(total[k])
+        assert torch.equal(b.get_state(k), s.get_state()), k
+
+
+def test_step_slots_rejects_counts_outside_the_call():
+    prm, f = _inst(32, 1e-2, 1e-2, 1, api.FP64)
+    b = api.Batch(prm.copy(), capacity=2)
+    b.attach(0, prm)
+    b.set_equilibrium(*[torch.from_numpy(a).cuda() for a in f], slot=0)
+    before = b.get_state(0).clone()
+    for bad in (4, -1):
+        with pytest.raises(api.ApDvmError) as e:
+            b.step_slots(3, {0: bad})
+        assert e.value.status == 1
+    assert torch.equal(b.get_state(0), before)
+
+
 def test_mix_matches_oracle_fp64():
     insts = [_inst(*m, api.FP64) for m in MIX[:4]]
     b = api.Batch(insts[1][0].copy(), capacity=4)
