@@ -115,11 +115,11 @@ class Params:
     Ly: float = 2 * math.pi
     weno_eps: float = 1e-6
     alpha: float = 1.0            # LF dissipation of the alpha = 1 fluxes (Sec. 3.2)
-    theta_hist_sign: float = -1.0  # G4
+    theta_hist_sign: float = -1.0  # the theta-history sign (reading G4 above)
     # test-only: "consistent" replaces D_Delta by D_0.D_0, D_0^2:B(v) by D_0.(D_0.B(v))
     # and sets alpha = 0, so that the stage equations of Sec. 3.1 hold exactly.
     operators: str = "paper"
-    # G6 reading of the j = i dissipation partner: "explicit" (default) or the
+    # the j = i dissipation partner (reading G6 above): "explicit" (default) or the
     # rejected "lagged" u^(i-1) and "un" u^n readings (kept to pin their instability)
     partner: str = "explicit"
 
@@ -213,7 +213,8 @@ def div_c(w1, w2, p: Params):
 
 def vorticity(u1, u2, p: Params):
     """omega = D_0x u2 - D_0y u1, the central vorticity of the Sec. 4 figures and
-    Tables 1-2 (reading G11), with the scheme's central difference."""
+    Tables 1-2 (the paper does not define it; the central difference is the natural
+    discrete curl), with the scheme's central difference."""
     return dx_c(u2, p) - dy_c(u1, p)
 
 

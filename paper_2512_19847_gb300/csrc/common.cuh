@@ -33,7 +33,7 @@ struct Coef {
   T kappa[APD_MAXS + 1];                  // 2 eps^2 / (dt a_ii)^2
   T aex[APD_MAXS + 1][APD_MAXS + 1];      // atilde_ij
   T aim[APD_MAXS + 1][APD_MAXS + 1];      // a_ij
-  T wp[APD_MAXS + 1][APD_MAXS + 1];       // (atilde_ij - a_ij) / a_ii: dissipation-partner weights (reading G6)
+  T wp[APD_MAXS + 1][APD_MAXS + 1];       // (atilde_ij - a_ij) / a_ii: weights of the explicit-weight dissipation partner
   // closed forms of steps 1 and 4 with the division folded into the coefficients:
   //   v^(i) = r_n v^n + sum_j rv_e E^(j) + sum_j rv_v v^(j),
   //   q^(i) = r_n q^n + sum_{j<=i} rq_d D0.v^(j) + sum_{j<i} rq_q q^(j)
@@ -45,7 +45,7 @@ struct Coef {
   T c_du[APD_MAXS + 1][APD_MAXS + 1];     // a_ij / (dt a_ii^2), j < i
   T c_dun[APD_MAXS + 1];                  // 1 / (dt a_ii)
   T c_db[APD_MAXS + 1][APD_MAXS + 1];     // a_ij / a_ii, j <= i
-  T c_lth[APD_MAXS + 1][APD_MAXS + 1];    // -a_ij / a_ii, j < i (reading G4)
+  T c_lth[APD_MAXS + 1][APD_MAXS + 1];    // -a_ij / a_ii, j < i: theta-history weights (minus sign)
 };
 
 // Per-instance description, resident in device memory.  Plane pointers are

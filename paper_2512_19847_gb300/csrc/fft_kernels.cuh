@@ -6,7 +6,7 @@
 //   k_fft_rows_fwd : real row DFTs of R (two rows packed as one complex row),
 //                    written as the half spectrum S[y][0..nx/2];
 //   k_fft_cols     : per spectral column, DFT along y, division by the
-//                    symbol (mode k = 0 set to mean(theta^n), reading G5),
+//                    symbol (mode k = 0 set to mean(theta^n): every other term of R has zero mean),
 //                    inverse DFT along y, scaled by 1/(nx ny);
 //   k_fft_rows_inv : inverse real row DFTs into theta^(i).
 // Power-of-two lengths: radix-2^3 passes in shared memory, decimation in time

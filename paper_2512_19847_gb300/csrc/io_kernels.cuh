@@ -5,7 +5,7 @@
 // f = dF/(rho0 A) and the six rescaled moments of Sec. 2.1,
 //   sum f = 2 eps theta, sum c f = u, sum (c1^2 - 1/2) f = -eps v1,
 //   sum c1 c2 f = eps v2, sum c1 (c2^2 - 1/4) f = eps^2 q,
-// (sign of v1: reading G1).  Opposite velocities c_{k+3} = -c_k make even
+// (v1 = sum (c2^2 - 1/2) f: the sign with which the moment system of Sec. 2.1 holds).  Opposite velocities c_{k+3} = -c_k make even
 // and odd pair sums s_k = f_k + f_{k+3}, d_k = f_k - f_{k+3} the natural
 // variables; both directions of the map are evaluated in FP64.
 #pragma once

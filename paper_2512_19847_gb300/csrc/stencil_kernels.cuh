@@ -406,7 +406,7 @@ __device__ __forceinline__ float w5_rec_f32(float a, float b, float c, float d, 
 }
 
 // Values of the LF partner U at a staged point: one plane, or the weighted sum of
-// the staged u planes of earlier stages (the dissipation partner of reading G6),
+// the staged u planes of earlier stages (the explicit-weight dissipation partner),
 // summed in stage order.
 struct PlaneOne {
   const float* p;
@@ -802,8 +802,8 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp,
     // cells beyond the grid (ragged edge tile) read cell 0 and store nothing
     const bool own = t.x0 + tx < nx && t.y0 + ty < I.ny;
     const size_t o = own ? (size_t)(t.y0 + ty) * nx + (t.x0 + tx) : 0;
-    // right-hand side of the Helmholtz equation (Algorithm 1, step 2; theta-history sign per
-    // reading G4), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii
+    // right-hand side of the Helmholtz equation (Algorithm 1, step 2; the theta-history term
+    // with a minus sign, the sign the stage equations of Sec. 3.1 give), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii
     // precomputed.  Its pointwise inputs: the FP32 form loads them before the shared-memory
     // pass so that their latency overlaps it; FP64 loads them where they are used (fewer
     // registers for the FP64-pipe-bound form).
@@ -889,7 +889,7 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const Ba
     const T* sv2 = s + 2 * PL;
     const int nx = I.nx;
     const size_t pl = (size_t)nx * I.ny;
-    // dissipation partner of D_LF . B(v^(i)) (reading G6): (1/a_ii) sum_{j<i} (atilde_ij - a_ij) u^(j)
+    // dissipation partner of D_LF . B(v^(i)), the explicit-weight predictor (1/a_ii) sum_{j<i} (atilde_ij - a_ij) u^(j)
     const Coef<T>& K = coef<T>(I);
     if constexpr (G::RUNS) {
       // FP32 WENO5: the register runs form the partner at each point they load

@@ -35,7 +35,8 @@ struct StepKernels {
 };
 
 // Planes k_update stages at its largest stage: theta, v1, v2 and u1, u2 of every
-// earlier stage entering the dissipation partner (reading G6).
+// earlier stage entering the dissipation partner (the explicit-weight predictor
+// (1/a_ii) sum_{j<i} (atilde_ij - a_ij) u^(j)).
 inline int update_planes_max(const ap_dvm_params& t) {
   int best = 0;
   for (int i = 1; i <= t.s; ++i) {
@@ -136,7 +137,7 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
       void* a[] = {&bp, &j, &need, &weno_eps};
       if ((st = launch(K.ks.k_explicit, K.g_explicit, blk, K.ks.smem_explicit, a, KK_EXPLICIT))) return st;
     }
-    double sign = -1.0;                                    // reading G4
+    double sign = -1.0;   // theta-history term with a minus sign (the stage equations of Sec. 3.1)
     int first = (i == (type_a ? 1 : 2)) ? 1 : 0;           // the first right-hand side also sums theta^n
     {
       void* a[] = {&bp, &i, &sign, &first};

@@ -3,7 +3,7 @@
 * ``shear_thick`` - double shear layer of Sec. 4.1, 1/rho = 15/pi, up to t = 6;
 * ``shear_thin``  - thin double shear layer of Sec. 4.2, 1/rho = 50/pi, up to t = 9.5;
 * ``kelvin_helmholtz`` - the layer u = (cos y, 0.03 sin(x/2)) of Sec. 4.3 on
-  [0, 4pi)^2 up to t = 45 (tau = 0.05, reading G12).
+  [0, 4pi)^2 up to t = 45 (tau = 0.05, the value of the figure caption; the text says 0).
 
 Each run records, every ``record_every`` steps, the diagnostics the paper plots
 (Figs. 2-3: max |D_0 . u| over time) plus the L2 divergence and the enstrophy,

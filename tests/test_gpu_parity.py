@@ -194,7 +194,7 @@ def test_domain_lengths(Lx, Ly):
 
 
 def test_kelvin_helmholtz_domain():
-    """Kelvin-Helmholtz data of Sec. 4.3 on [0, 4pi)^2 (tau = 0.05, reading G12), 5 steps
+    """Kelvin-Helmholtz data of Sec. 4.3 on [0, 4pi)^2 (tau = 0.05, the value of the figure caption; the text says 0), 5 steps
     (the layer is unstable, so round-off is compared over a short horizon)."""
     n = 128
     u1, u2, pr = W.kelvin_helmholtz(n)
@@ -303,7 +303,7 @@ def test_fp32_form_every_tile_shape(tile):
 def test_four_stages_every_tile_shape(tile, scheme):
     """s = 4 (the largest stage count the library takes; the ARS-type pair
     tableaux.ars4): the stage sums of Algorithm 1 over three earlier stages, the
-    dissipation partner over three earlier stages (reading G6) and the update's
+    dissipation partner (the explicit-weight predictor) over three earlier stages and the update's
     largest staged plane set, on every tile shape, over 3 steps, on a grid with
     ragged edge tiles in both directions."""
     nx, ny = 72, 40

@@ -162,7 +162,7 @@ class Brute:
                 r = -kappa * thn[j][i] + divu(S[1], i, j) / (dt * a)
                 for jj in range(1, st):
                     r += A[st - 1][jj - 1] * divu(S[jj], i, j) / (dt * a * a)
-                    r -= A[st - 1][jj - 1] / a * lap(S[jj]["th"], i, j)       # reading G4
+                    r -= A[st - 1][jj - 1] / a * lap(S[jj]["th"], i, j)       # theta-history term with a minus sign
                 for jj in range(1, st + 1):
                     r -= A[st - 1][jj - 1] / a * ddB(S[jj] if jj < st else cur, i, j)
                 return r
@@ -170,7 +170,7 @@ class Brute:
             R = self.field(R_at)
             th = self.helmholtz(R, kappa, mean_thn)
             cur["th"] = th
-            # dissipation partner of D_LF.B(v^(st)) (reading G6): explicit-weight predictor
+            # dissipation partner of D_LF.B(v^(st)) (j = i): explicit-weight predictor
             P1 = self.field(lambda i, j: sum((Ae[st - 1][k - 1] - A[st - 1][k - 1]) * S[k]["u1"][j][i]
                                              for k in range(1, st)) / a)
             P2 = self.field(lambda i, j: sum((Ae[st - 1][k - 1] - A[st - 1][k - 1]) * S[k]["u2"][j][i]

@@ -67,7 +67,7 @@ def test_population_map_roundtrip(eps):
 
 
 def test_population_moments_by_brute_force():
-    """The rescaled moments of Sec. 2.1 (with the G1 sign of v1) by scalar loops."""
+    """The rescaled moments of Sec. 2.1 (v1 = sum (c2^2 - 1/2) F) by scalar loops."""
     rng = np.random.default_rng(1)
     eps, rho0, amp = 0.03, 1.0, 1.0
     dF = rng.standard_normal((6, 3, 3)) * 1e-3
@@ -82,7 +82,7 @@ def test_population_moments_by_brute_force():
                 s0 += f[k]
                 s1 += ck1 * f[k]
                 s2 += ck2 * f[k]
-                s3 += (ck2 * ck2 - 0.5) * f[k]          # G1: v1 uses (c2^2 - 1/2)
+                s3 += (ck2 * ck2 - 0.5) * f[k]          # v1 uses (c2^2 - 1/2)
                 s4 += ck1 * ck2 * f[k]
                 s5 += ck1 * (ck2 * ck2 - 0.25) * f[k]
             expect = [s1, s2, s0 / (2 * eps), s3 / eps, s4 / eps, s5 / eps ** 2]
@@ -101,7 +101,7 @@ def test_equilibrium_moments():
     assert np.allclose(M[0], rho, atol=1e-14)
     assert np.allclose(M[1], m1, atol=1e-14)
     assert np.allclose(M[2], m2, atol=1e-14)
-    # sum (c1^2-1/2) F^eq = (m1^2 - m2^2)/2, i.e. v1^eq = (m2^2 - m1^2)/2 = F(u)_1 under G1
+    # sum (c1^2-1/2) F^eq = (m1^2 - m2^2)/2, i.e. v1^eq = (m2^2 - m1^2)/2 = F(u)_1 with that sign of v1
     assert np.allclose(M[3], 0.5 * (m1 ** 2 - m2 ** 2), atol=1e-14)
     assert np.allclose(M[4], m1 * m2, atol=1e-14)
     assert np.allclose(M[5], 0.0, atol=1e-14)
@@ -112,8 +112,8 @@ def test_equilibrium_moments():
 def test_outputs_are_the_moments_of_the_populations():
     """outputs() against the definitions of Sec. 2.1 evaluated on the populations
     F_i = rho0/6 + dF_i by scalar loops: the density is sum_i F_i, the momentum
-    sum_i c_i F_i = rho0 A u (A the storage amplitude, G10), and
-    theta = (sum_i F_i - rho0)/2 rescaled by rho0 A eps (G10); the pressure is
+    sum_i c_i F_i = rho0 A u (A the storage amplitude of the population view), and
+    theta = (sum_i F_i - rho0)/2 rescaled by rho0 A eps; the pressure is
     p = theta - |u|^2/2 with that theta and that u."""
     X = W.random_moment_state(5, 4, seed=5, amp=0.7)
     eps, rho0, amp = 0.02, 1.3, 2e-3
@@ -167,7 +167,7 @@ def _spec_d(f, axis, L=2 * math.pi):
 
 
 def test_moment_system_follows_from_the_dvm():
-    """Pins G1, G2, G3, the moment map (G10) and F(u): the time derivative of
+    """Pins the sign of v1, the divergence in the q equation, the relaxation sign, the moment map and F(u): the time derivative of
     the populations under the scaled DVM dF/dt + (1/eps) c.grad F =
     -(F - F^eq)/(eps^2 tau), mapped to moments, equals the right-hand side of
     the closed moment system of Sec. 2.1 under those readings."""
@@ -199,7 +199,7 @@ def test_moment_system_follows_from_the_dvm():
     scale = np.max(np.abs(rhs), axis=(1, 2))
     err = np.max(np.abs(dXdt - rhs), axis=(1, 2))
     assert np.all(err <= 1e-10 * scale), (err, scale)
-    # the printed q equation (d_x v1 + d_x v2) does not hold (G2)
+    # the printed q equation (d_x v1 + d_x v2) does not hold
     printed_q = -(Dx(v1) + Dx(v2)) / (2 * eps * eps) - r * q
     assert np.max(np.abs(dXdt[5] - printed_q)) > 1e-3 * scale[5]
 
@@ -225,7 +225,7 @@ def test_tableau_properties(name):
                 assert abs(w @ cc - 0.5) < 1e-14           # second-order and coupling conditions
     if name == "ars4":
         assert s == 4 and np.all(A_im[:, 0] == 0.0)        # ARS: zero first implicit column
-        # every dissipation-partner weight atilde_ij - a_ij (j < i, reading G6) is nonzero
+        # every dissipation-partner weight atilde_ij - a_ij (j < i, the explicit-weight predictor) is nonzero
         assert all(A_ex[i, j] - A_im[i, j] != 0.0 for i in range(1, s) for j in range(i))
 
 
@@ -238,7 +238,7 @@ def test_ars4_data_matches_the_package_tableau():
     assert np.array_equal(A_ex, np.array(T_ex)) and np.array_equal(A_im, np.array(T_im))
 
 
-# ---------------------------------------------------------------- stencils (Sec. 3.2, G7)
+# ---------------------------------------------------------------- stencils (Sec. 3.2, fourth-order versions)
 
 def test_central_difference_orders():
     errs = {2: [], 4: []}
@@ -286,7 +286,7 @@ def test_d0sqB_is_div_div_B():
     assert abs(math.log2(errs[0] / errs[1]) - 2) < 0.15
 
 
-# ---------------------------------------------------------------- WENO (G7, G8)
+# ---------------------------------------------------------------- WENO (Jiang-Shu weights)
 
 def test_weno5_linear_weights_limit_is_upwind5():
     rng = np.random.default_rng(5)
@@ -350,7 +350,7 @@ def test_helmholtz_against_dense_solve(scheme, n):
     th_dense = np.linalg.solve(M, R.ravel()).reshape(n, n)
     th = O.helmholtz_solve(R, kappa, float(np.mean(th_dense)), p)
     assert np.max(np.abs(th - th_dense)) <= 1e-12 * np.max(np.abs(th_dense))
-    # kappa = 0: zero-mean right-hand side, mean fixed by the G5 rule
+    # kappa = 0: zero-mean right-hand side, mean fixed to mean(theta^n)
     R0 = R - R.mean()
     th0 = O.helmholtz_solve(R0, 0.0, 0.25, p)
     res = O.laplacian(th0, p) - R0
@@ -405,7 +405,7 @@ def test_g4_sign_from_the_stage_equations():
     """With mutually consistent operators (D_Delta := D_0.D_0, D_0^2:B := D_0.(D_0.B),
     alpha = 0) Algorithm 1 must satisfy the theta stage equation of Sec. 3.1:
     theta^(i) = theta^n - dt/(2 eps^2) [sum_{j<i} a_ij D0.u^(j) + a_ii D0.u^(i)].
-    Only the minus sign of the theta-history term (reading G4) does."""
+    Only the minus sign of the theta-history term does."""
     n = 16
     X = W.random_moment_state(n, n, seed=41, amp=0.3)
     res = {}
