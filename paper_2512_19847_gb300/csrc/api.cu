@@ -76,6 +76,7 @@ struct ap_dvm_handle {
   InstDev* d_inst[2] = {nullptr, nullptr};
   int* d_tile_start = nullptr;
   int* d_row_start = nullptr;
+  int* d_rhs_start = nullptr;
   int* d_col_start = nullptr;
   int* d_counts = nullptr;
   double2* d_tw = nullptr;
@@ -88,8 +89,8 @@ struct ap_dvm_handle {
   int n_active = 0;
   // upload staging (kept alive across async copies)
   std::vector<InstDev> up_inst[2];
-  std::vector<int> up_tiles, up_rows, up_cols;
-  int up_counts[4] = {0, 0, 0, 0};
+  std::vector<int> up_tiles, up_rows, up_cols, up_rhs;
+  int up_counts[5] = {0, 0, 0, 0, 0};
   // kernels
   StencilSet ks{};
   MiscSet km{};
@@ -223,7 +224,8 @@ size_t batch_bytes(int capacity, int nmax) {
   take(sizeof(int) * (capacity + 1));
   take(sizeof(int) * (capacity + 1));
   take(sizeof(int) * (capacity + 1));
-  take(sizeof(int) * 4);
+  take(sizeof(int) * (capacity + 1));
+  take(sizeof(int) * 5);
   take(sizeof(double2) * (nmax / 2));
   take(sizeof(float2) * (nmax / 2));
   take(sizeof(unsigned) * 4);
@@ -284,7 +286,7 @@ ap_dvm_status prepare_kernels(ap_dvm_handle* h) {
   const int thr = h->ks.tx * h->ks.ty;
   ap_dvm_status st;
   if ((st = occupancy_grid(h, h->ks.k_explicit, thr, h->ks.smem_explicit, &h->grid_explicit))) return st;
-  if ((st = occupancy_grid(h, h->ks.k_rhs, thr, h->ks.smem_rhs, &h->grid_rhs))) return st;
+  if ((st = occupancy_grid(h, h->ks.k_rhs, h->ks.rhs_threads, 0, &h->grid_rhs))) return st;
   h->smem_update = update_smem(h->ks, h->tmpl);
   if ((st = occupancy_grid(h, h->ks.k_update, thr, h->smem_update, &h->grid_update))) return st;
   if ((st = occupancy_grid(h, h->km.k_finish, thr, 0, &h->grid_finish))) return st;
@@ -316,6 +318,7 @@ ap_dvm_status flush(ap_dvm_handle* h) {
   h->up_inst[1].clear();
   h->up_tiles.assign(1, 0);
   h->up_rows.assign(1, 0);
+  h->up_rhs.assign(1, 0);
   h->up_cols.assign(1, 0);
   for (Slot& s : h->slots) {
     if (!s.attached || s.paused) continue;
@@ -339,6 +342,7 @@ ap_dvm_status flush(ap_dvm_handle* h) {
     }
     h->up_tiles.push_back(h->up_tiles.back() + d.tiles_x * d.tiles_y);
     h->up_rows.push_back(h->up_rows.back() + (pairs + d.row_pairs - 1) / d.row_pairs);
+    h->up_rhs.push_back(h->up_rhs.back() + rhs_items(s.p.nx, s.p.ny));
     h->up_cols.push_back(h->up_cols.back() + (s.p.nx / 2 + 1 + d.col_group - 1) / d.col_group);
   }
   const int n = (int)h->up_inst[0].size();
@@ -347,15 +351,17 @@ ap_dvm_status flush(ap_dvm_handle* h) {
   h->up_counts[1] = h->up_rows.back();
   h->up_counts[2] = h->up_cols.back();
   h->up_counts[3] = n;
+  h->up_counts[4] = h->up_rhs.back();
   if (n > 0) {
     for (int par = 0; par < 2; ++par)
       CUDA_TRY(h, cudaMemcpyAsync(h->d_inst[par], h->up_inst[par].data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
                                   h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_tile_start, h->up_tiles.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_row_start, h->up_rows.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_rhs_start, h->up_rhs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_col_start, h->up_cols.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
   }
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_counts, h->up_counts, sizeof(int) * 4, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_counts, h->up_counts, sizeof(int) * 5, cudaMemcpyHostToDevice, h->stream));
   h->dirty = false;
   return AP_DVM_OK;
 }
@@ -520,7 +526,8 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   h->d_tile_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
   h->d_row_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
   h->d_col_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
-  h->d_counts = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  h->d_rhs_start = reinterpret_cast<int*>(take(sizeof(int) * (capacity + 1)));
+  h->d_counts = reinterpret_cast<int*>(take(sizeof(int) * 5));
   h->d_tw = reinterpret_cast<double2*>(take(sizeof(double2) * (h->nmax / 2)));
   h->d_tw32 = reinterpret_cast<float2*>(take(sizeof(float2) * (h->nmax / 2)));
   h->d_err = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * 4));
@@ -540,6 +547,7 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   hb.tile_start = h->d_tile_start;
   hb.row_start = h->d_row_start;
   hb.col_start = h->d_col_start;
+  hb.rhs_start = h->d_rhs_start;
   hb.counts = h->d_counts;
   hb.tw = h->d_tw;
   hb.tw32 = h->d_tw32;
@@ -556,7 +564,7 @@ ap_dvm_status ap_dvm_batch_create(const ap_dvm_params* tmpl, int capacity, void*
   for (int par = 0; par < 2; ++par)
     CUDA_TRY(h, cudaMemcpyAsync(h->d_batch[par], &h->hb[par], sizeof(BatchDev), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned) * 4, h->stream));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_counts, 0, sizeof(int) * 4, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_counts, 0, sizeof(int) * 5, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->slots.resize(capacity);
   h->dirty = true;

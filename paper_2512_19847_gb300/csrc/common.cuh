@@ -92,7 +92,7 @@ struct InstDev {
   float* lamx32;                // FP32 form: the same tables rounded once (null in the FP64 form)
   float* lamy32;
   float hscale32;               // FP32 form: 1/(nx ny) rounded once
-  double* th_part;              // per-tile partial sums of theta^n (ceil(nx/8) * ceil(ny/4) entries)
+  double* th_part;              // partial sums of theta^n, one per k_rhs item (rhs_items)
   float* dF;                    // FP32 form: deviation populations (6 planes)
   unsigned mr_plan[2];          // axes whose n is not a power of two but factors into 2, 3, 5, 7 (x, y):
                                 // the mixed-radix passes' radices, 4 bits each, first pass lowest
@@ -114,7 +114,8 @@ struct BatchDev {
   int* tile_start;       // [n+1]
   int* row_start;        // [n+1]
   int* col_start;        // [n+1]
-  int* counts;           // [0] tiles, [1] row items, [2] column items, [3] instances
+  int* rhs_start;        // [n+1]
+  int* counts;           // [0] tiles, [1] row items, [2] column items, [3] instances, [4] k_rhs items
   double2* tw;           // twiddles exp(-2 pi i k / nmax), k < nmax/2
   float2* tw32;          // the same, rounded once to FP32 (FP32 form)
   int lnmax;             // log2 of the largest transform length
@@ -126,6 +127,14 @@ struct BatchDev {
   unsigned m_ex[APD_MAXS + 1], m_im[APD_MAXS + 1], m_wp[APD_MAXS + 1];
   unsigned* err;         // device error flags (bit 0: non-finite state, bit 1: a bounded wait expired)
 };
+
+// Work items of the Helmholtz right-hand side kernel (k_rhs): a row pair times
+// RHS_WARPS * RHS_U segments of RHS_SEG columns, RHS_U per warp.
+#ifndef APD_RHS_U
+#define APD_RHS_U 1
+#endif
+constexpr int RHS_WARPS = 4, RHS_SEG = 28, RHS_U = APD_RHS_U, RHS_COLS = RHS_WARPS * RHS_SEG * RHS_U;
+__host__ __device__ constexpr int rhs_items(int nx, int ny) { return ((ny + 1) / 2) * ((nx + RHS_COLS - 1) / RHS_COLS); }
 
 // Instance owning work item `item`: the last k with start[k] <= item.
 __device__ __forceinline__ int find_inst(const int* __restrict__ start, int n, int item) {
@@ -174,6 +183,24 @@ __device__ __forceinline__ T cdiff2(const T* f, int st, T inv_h2) {
   if (SCHEME == LF1_C2) return (f[st] - T(2) * f[0] + f[-st]) * inv_h2;
   return (-f[2 * st] + T(16) * f[st] - T(30) * f[0] + T(16) * f[-st] - f[-2 * st]) * (inv_h2 * T(1.0 / 12.0));
 }
+
+// The same two differences from the values at offsets -2 .. 2 along a line, without
+// their scale (fm2 and fp2 unused by the second-order scheme): the first difference is
+// d1_scale(inv_h) * d1_sum(...), the second d2_scale(inv_h) * d2_sum(...).
+template <typename T, int SCHEME>
+__device__ __forceinline__ T d1_sum(T fm2, T fm1, T fp1, T fp2) {
+  if (SCHEME == LF1_C2) return fp1 - fm1;
+  return T(8) * (fp1 - fm1) - (fp2 - fm2);
+}
+template <typename T, int SCHEME>
+__device__ __forceinline__ T d2_sum(T fm2, T fm1, T f0, T fp1, T fp2) {
+  if (SCHEME == LF1_C2) return (fp1 + fm1) - T(2) * f0;
+  return T(16) * (fp1 + fm1) - T(30) * f0 - (fp2 + fm2);
+}
+template <typename T, int SCHEME>
+__device__ __forceinline__ T d1_scale(T inv_h) { return SCHEME == LF1_C2 ? T(0.5) * inv_h : inv_h * T(1.0 / 12.0); }
+template <typename T, int SCHEME>
+__device__ __forceinline__ T d2_scale(T inv_h) { return SCHEME == LF1_C2 ? inv_h * inv_h : inv_h * inv_h * T(1.0 / 12.0); }
 
 // FP32 <-> FP64 conversions on the integer pipe.  On this GPU the conversion
 // instructions issue on the FP64 pipe (2 per clock per SM); these rebuild the

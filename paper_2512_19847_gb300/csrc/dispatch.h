@@ -14,7 +14,8 @@ struct StencilSet {
   const void* k_explicit;
   const void* k_rhs;
   const void* k_update;
-  size_t smem_explicit, smem_rhs;
+  size_t smem_explicit;
+  int rhs_threads;                     // k_rhs: threads per block (no dynamic shared memory)
   size_t plane_bytes, update_fixed;   // k_update: update_fixed + nbuf * (planes staged) * plane_bytes
   int nbuf;                            // staged plane buffers of k_update (1 or 2)
   int tx, ty;

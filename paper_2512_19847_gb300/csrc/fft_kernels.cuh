@@ -273,13 +273,21 @@ __device__ __forceinline__ void bluestein_conv(typename Cplx<T>::type* x, int lm
   fft_dit<T>(x, lm, ntr, tw, lnmax, true, tid, nthr);
 }
 
-// mean(theta^n) of instance I from its per-tile partial sums, in a fixed order,
-// into *mean (shared); every thread of the block calls it; red holds one value
-// per warp of the block.
-__device__ __forceinline__ void theta_mean(const InstDev& I, double* red, double* mean, int tid, int nthr) {
-  const int nt = I.tiles_x * I.tiles_y;
-  double acc = 0.0;
-  for (int k = tid; k < nt; k += nthr) acc += I.th_part[k];
+// mean(theta^n) of instance I from its nt partial sums (one per item of the first
+// stage's right-hand side kernel), in a fixed order, into *mean (shared); every thread of the
+// block calls it; red holds one value per warp of the block.
+__device__ __forceinline__ void theta_mean(const InstDev& I, int nt, double* red, double* mean, int tid, int nthr) {
+  // four independent partial sums per thread (their loads in flight together)
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = tid;
+  for (; k + 3 * nthr < nt; k += 4 * nthr) {
+    a0 += I.th_part[k];
+    a1 += I.th_part[k + nthr];
+    a2 += I.th_part[k + 2 * nthr];
+    a3 += I.th_part[k + 3 * nthr];
+  }
+  for (; k < nt; k += nthr) a0 += I.th_part[k];
+  double acc = (a0 + a1) + (a2 + a3);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((tid & 31) == 0) red[tid >> 5] = acc;
   __syncthreads();
@@ -365,7 +373,7 @@ __global__ void __launch_bounds__(cols_threads<T>(), sizeof(T) == 4 ? 1 : 2) k_f
     const int G = I.col_group, lg = __ffs(G) - 1;
     const int col0 = (it - b.col_start[k_inst]) * G;
     const int ntr = min(G, nh - col0);
-    if (col0 == 0) theta_mean(I, red, &s_mean, tid, nthr);
+    if (col0 == 0) theta_mean(I, b.rhs_start[k_inst + 1] - b.rhs_start[k_inst], red, &s_mean, tid, nthr);
     C* S = reinterpret_cast<C*>(I.S);
 #pragma unroll 4
     for (int e = tid; e < (n << lg); e += nthr) {
@@ -659,7 +667,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols_bs(con
     const int n = I.ny, ln = I.lny, m = 1 << ln, ss = I.sstride, nh = (I.nx >> 1) + 1;
     const int col0 = (it - b.col_start[k_inst]) * I.col_group;
     const int ntr = min(I.col_group, nh - col0);
-    if (col0 == 0) theta_mean(I, red, &s_mean, tid, nthr);
+    if (col0 == 0) theta_mean(I, b.rhs_start[k_inst + 1] - b.rhs_start[k_inst], red, &s_mean, tid, nthr);
     C* S = reinterpret_cast<C*>(I.S);
     if (I.mr_npass[1]) {
       const C* tw = reinterpret_cast<const C*>(I.mr_tw[1]);

@@ -31,7 +31,7 @@ void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Layout of the scratch: batch tables, then the instance's planes.
 struct Layout {
-  size_t batch, inst, tile_start, row_start, col_start, counts, tw, err, ws;
+  size_t batch, inst, tile_start, row_start, col_start, rhs_start, counts, tw, err, ws;
   size_t total;
 };
 
@@ -44,7 +44,8 @@ Layout layout(const ap_dvm_params& p, int nmax) {
   L.tile_start = take(2 * sizeof(int));
   L.row_start = take(2 * sizeof(int));
   L.col_start = take(2 * sizeof(int));
-  L.counts = take(4 * sizeof(int));
+  L.rhs_start = take(2 * sizeof(int));
+  L.counts = take(5 * sizeof(int));
   L.tw = take(sizeof(double2) * (nmax / 2));
   L.err = take(4 * sizeof(unsigned));
   L.ws = take(carve_instance(p, nullptr, nullptr));
@@ -106,7 +107,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   const int thr = ks.tx * ks.ty;
   int g_exp = 0, g_rhs = 0, g_upd = 0, g_fin = 0, g1 = 0, g2 = 0, g3 = 0;
   NA_TRY(grid_of(ks.k_explicit, thr, ks.smem_explicit, sms, &g_exp));
-  NA_TRY(grid_of(ks.k_rhs, thr, ks.smem_rhs, sms, &g_rhs));
+  NA_TRY(grid_of(ks.k_rhs, ks.rhs_threads, 0, sms, &g_rhs));
   const size_t smem_upd = update_smem(ks, *p);
   NA_TRY(grid_of(ks.k_update, thr, smem_upd, sms, &g_upd));
   NA_TRY(grid_of(km.k_finish, thr, 0, sms, &g_fin));
@@ -131,6 +132,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   B.tile_start = reinterpret_cast<int*>(base + L.tile_start);
   B.row_start = reinterpret_cast<int*>(base + L.row_start);
   B.col_start = reinterpret_cast<int*>(base + L.col_start);
+  B.rhs_start = reinterpret_cast<int*>(base + L.rhs_start);
   B.counts = reinterpret_cast<int*>(base + L.counts);
   B.tw = reinterpret_cast<double2*>(base + L.tw);
   B.lnmax = ilog2(nmax);
@@ -140,7 +142,9 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   const int ntiles = I.tiles_x * I.tiles_y;
   const int nrows = (p->ny / 2 + I.row_pairs - 1) / I.row_pairs;
   const int ncols = (p->nx / 2 + 1 + I.col_group - 1) / I.col_group;
-  const int ts[2] = {0, ntiles}, rs[2] = {0, nrows}, cs[2] = {0, ncols}, counts[4] = {ntiles, nrows, ncols, 1};
+  const int nrhs = rhs_items(p->nx, p->ny);
+  const int ts[2] = {0, ntiles}, rs[2] = {0, nrows}, cs[2] = {0, ncols}, hs[2] = {0, nrhs};
+  const int counts[5] = {ntiles, nrows, ncols, 1, nrhs};
   double2 tw[64];                                   // nmax/2 <= 64 for grids of at most 128 cells a side
   double lx[65], ly[128];
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -156,6 +160,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   NA_TRY(cudaMemcpyAsync(B.tile_start, ts, sizeof(ts), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(B.row_start, rs, sizeof(rs), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(B.col_start, cs, sizeof(cs), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(B.rhs_start, hs, sizeof(hs), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(B.counts, counts, sizeof(counts), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(B.tw, tw, sizeof(double2) * (nmax / 2), cudaMemcpyHostToDevice, stream));
   NA_TRY(cudaMemcpyAsync(I.lamx, lx, sizeof(double) * (p->nx / 2 + 1), cudaMemcpyHostToDevice, stream));

@@ -5,7 +5,7 @@
 //     the derived operators of stage j that later stages reuse
 //       D_0 . u^(j), D_Delta theta^(j), D_LF . B(v^(j)) (partner u^(j)) + D_0 theta^(j),
 //     and step 1 of stage j+1: the closed-form v^(j+1), once per cell.
-//   k_rhs(i):  the right-hand side R_i of the Helmholtz equation (step 2).
+//   k_rhs(i):  the right-hand side R_i of the Helmholtz equation (step 2), by rows.
 //   k_update(i): step 3 (u^(i)) and step 4 (closed-form q^(i)); for the last stage
 //     with close_step set, also the close of the step (GSA: X^{n+1} = X^(s); the
 //     FP32 forms pack the populations and sum the next step's moments), written
@@ -59,7 +59,6 @@ struct Geo {
   // shared memory besides the staged planes, and its element count
   static constexpr int EXPLICIT_EXTRA = 3 * SPLIT_PER_PAIR + 3 * NX + 3 * NY;
   static constexpr int UPDATE_EXTRA = (RUNS ? 0 : 2 * PL) + 2 * SPLIT_U_PER_PAIR + 2 * NX + 2 * NY;
-  static constexpr int RHS_EXTRA = TY * (TX + 2 * CH) + 64;     // d_y v2 rows, block-sum scratch
 };
 
 // The planes a kernel stages, packed 6 bits each (buffer << 3 | plane) so the
@@ -583,19 +582,6 @@ __device__ __forceinline__ void both_axes(const T* const* gx, const T* const* ux
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T block_sum(T v, T* red, int tid, int nthr) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((tid & 31) == 0) red[tid >> 5] = v;
-  __syncthreads();
-  T r = T(0);
-  if (tid == 0) {
-    for (int w = 0; w < (nthr + 31) / 32; ++w) r += red[w];
-  }
-  __syncthreads();
-  return r;
-}
-
 // Planes staged by k_update of stage i: theta, v1, v2 of X^(i), then u1, u2 of
 // every earlier stage that enters the dissipation partner.
 __device__ __forceinline__ PlaneList update_planes(const BatchDev& b, int i) {
@@ -617,7 +603,6 @@ struct StencilSmem {
   using G = Geo<T, SCHEME, TX, TY>;
   static constexpr size_t plane_bytes = sizeof(T) * G::PL;
   static constexpr size_t explicit_bytes = 128 + sizeof(T) * (2 * 6 * G::PL + G::EXPLICIT_EXTRA);
-  static constexpr size_t rhs_bytes = 128 + sizeof(T) * (2 * 2 * G::PL) + sizeof(double) * G::RHS_EXTRA;
   static constexpr size_t update_fixed_bytes = 128 + sizeof(T) * G::UPDATE_EXTRA;   // + NBUF_U * np * plane_bytes
 };
 
@@ -778,89 +763,162 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const 
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, int SCHEME, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign, int first_stage) {
-  using G = Geo<T, SCHEME, TX, TY>;
-  constexpr int BW = G::BW, PL = G::PL, CH = G::CH, WD = TX + 2 * CH;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint64_t bars[2];
-  T* stage = aligned_smem<T>(smem_raw);        // 2 x 2 planes: v1, v2 of X^(i)
-  T* sdy = stage + 2 * 2 * PL;                 // [TY][WD]: d_y v2 on interior rows
-  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(sdy + TY * WD) + 7) & ~uintptr_t(7));
+// Right-hand side of the Helmholtz equation of stage i (Algorithm 1, step 2; the
+// theta-history term with a minus sign, the sign the stage equations of Sec. 3.1 give):
+//   R_i = -kappa_i theta^n + sum_{j<i} a_ij/(dt a_ii^2) D_0.u^(j) + 1/(dt a_ii) D_0.u^n
+//         - sum_{j<=i} a_ij/a_ii D_0^2:B(v^(j)) - sum_{j<i} a_ij/a_ii D_Delta theta^(j),
+// with D_0^2:B(v^(i)) = -D_xx v1 + 2 D_xy v2 + D_yy v1 formed here from v^(i) and stored
+// for the later stages.  A work item (rhs_start, rhs_items) is a row pair times RHS_COLS
+// columns of one instance; each warp takes a segment of RHS_SEG columns, its lanes holding
+// the columns x0 - 2 .. x0 + RHS_SEG + 1: it loads rows y0 - 2 .. y0 + 3 of v1 and v2 at
+// its column once for both rows of the pair, forms D_y v2 there, and takes the
+// x-neighbours of v1 and D_y v2 from the neighbouring lanes (shuffles): no staging, no
+// barrier but around the per-instance coefficient list and the theta sum.  The
+// earlier-stage plane terms are summed as (coefficient, plane) pairs from that list in
+// one unrolled, predicated loop, all their loads in flight together, before any store.
+// The first stage also sums theta^n over the item in a fixed order (th_part).
+constexpr int RHS_THREADS = 32 * RHS_WARPS;
+
+template <typename T, int SCHEME>
+__global__ void __launch_bounds__(RHS_THREADS) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign,
+                                                    int first_stage) {
+  constexpr int MAXT = 1 + 3 * (APD_MAXS - 1);
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ const T* tp[MAXT];
+  __shared__ T tc[MAXT];
+  __shared__ int s_nt;
+  __shared__ double red[RHS_WARPS];
   const BatchDev& b = *bp;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * TX;
-  PlaneList pr;
-  pr.add(i, 3);
-  pr.add(i, 4);
-  tile_loop<T, G, TX, TY>(b, pr, stage, bars, tid, [&](const InstDev& I, const TileRef& t, T* s) {
-    const T* sv1 = s;
-    const T* sv2 = s + PL;
-    const int nx = I.nx;
-    const size_t pl = (size_t)nx * I.ny;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nitems = b.counts[4];
+  int cur = -1;   // instance whose coefficient list is in tp, tc
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k_inst = find_inst(b.rhs_start, b.counts[3], it);
+    const InstDev& I = b.inst[k_inst];
     const Coef<T>& K = coef<T>(I);
-    const T idx = K.inv_dx, idy = K.inv_dy;
-    // cells beyond the grid (ragged edge tile) read cell 0 and store nothing
-    const bool own = t.x0 + tx < nx && t.y0 + ty < I.ny;
-    const size_t o = own ? (size_t)(t.y0 + ty) * nx + (t.x0 + tx) : 0;
-    // right-hand side of the Helmholtz equation (Algorithm 1, step 2; the theta-history term
-    // with a minus sign, the sign the stage equations of Sec. 3.1 give), with the stage coefficients a_ij/(dt a_ii^2), 1/(dt a_ii), a_ij/a_ii
-    // precomputed.  Its pointwise inputs: the FP32 form loads them before the shared-memory
-    // pass so that their latency overlaps it; FP64 loads them where they are used (fewer
-    // registers for the FP64-pipe-bound form).
-    const unsigned mim = b.m_im[i];
-    const T* Xn = reinterpret_cast<const T*>(I.X);
-    T thn = T(0), du1 = T(0), ldu[APD_MAXS], ldb[APD_MAXS], llth[APD_MAXS];
-    if constexpr (sizeof(T) == 4) {
-      thn = Xn[o + 2 * pl];
-      du1 = reinterpret_cast<const T*>(I.Dun)[o];
+    if (k_inst != cur) {
+      __syncthreads();   // readers of the previous list are done
+      if (tid == 0) {
+        const unsigned mim = b.m_im[i];
+        int nt = 0;
+        auto add = [&](const void* p, T c) {
+          tp[nt] = reinterpret_cast<const T*>(p);
+          tc[nt++] = c;
+        };
+        for (int jj = 1; jj < i; ++jj)
+          if (has(mim, jj)) add(I.Du[jj], K.c_du[i][jj]);
+        add(I.Dun, K.c_dun[i]);
+        for (int jj = 1; jj < i; ++jj)
+          if (has(mim, jj)) add(I.DB[jj], -K.c_db[i][jj]);
+        for (int jj = 1; jj < i; ++jj)
+          if (has(mim, jj)) add(I.Lth[jj], theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]);
+        s_nt = nt;
+      }
+      __syncthreads();
+      cur = k_inst;
+    }
+    const int nt = s_nt;
+    const int nx = I.nx, ny = I.ny;
+    const size_t pl = (size_t)nx * ny;
+    // D_0^2:B(v) = -sx2 S_xx + 2 sx1 S_xy + sy2 S_yy with the unscaled sums S (d1_sum,
+    // d2_sum) and D_y v2 = sy1 S_y
+    const T sx1 = d1_scale<T, SCHEME>(K.inv_dx), sy1 = d1_scale<T, SCHEME>(K.inv_dy);
+    const T msx2 = -d2_scale<T, SCHEME>(K.inv_dx), sy2 = d2_scale<T, SCHEME>(K.inv_dy), sx1x2 = T(2) * sx1;
+    const T kap = K.kappa[i];
+    const T cdb = has(b.m_im[i], i) ? K.c_db[i][i] : T(0);
+    const T* v1 = reinterpret_cast<const T*>(I.Xs[i]) + 3 * pl;
+    const T* v2 = v1 + pl;
+    const T* th = reinterpret_cast<const T*>(I.X) + 2 * pl;
+    T* DBi = reinterpret_cast<T*>(I.DB[i]);
+    T* Rp = reinterpret_cast<T*>(I.R);
+    const int local = it - b.rhs_start[k_inst];
+    const int nxb = (nx + RHS_COLS - 1) / RHS_COLS;
+    const int p = local / nxb, xb = local - p * nxb;
+    const int y0 = 2 * p;
+    const bool two = y0 + 1 < ny;
+    const int seg0 = xb * RHS_COLS + warp * (RHS_SEG * RHS_U);   // first column of this warp's segments
+    double tsum = 0.0;
+    // rows y0 - 2 .. y0 + 3 of v1 and v2 at this lane's column of each segment, and the
+    // pointwise inputs of both rows, all loaded before any store
+    T a[RHS_U][6], c[RHS_U][6], R[RHS_U][2], thn[RHS_U][2];
+    int xc[RHS_U];
+    bool outc[RHS_U];
 #pragma unroll
-      for (int jj = 1; jj < APD_MAXS; ++jj) {
-        const bool use = jj < i && has(mim, jj);
-        ldu[jj] = use ? reinterpret_cast<const T*>(I.Du[jj])[o] : T(0);
-        ldb[jj] = use ? reinterpret_cast<const T*>(I.DB[jj])[o] : T(0);
-        llth[jj] = use ? reinterpret_cast<const T*>(I.Lth[jj])[o] : T(0);
+    for (int u = 0; u < RHS_U; ++u) {
+      const int xs = seg0 + u * RHS_SEG + lane - 2;   // this lane's column, unwrapped
+      int x = xs % nx;
+      if (x < 0) x += nx;
+      xc[u] = x;
+      outc[u] = lane >= 2 && lane < RHS_SEG + 2 && xs < nx;
+      if (seg0 + u * RHS_SEG >= nx) continue;       // warp-uniform: a segment past the row end
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        int yy = y0 - 2 + r;
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        const size_t o = (size_t)yy * nx + x;
+        a[u][r] = v1[o];
+        c[u][r] = v2[o];
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const size_t o = (size_t)(y0 + h) * nx + x;
+        const bool on = outc[u] && (h == 0 || two);
+        thn[u][h] = on ? th[o] : T(0);
+        T acc = -kap * thn[u][h];
+        if constexpr (sizeof(T) == 8) {
+          // FP64: only the terms the stage has (a predicated-off FP64 operation still
+          // takes its issue slot on the FP64 pipe)
+          if (on)
+            for (int t = 0; t < nt; ++t) acc = acc + tc[t] * tp[t][o];
+        } else {
+#pragma unroll
+          for (int t = 0; t < MAXT; ++t)
+            if (t < nt && on) acc = acc + tc[t] * tp[t][o];
+        }
+        R[u][h] = acc;
       }
     }
-    for (int k = tid; k < TY * WD; k += TX * TY) {
-      const int r = k / WD, cc = k - r * WD;
-      sdy[k] = cdiff<T, SCHEME>(sv2 + (G::H + r) * BW + (4 - CH) + cc, BW, idy);
+#pragma unroll
+    for (int u = 0; u < RHS_U; ++u) {
+      if (seg0 + u * RHS_SEG >= nx) continue;
+      T B[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const T dy = sy1 * d1_sum<T, SCHEME>(c[u][h], c[u][h + 1], c[u][h + 3], c[u][h + 4]);   // D_y v2 at (x, y0 + h)
+        const T v = a[u][h + 2];
+        const T vm1 = __shfl_up_sync(FULL, v, 1), vm2 = __shfl_up_sync(FULL, v, 2);
+        const T vp1 = __shfl_down_sync(FULL, v, 1), vp2 = __shfl_down_sync(FULL, v, 2);
+        const T dm1 = __shfl_up_sync(FULL, dy, 1), dm2 = __shfl_up_sync(FULL, dy, 2);
+        const T dp1 = __shfl_down_sync(FULL, dy, 1), dp2 = __shfl_down_sync(FULL, dy, 2);
+        const T sxx = d2_sum<T, SCHEME>(vm2, vm1, v, vp1, vp2);
+        const T sxy = d1_sum<T, SCHEME>(dm2, dm1, dp1, dp2);
+        const T syy = d2_sum<T, SCHEME>(a[u][h], a[u][h + 1], a[u][h + 2], a[u][h + 3], a[u][h + 4]);
+        B[h] = msx2 * sxx + sx1x2 * sxy + sy2 * syy;
+      }
+      if (outc[u]) {
+        const size_t o0 = (size_t)y0 * nx + xc[u];
+        DBi[o0] = B[0];
+        Rp[o0] = R[u][0] - cdb * B[0];
+        tsum += double(thn[u][0]);
+        if (two) {
+          DBi[o0 + nx] = B[1];
+          Rp[o0 + nx] = R[u][1] - cdb * B[1];
+          tsum += double(thn[u][1]);
+        }
+      }
     }
-    __syncthreads();
-    const int c = G::C00 + ty * BW + tx;
-    const T dbi = -cdiff2<T, SCHEME>(sv1 + c, 1, idx * idx) + T(2) * cdiff<T, SCHEME>(sdy + ty * WD + CH + tx, 1, idx) +
-                  cdiff2<T, SCHEME>(sv1 + c, BW, idy * idy);
-    if (own) reinterpret_cast<T*>(I.DB[i])[o] = dbi;
-    T R;
-    if constexpr (sizeof(T) == 4) {
-      R = -K.kappa[i] * thn;
-#pragma unroll
-      for (int jj = 1; jj < APD_MAXS; ++jj)
-        if (jj < i && has(mim, jj)) R = R + K.c_du[i][jj] * ldu[jj];
-      R = R + K.c_dun[i] * du1;
-#pragma unroll
-      for (int jj = 1; jj < APD_MAXS; ++jj)
-        if (jj < i && has(mim, jj)) R = R - K.c_db[i][jj] * ldb[jj];
-      if (has(mim, i)) R = R - K.c_db[i][i] * dbi;
-#pragma unroll
-      for (int jj = 1; jj < APD_MAXS; ++jj)
-        if (jj < i && has(mim, jj)) R = R + (theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]) * llth[jj];
-    } else {
-      thn = Xn[o + 2 * pl];
-      R = -K.kappa[i] * thn;
-      for (int jj = 1; jj < i; ++jj)
-        if (has(mim, jj)) R = R + K.c_du[i][jj] * reinterpret_cast<const T*>(I.Du[jj])[o];
-      R = R + K.c_dun[i] * reinterpret_cast<const T*>(I.Dun)[o];
-      for (int jj = 1; jj <= i; ++jj)
-        if (has(mim, jj)) R = R - K.c_db[i][jj] * (jj == i ? dbi : reinterpret_cast<const T*>(I.DB[jj])[o]);
-      for (int jj = 1; jj < i; ++jj)
-        if (has(mim, jj)) R = R + (theta_sign < 0 ? K.c_lth[i][jj] : -K.c_lth[i][jj]) * reinterpret_cast<const T*>(I.Lth[jj])[o];
-    }
-    if (own) reinterpret_cast<T*>(I.R)[o] = R;
     if (first_stage) {
-      const double tsum = block_sum<double>(own ? double(thn) : 0.0, red, tid, TX * TY);
-      if (tid == 0) I.th_part[t.tile] = tsum;
+      for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(FULL, tsum, o);
+      if (lane == 0) red[warp] = tsum;
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < RHS_WARPS; ++w) sum += red[w];
+        I.th_part[local] = sum;
+      }
+      __syncthreads();   // red is rewritten by the next item
     }
-  });
+  }
 }
 
 // ---------------------------------------------------------------------------

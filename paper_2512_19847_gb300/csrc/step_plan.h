@@ -141,7 +141,7 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
     int first = (i == (type_a ? 1 : 2)) ? 1 : 0;           // the first right-hand side also sums theta^n
     {
       void* a[] = {&bp, &i, &sign, &first};
-      if ((st = launch(K.ks.k_rhs, K.g_rhs, blk, K.ks.smem_rhs, a, KK_RHS))) return st;
+      if ((st = launch(K.ks.k_rhs, K.g_rhs, dim3(K.ks.rhs_threads), 0, a, KK_RHS))) return st;
     }
     {
       // each pass: the power-of-two kernel and/or the Bluestein kernel, as the batch needs
