@@ -342,7 +342,7 @@ ap_dvm_status flush(ap_dvm_handle* h) {
     }
     h->up_tiles.push_back(h->up_tiles.back() + d.tiles_x * d.tiles_y);
     h->up_rows.push_back(h->up_rows.back() + (pairs + d.row_pairs - 1) / d.row_pairs);
-    h->up_rhs.push_back(h->up_rhs.back() + rhs_items(s.p.nx, s.p.ny));
+    h->up_rhs.push_back(h->up_rhs.back() + rhs_items(s.p.nx, s.p.ny, h->f32));
     h->up_cols.push_back(h->up_cols.back() + (s.p.nx / 2 + 1 + d.col_group - 1) / d.col_group);
   }
   const int n = (int)h->up_inst[0].size();

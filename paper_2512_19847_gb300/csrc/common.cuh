@@ -128,13 +128,16 @@ struct BatchDev {
   unsigned* err;         // device error flags (bit 0: non-finite state, bit 1: a bounded wait expired)
 };
 
-// Work items of the Helmholtz right-hand side kernel (k_rhs): a row pair times
-// RHS_WARPS * RHS_U segments of RHS_SEG columns, RHS_U per warp.
-#ifndef APD_RHS_U
-#define APD_RHS_U 1
+// Work items of the Helmholtz right-hand side kernel (k_rhs): rhs_pairs row pairs
+// times RHS_WARPS segments of RHS_SEG columns, one segment per warp.
+#ifndef APD_RHS_PY
+#define APD_RHS_PY 2
 #endif
-constexpr int RHS_WARPS = 4, RHS_SEG = 28, RHS_U = APD_RHS_U, RHS_COLS = RHS_WARPS * RHS_SEG * RHS_U;
-__host__ __device__ constexpr int rhs_items(int nx, int ny) { return ((ny + 1) / 2) * ((nx + RHS_COLS - 1) / RHS_COLS); }
+constexpr int RHS_WARPS = 4, RHS_SEG = 28, RHS_COLS = RHS_WARPS * RHS_SEG;
+__host__ __device__ constexpr int rhs_pairs(bool f32) { return f32 ? APD_RHS_PY : 1; }
+__host__ __device__ constexpr int rhs_items(int nx, int ny, bool f32) {
+  return (((ny + 1) / 2 + rhs_pairs(f32) - 1) / rhs_pairs(f32)) * ((nx + RHS_COLS - 1) / RHS_COLS);
+}
 
 // Instance owning work item `item`: the last k with start[k] <= item.
 __device__ __forceinline__ int find_inst(const int* __restrict__ start, int n, int item) {

@@ -142,7 +142,7 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   const int ntiles = I.tiles_x * I.tiles_y;
   const int nrows = (p->ny / 2 + I.row_pairs - 1) / I.row_pairs;
   const int ncols = (p->nx / 2 + 1 + I.col_group - 1) / I.col_group;
-  const int nrhs = rhs_items(p->nx, p->ny);
+  const int nrhs = rhs_items(p->nx, p->ny, false);
   const int ts[2] = {0, ntiles}, rs[2] = {0, nrows}, cs[2] = {0, ncols}, hs[2] = {0, nrhs};
   const int counts[5] = {ntiles, nrows, ncols, 1, nrhs};
   double2 tw[64];                                   // nmax/2 <= 64 for grids of at most 128 cells a side

@@ -768,10 +768,10 @@ __global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const 
 //   R_i = -kappa_i theta^n + sum_{j<i} a_ij/(dt a_ii^2) D_0.u^(j) + 1/(dt a_ii) D_0.u^n
 //         - sum_{j<=i} a_ij/a_ii D_0^2:B(v^(j)) - sum_{j<i} a_ij/a_ii D_Delta theta^(j),
 // with D_0^2:B(v^(i)) = -D_xx v1 + 2 D_xy v2 + D_yy v1 formed here from v^(i) and stored
-// for the later stages.  A work item (rhs_start, rhs_items) is a row pair times RHS_COLS
-// columns of one instance; each warp takes a segment of RHS_SEG columns, its lanes holding
-// the columns x0 - 2 .. x0 + RHS_SEG + 1: it loads rows y0 - 2 .. y0 + 3 of v1 and v2 at
-// its column once for both rows of the pair, forms D_y v2 there, and takes the
+// for the later stages.  A work item (rhs_start, rhs_items) is rhs_pairs row pairs times
+// RHS_COLS columns of one instance; each warp takes a segment of RHS_SEG columns, its lanes
+// holding the columns x0 - 2 .. x0 + RHS_SEG + 1: it loads rows y0 - 2 .. y0 + NR + 1 of v1
+// and v2 at its column once for the item's NR rows, forms D_y v2 there, and takes the
 // x-neighbours of v1 and D_y v2 from the neighbouring lanes (shuffles): no staging, no
 // barrier but around the per-instance coefficient list and the theta sum.  The
 // earlier-stage plane terms are summed as (coefficient, plane) pairs from that list in
@@ -783,6 +783,7 @@ template <typename T, int SCHEME>
 __global__ void __launch_bounds__(RHS_THREADS) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign,
                                                     int first_stage) {
   constexpr int MAXT = 1 + 3 * (APD_MAXS - 1);
+  constexpr int NR = 2 * rhs_pairs(sizeof(T) == 4);   // rows per item
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ const T* tp[MAXT];
   __shared__ T tc[MAXT];
@@ -833,38 +834,32 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs(const BatchDev* __restrict_
     T* Rp = reinterpret_cast<T*>(I.R);
     const int local = it - b.rhs_start[k_inst];
     const int nxb = (nx + RHS_COLS - 1) / RHS_COLS;
-    const int p = local / nxb, xb = local - p * nxb;
-    const int y0 = 2 * p;
-    const bool two = y0 + 1 < ny;
-    const int seg0 = xb * RHS_COLS + warp * (RHS_SEG * RHS_U);   // first column of this warp's segments
+    const int g = local / nxb, xb = local - g * nxb;
+    const int y0 = NR * g, nrows = min(NR, ny - y0);
+    const int seg0 = xb * RHS_COLS + warp * RHS_SEG;   // first column of this warp's segment
     double tsum = 0.0;
-    // rows y0 - 2 .. y0 + 3 of v1 and v2 at this lane's column of each segment, and the
-    // pointwise inputs of both rows, all loaded before any store
-    T a[RHS_U][6], c[RHS_U][6], R[RHS_U][2], thn[RHS_U][2];
-    int xc[RHS_U];
-    bool outc[RHS_U];
-#pragma unroll
-    for (int u = 0; u < RHS_U; ++u) {
-      const int xs = seg0 + u * RHS_SEG + lane - 2;   // this lane's column, unwrapped
+    if (seg0 < nx) {   // warp-uniform: the segment starts inside the row
+      const int xs = seg0 + lane - 2;                 // this lane's column, unwrapped
       int x = xs % nx;
       if (x < 0) x += nx;
-      xc[u] = x;
-      outc[u] = lane >= 2 && lane < RHS_SEG + 2 && xs < nx;
-      if (seg0 + u * RHS_SEG >= nx) continue;       // warp-uniform: a segment past the row end
+      const bool outc = lane >= 2 && lane < RHS_SEG + 2 && xs < nx;
+      // rows y0 - 2 .. y0 + NR + 1 of v1 and v2 at this lane's column, and the pointwise
+      // inputs of the item's rows, all loaded before any store
+      T a[NR + 4], c[NR + 4], R[NR], thn[NR];
 #pragma unroll
-      for (int r = 0; r < 6; ++r) {
+      for (int r = 0; r < NR + 4; ++r) {
         int yy = y0 - 2 + r;
         yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
         const size_t o = (size_t)yy * nx + x;
-        a[u][r] = v1[o];
-        c[u][r] = v2[o];
+        a[r] = v1[o];
+        c[r] = v2[o];
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < NR; ++h) {
         const size_t o = (size_t)(y0 + h) * nx + x;
-        const bool on = outc[u] && (h == 0 || two);
-        thn[u][h] = on ? th[o] : T(0);
-        T acc = -kap * thn[u][h];
+        const bool on = outc && h < nrows;
+        thn[h] = on ? th[o] : T(0);
+        T acc = -kap * thn[h];
         if constexpr (sizeof(T) == 8) {
           // FP64: only the terms the stage has (a predicated-off FP64 operation still
           // takes its issue slot on the FP64 pipe)
@@ -875,35 +870,25 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs(const BatchDev* __restrict_
           for (int t = 0; t < MAXT; ++t)
             if (t < nt && on) acc = acc + tc[t] * tp[t][o];
         }
-        R[u][h] = acc;
+        R[h] = acc;
       }
-    }
 #pragma unroll
-    for (int u = 0; u < RHS_U; ++u) {
-      if (seg0 + u * RHS_SEG >= nx) continue;
-      T B[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const T dy = sy1 * d1_sum<T, SCHEME>(c[u][h], c[u][h + 1], c[u][h + 3], c[u][h + 4]);   // D_y v2 at (x, y0 + h)
-        const T v = a[u][h + 2];
+      for (int h = 0; h < NR; ++h) {
+        const T dy = sy1 * d1_sum<T, SCHEME>(c[h], c[h + 1], c[h + 3], c[h + 4]);   // D_y v2 at (x, y0 + h)
+        const T v = a[h + 2];
         const T vm1 = __shfl_up_sync(FULL, v, 1), vm2 = __shfl_up_sync(FULL, v, 2);
         const T vp1 = __shfl_down_sync(FULL, v, 1), vp2 = __shfl_down_sync(FULL, v, 2);
         const T dm1 = __shfl_up_sync(FULL, dy, 1), dm2 = __shfl_up_sync(FULL, dy, 2);
         const T dp1 = __shfl_down_sync(FULL, dy, 1), dp2 = __shfl_down_sync(FULL, dy, 2);
         const T sxx = d2_sum<T, SCHEME>(vm2, vm1, v, vp1, vp2);
         const T sxy = d1_sum<T, SCHEME>(dm2, dm1, dp1, dp2);
-        const T syy = d2_sum<T, SCHEME>(a[u][h], a[u][h + 1], a[u][h + 2], a[u][h + 3], a[u][h + 4]);
-        B[h] = msx2 * sxx + sx1x2 * sxy + sy2 * syy;
-      }
-      if (outc[u]) {
-        const size_t o0 = (size_t)y0 * nx + xc[u];
-        DBi[o0] = B[0];
-        Rp[o0] = R[u][0] - cdb * B[0];
-        tsum += double(thn[u][0]);
-        if (two) {
-          DBi[o0 + nx] = B[1];
-          Rp[o0 + nx] = R[u][1] - cdb * B[1];
-          tsum += double(thn[u][1]);
+        const T syy = d2_sum<T, SCHEME>(a[h], a[h + 1], a[h + 2], a[h + 3], a[h + 4]);
+        const T Bh = msx2 * sxx + sx1x2 * sxy + sy2 * syy;
+        if (outc && h < nrows) {
+          const size_t o = (size_t)(y0 + h) * nx + x;
+          DBi[o] = Bh;
+          Rp[o] = R[h] - cdb * Bh;
+          tsum += double(thn[h]);
         }
       }
     }

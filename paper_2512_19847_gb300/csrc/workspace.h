@@ -85,7 +85,7 @@ inline size_t carve_instance(const ap_dvm_params& p, char* base, InstDev* d, boo
   I.lamx32 = f32 ? reinterpret_cast<float*>(take((size_t)(p.nx / 2 + 1) * sizeof(float))) : nullptr;
   I.lamy32 = f32 ? reinterpret_cast<float*>(take((size_t)p.ny * sizeof(float))) : nullptr;
   // one partial sum per tile: at most ceil(nx/8) * ceil(ny/4) tiles (the smallest tile sides)
-  I.th_part = reinterpret_cast<double*>(take((size_t)rhs_items(p.nx, p.ny) * sizeof(double)));
+  I.th_part = reinterpret_cast<double*>(take((size_t)rhs_items(p.nx, p.ny, p.precision != AP_DVM_FP64) * sizeof(double)));
   for (int a = 0; a < 2; ++a) {   // tables of an axis that is not a power of two: mixed radix or Bluestein
     const int na = a ? p.ny : p.nx;
     unsigned plan = 0;
