@@ -658,6 +658,19 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
   r2 = T(a2);
 }
 
+// Resident blocks per SM the explicit and update kernels are compiled for: threads worth
+// three 256-thread blocks in FP64 (the register budget that removes spills: 128 at 512
+// threads), APD_STENCIL_THREADS32 threads in the FP32 forms: 896 (seven 128-thread blocks of
+// the 16x8 tile at 72 registers, no spills) measured 8-9 % faster than 768 (six blocks, 80
+// registers); 1024 (64 registers) spills.
+#ifndef APD_STENCIL_THREADS32
+#define APD_STENCIL_THREADS32 896
+#endif
+template <typename T>
+__host__ __device__ constexpr int stencil_min_blocks(int threads) {
+  return (sizeof(T) == 4 ? APD_STENCIL_THREADS32 : 768) / threads;
+}
+
 // Factor of 1/h in the difference of interface fluxes: the WENO fluxes come out
 // doubled (the split without its 1/2), the LF1 flux of Sec. 3.2 does not.
 template <typename T, int SCHEME>
@@ -665,7 +678,7 @@ __device__ __forceinline__ T flux_scale(T inv_h) { return SCHEME == LF1_C2 ? inv
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_explicit(const BatchDev* __restrict__ bp, int j, unsigned need, double weno_eps) {
+__global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_explicit(const BatchDev* __restrict__ bp, int j, unsigned need, double weno_eps) {
   using G = Geo<T, SCHEME, TX, TY>;
   constexpr int BW = G::BW, PL = G::PL, NX = G::NX, NY = G::NY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -908,7 +921,7 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs(const BatchDev* __restrict_
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 3 * 256 / (TX * TY)) k_update(const BatchDev* __restrict__ bp, int i, double weno_eps,
+__global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_update(const BatchDev* __restrict__ bp, int i, double weno_eps,
                                                                        int close_step, int form) {
   using G = Geo<T, SCHEME, TX, TY>;
   constexpr int BW = G::BW, PL = G::PL, NX = G::NX, NY = G::NY;
