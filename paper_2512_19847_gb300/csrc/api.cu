@@ -94,7 +94,7 @@ struct ap_dvm_handle {
   // kernels
   StencilSet ks{};
   MiscSet km{};
-  int grid_explicit = 0, grid_rhs = 0, grid_update = 0, grid_fft = 0, grid_cols = 0, grid_finish = 0;
+  int grid_explicit = 0, grid_rhs = 0, grid_update = 0, grid_fft = 0, grid_cols = 0, grid_finish = 0, grid_rows = 0;
   unsigned fft_kinds = 0;   // FftKinds of the attached solves (the launches a step enqueues)
   size_t smem_update = 0;
   bool kernels_ready = false;
@@ -291,12 +291,18 @@ ap_dvm_status prepare_kernels(ap_dvm_handle* h) {
   if ((st = occupancy_grid(h, h->ks.k_update, thr, h->smem_update, &h->grid_update))) return st;
   if ((st = occupancy_grid(h, h->km.k_finish, thr, 0, &h->grid_finish))) return st;
   h->grid_fft = 1 << 30;
-  for (const void* fn : {h->km.k_rows_fwd, h->km.k_rows_inv, h->km.k_rows_fwd_bs, h->km.k_cols_bs, h->km.k_rows_inv_bs}) {
+  for (const void* fn : {h->km.k_rows_fwd_bs, h->km.k_cols_bs, h->km.k_rows_inv_bs}) {
     int g = 0;
     if ((st = occupancy_grid(h, fn, 256, fft_smem(h), &g))) return st;
     h->grid_fft = std::min(h->grid_fft, g);
   }
-  if ((st = occupancy_grid(h, h->km.k_cols, h->f32 ? 1024 : 256, cols_smem(h), &h->grid_cols))) return st;
+  h->grid_rows = 1 << 30;
+  for (const void* fn : {h->km.k_rows_fwd, h->km.k_rows_inv}) {
+    int g = 0;
+    if ((st = occupancy_grid(h, fn, h->km.rows_threads, fft_smem(h), &g))) return st;
+    h->grid_rows = std::min(h->grid_rows, g);
+  }
+  if ((st = occupancy_grid(h, h->km.k_cols, h->km.cols_threads, cols_smem(h), &h->grid_cols))) return st;
   h->kernels_ready = true;
   h->graph_valid[0] = h->graph_valid[1] = false;
   return AP_DVM_OK;
@@ -410,7 +416,8 @@ ap_dvm_status profile_collect(ap_dvm_handle* h) {
 // Kernels of one IMEX step of the given parity for all attached solves (see the file header).
 ap_dvm_status enqueue_step(ap_dvm_handle* h, cudaStream_t stream, int parity) {
   StepKernels K{h->ks,       h->km,         h->grid_explicit, h->grid_rhs,   h->grid_update, h->grid_finish,
-                h->grid_fft, h->grid_cols, h->f32 ? 1024 : 256, fft_smem(h), cols_smem(h), h->smem_update, h->fft_kinds};
+                h->grid_fft, h->grid_cols, h->km.cols_threads, fft_smem(h), cols_smem(h), h->smem_update, h->fft_kinds,
+                h->grid_rows};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int kind) -> int {
     return (int)launch(h, stream, fn, grid, block, smem, args, kind);
   };

@@ -27,6 +27,8 @@ struct MiscSet {
   const void* k_stage1;    // per tile shape; type-A tableaux only
   const void* k_rows_fwd;    // Helmholtz transforms, power-of-two axes ...
   const void* k_cols;
+  int cols_threads;        // threads per block of k_cols
+  int rows_threads;        // threads per block of k_rows_fwd and k_rows_inv
   const void* k_rows_inv;
   const void* k_rows_fwd_bs; // ... and axes of other lengths (Bluestein)
   const void* k_cols_bs;

@@ -301,8 +301,18 @@ __device__ __forceinline__ void theta_mean(const InstDev& I, int nt, double* red
 
 // ---- power-of-two axes (shared memory padded, pidx<pad_shift<T>()>)
 
+// Threads per block of the power-of-two row passes (FP32 configurable; 1024 / threads
+// resident blocks per SM in FP32, three in FP64).
+#ifndef APD_ROWS_THREADS32
+#define APD_ROWS_THREADS32 256
+#endif
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
+__host__ __device__ constexpr int rows_threads() { return sizeof(T) == 4 ? APD_ROWS_THREADS32 : 256; }
+template <typename T>
+__host__ __device__ constexpr int rows_min_blocks() { return sizeof(T) == 4 ? 1024 / APD_ROWS_THREADS32 : 3; }
+
+template <typename T>
+__global__ void __launch_bounds__(rows_threads<T>(), rows_min_blocks<T>()) k_fft_rows_fwd(const BatchDev* __restrict__ bp) {
   using C = typename Cplx<T>::type;
   constexpr int PS = pad_shift<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -348,15 +358,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_fwd(co
 // frequency (natural order in, bit-reversed out) and the inverse by decimation
 // in time (bit-reversed in, natural out), so the symbol division takes the
 // spectrum in bit-reversed order and no permutation pass is needed.  The FP32
-// form runs it with 1024 threads (cols_threads<T>: one radix-2^3 butterfly per
-// thread and pass for four columns of 2048), the FP64 form with 256 (its
+// form runs it with blocks of 512 threads, two per SM (cols_threads<T>; at 2048^2
+// its 257 items of four columns then run in one wave: 0.098 ms per step against
+// 0.120 with one block of 1024 and 0.143 with 256), the FP64 form with 256 (its
 // butterflies keep the FP64 pipe busy either way); the load and store loops are
 // unrolled so that several global accesses per thread are in flight.
+#ifndef APD_COLS_THREADS32
+#define APD_COLS_THREADS32 512
+#endif
 template <typename T>
-__host__ __device__ constexpr int cols_threads() { return sizeof(T) == 4 ? 1024 : 256; }
+__host__ __device__ constexpr int cols_threads() { return sizeof(T) == 4 ? APD_COLS_THREADS32 : 256; }
 
 template <typename T>
-__global__ void __launch_bounds__(cols_threads<T>(), sizeof(T) == 4 ? 1 : 2) k_fft_cols(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(cols_threads<T>(), sizeof(T) == 4 ? 1024 / APD_COLS_THREADS32 : 2)
+    k_fft_cols(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   constexpr int PS = pad_shift<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -411,7 +426,7 @@ __global__ void __launch_bounds__(cols_threads<T>(), sizeof(T) == 4 ? 1 : 2) k_f
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
+__global__ void __launch_bounds__(rows_threads<T>(), rows_min_blocks<T>()) k_fft_rows_inv(const BatchDev* __restrict__ bp, int i) {
   using C = typename Cplx<T>::type;
   constexpr int PS = pad_shift<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -32,6 +32,8 @@ MiscSet make_misc() {
   m.k_stage1 = reinterpret_cast<const void*>(&k_stage1<T, TX, TY>);
   m.k_rows_fwd = reinterpret_cast<const void*>(&k_fft_rows_fwd<T>);
   m.k_cols = reinterpret_cast<const void*>(&k_fft_cols<T>);
+  m.cols_threads = cols_threads<T>();
+  m.rows_threads = rows_threads<T>();
   m.k_rows_inv = reinterpret_cast<const void*>(&k_fft_rows_inv<T>);
   m.k_rows_fwd_bs = reinterpret_cast<const void*>(&k_fft_rows_fwd_bs<T>);
   m.k_cols_bs = reinterpret_cast<const void*>(&k_fft_cols_bs<T>);

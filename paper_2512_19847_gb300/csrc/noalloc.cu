@@ -111,9 +111,9 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
   const size_t smem_upd = update_smem(ks, *p);
   NA_TRY(grid_of(ks.k_update, thr, smem_upd, sms, &g_upd));
   NA_TRY(grid_of(km.k_finish, thr, 0, sms, &g_fin));
-  NA_TRY(grid_of(km.k_rows_fwd, 256, fft_smem, sms, &g1));
-  NA_TRY(grid_of(km.k_cols, 256, cols_smem, sms, &g2));
-  NA_TRY(grid_of(km.k_rows_inv, 256, fft_smem, sms, &g3));
+  NA_TRY(grid_of(km.k_rows_fwd, km.rows_threads, fft_smem, sms, &g1));
+  NA_TRY(grid_of(km.k_cols, km.cols_threads, cols_smem, sms, &g2));
+  NA_TRY(grid_of(km.k_rows_inv, km.rows_threads, fft_smem, sms, &g3));
   const int g_fft = std::min(g1, g3);
 
   // descriptors, built on the host stack and copied into the scratch
@@ -173,7 +173,8 @@ extern "C" ap_dvm_status ap_dvm_step_noalloc(const ap_dvm_params* p, double* d_s
 
   // the steps: the launch sequence of one IMEX step shared with the handle path
   BatchDev* bp = reinterpret_cast<BatchDev*>(base + L.batch);
-  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, g2, 256, fft_smem, cols_smem, smem_upd, FFT_X_POW2 | FFT_Y_POW2};
+  StepKernels K{ks, km, g_exp, g_rhs, g_upd, g_fin, g_fft, g2, km.cols_threads, fft_smem, cols_smem, smem_upd, FFT_X_POW2 | FFT_Y_POW2,
+                g_fft};
   auto ln = [&](const void* fn, int grid, dim3 block, size_t smem, void** args, int) -> int {
     return cudaLaunchKernel(fn, dim3(grid), block, args, smem, stream) == cudaSuccess ? 0 : (int)AP_DVM_ERR_CUDA;
   };

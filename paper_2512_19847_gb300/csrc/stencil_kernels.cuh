@@ -424,11 +424,14 @@ struct PlaneSum {
   }
 };
 
+#ifndef APD_RUN_LEN
+#define APD_RUN_LEN 5   // interfaces per register run
+#endif
 template <int TX, int TY, int NP, int AX, class UF>
 __device__ __forceinline__ void w5_runs_item(const float* g, const UF& U, bool neg, float* out, float ew4, int line,
                                              int run) {
   using G = Geo<float, WENO5_C4, TX, TY>;
-  constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = 5, NPT = KR + 5;
+  constexpr int H = G::H, SW = G::BW, XO = G::XO, KR = APD_RUN_LEN, NPT = KR + 5;
   constexpr int LL = AX == 0 ? G::W : G::HH;
   constexpr int NI = AX == 0 ? TX + 1 : TY + 1;
   // the last run reads up to point RUNS*KR + 4: inside the staged row for x (BW = TX + 8
@@ -466,7 +469,7 @@ __device__ __forceinline__ void w5_runs_item(const float* g, const UF& U, bool n
 template <int TX, int TY, int NP, unsigned NEGX, unsigned NEGY, class UF>
 __device__ __forceinline__ void w5_runs_both_axes(const float* const* gx, const UF* ux, const float* const* gy, const UF* uy,
                                                   float* fx, float* fy, float ew, int tid) {
-  constexpr int KR = 5, NT = TX * TY;
+  constexpr int KR = APD_RUN_LEN, NT = TX * TY;
   constexpr int RX = (TX + 1 + KR - 1) / KR, RY = (TY + 1 + KR - 1) / KR;
   constexpr int IX = NP * TY * RX, IY = NP * TX * RY;
   constexpr int NXI = TY * (TX + 1), NYI = (TY + 1) * TX;
@@ -791,9 +794,12 @@ __global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_expl
 // one unrolled, predicated loop, all their loads in flight together, before any store.
 // The first stage also sums theta^n over the item in a fixed order (th_part).
 constexpr int RHS_THREADS = 32 * RHS_WARPS;
+#ifndef APD_RHS_MINB32
+#define APD_RHS_MINB32 8   // FP32: resident blocks per SM the kernel is compiled for (64 registers; 10 spill)
+#endif
 
 template <typename T, int SCHEME>
-__global__ void __launch_bounds__(RHS_THREADS) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign,
+__global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 : 1) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign,
                                                     int first_stage) {
   constexpr int MAXT = 1 + 3 * (APD_MAXS - 1);
   constexpr int NR = 2 * rhs_pairs(sizeof(T) == 4);   // rows per item

@@ -32,6 +32,7 @@ struct StepKernels {
   size_t fft_smem, cols_smem;   // the power-of-two column pass has its own (wider) work items
   size_t smem_update;
   unsigned fft_kinds;   // FftKinds present among the attached solves
+  int g_rows;           // grid of the power-of-two row passes (km.rows_threads threads per block)
 };
 
 // Planes k_update stages at its largest stage: theta, v1, v2 and u1, u2 of every
@@ -148,11 +149,11 @@ int enqueue_imex_step(const ap_dvm_params& t, const StepKernels& K, BatchDev* bp
       void* a[] = {&bp};
       void* b[] = {&bp, &i};
       const unsigned kk = K.fft_kinds;
-      if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_fwd, K.g_fft, dim3(256), K.fft_smem, a, KK_ROWS_FWD))) return st;
+      if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_fwd, K.g_rows, dim3(K.km.rows_threads), K.fft_smem, a, KK_ROWS_FWD))) return st;
       if ((kk & FFT_X_BS) && (st = launch(K.km.k_rows_fwd_bs, K.g_fft, dim3(256), K.fft_smem, a, KK_ROWS_FWD))) return st;
       if ((kk & FFT_Y_POW2) && (st = launch(K.km.k_cols, K.g_cols, dim3(K.cols_threads), K.cols_smem, b, KK_COLS))) return st;
       if ((kk & FFT_Y_BS) && (st = launch(K.km.k_cols_bs, K.g_fft, dim3(256), K.fft_smem, b, KK_COLS))) return st;
-      if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_inv, K.g_fft, dim3(256), K.fft_smem, b, KK_ROWS_INV))) return st;
+      if ((kk & FFT_X_POW2) && (st = launch(K.km.k_rows_inv, K.g_rows, dim3(K.km.rows_threads), K.fft_smem, b, KK_ROWS_INV))) return st;
       if ((kk & FFT_X_BS) && (st = launch(K.km.k_rows_inv_bs, K.g_fft, dim3(256), K.fft_smem, b, KK_ROWS_INV))) return st;
     }
     {
