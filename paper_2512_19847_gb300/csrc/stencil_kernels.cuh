@@ -90,13 +90,12 @@ __device__ __forceinline__ TileRef decode_tile(const BatchDev& b, int it) {
   return t;
 }
 
-// Plain loads of the staged box with periodic wrap; with outside_only, only
-// the cells outside the grid (which a TMA copy fills with zero) are written.
-// A ragged tile at the high edge of the grid stages periodic images past the
-// last cell as well: its cells beyond the grid are computed but not stored.
+// Plain loads of the staged box with periodic wrap (instances without TMA staging).
+// A ragged tile at the high edge of the grid stages periodic images past the last
+// cell as well: its cells beyond the grid are computed but not stored.
 template <typename T, class G>
-__device__ __forceinline__ void stage_plain(const InstDev& I, const PlaneList& pr, T* dst, int x0, int y0,
-                                            bool outside_only, int tid, int nthr) {
+__device__ __forceinline__ void stage_plain(const InstDev& I, const PlaneList& pr, T* dst, int x0, int y0, int tid,
+                                            int nthr) {
   const int nx = I.nx, ny = I.ny;
   const size_t pl = (size_t)nx * ny;
   for (int k = 0; k < pr.n; ++k) {
@@ -104,9 +103,50 @@ __device__ __forceinline__ void stage_plain(const InstDev& I, const PlaneList& p
     for (int e = tid; e < G::BW * G::BH; e += nthr) {
       const int r = e / G::BW, c = e - r * G::BW;
       const int gx = x0 - 4 + c, gy = y0 - G::H + r;
-      if (outside_only && gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
       dst[k * G::PL + e] = g[(size_t)wrap_index(gy, ny) * nx + wrap_index(gx, nx)];
     }
+  }
+}
+
+// After a TMA copy of a box that crosses the grid edge: write the periodic images into
+// the box cells outside the grid (which the copy filled with zero), visiting only those
+// cells (the rows above and below the grid, then the columns left and right of it on the
+// other rows), every staged plane's value of one cell loaded before any is stored.
+template <typename T, class G>
+__device__ __forceinline__ void stage_edges(const InstDev& I, const PlaneList& pr, T* dst, int x0, int y0, int tid,
+                                            int nthr) {
+  constexpr int MAXP = 3 + 2 * (APD_MAXS - 1);   // the most planes a kernel stages
+  const int nx = I.nx, ny = I.ny;
+  const size_t pl = (size_t)nx * ny;
+  const int bx0 = x0 - 4, by0 = y0 - G::H;
+  const int rlo = max(0, -by0), rhi = max(0, by0 + G::BH - ny);
+  const int clo = max(0, -bx0), chi = max(0, bx0 + G::BW - nx);
+  const int nfull = (rlo + rhi) * G::BW, ncol = clo + chi;
+  const int total = nfull + (G::BH - rlo - rhi) * ncol;
+  const T* src[MAXP];
+#pragma unroll
+  for (int k = 0; k < MAXP; ++k)
+    src[k] = k < pr.n ? reinterpret_cast<const T*>(stage_buffer(I, pr.buf(k))) + (size_t)pr.plane(k) * pl : nullptr;
+  for (int e = tid; e < total; e += nthr) {
+    int r, c;
+    if (e < nfull) {
+      const int q = e / G::BW;
+      c = e - q * G::BW;
+      r = q < rlo ? q : G::BH - rhi + (q - rlo);
+    } else {
+      const int e2 = e - nfull, q = e2 / ncol, w = e2 - q * ncol;
+      r = rlo + q;
+      c = w < clo ? w : G::BW - chi + (w - clo);
+    }
+    const size_t go = (size_t)wrap_index(by0 + r, ny) * nx + wrap_index(bx0 + c, nx);
+    const int so = r * G::BW + c;
+    T v[MAXP];
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k)
+      if (k < pr.n) v[k] = src[k][go];
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k)
+      if (k < pr.n) dst[k * G::PL + so] = v[k];
   }
 }
 
@@ -129,7 +169,7 @@ __device__ __forceinline__ void stage_begin(const BatchDev& b, int it, const Pla
         tma_load_3d(dst + k * G::PL, stage_map(I, pr.buf(k)), t.x0 - 4, t.y0 - G::H, pr.plane(k), bar);
     }
   } else {
-    stage_plain<T, G>(I, pr, dst, t.x0, t.y0, false, tid, nthr);
+    stage_plain<T, G>(I, pr, dst, t.x0, t.y0, tid, nthr);
   }
 }
 
@@ -162,7 +202,7 @@ __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr
           if (tid == 0) atomicOr(b.err, 2u);
           return;
         }
-        if (tile_on_edge<G>(I, t.x0, t.y0)) stage_plain<T, G>(I, pr, stage0, t.x0, t.y0, true, tid, NT);
+        if (tile_on_edge<G>(I, t.x0, t.y0)) stage_edges<T, G>(I, pr, stage0, t.x0, t.y0, tid, NT);
       }
       __syncthreads();
       body(I, t, stage0);
@@ -190,7 +230,7 @@ __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr
         if (next_tma) mbar_wait(&bars[cur ^ 1], (phase >> (cur ^ 1)) & 1u);
         return;
       }
-      if (tile_on_edge<G>(I, t.x0, t.y0)) stage_plain<T, G>(I, pr, sbuf, t.x0, t.y0, true, tid, NT);
+      if (tile_on_edge<G>(I, t.x0, t.y0)) stage_edges<T, G>(I, pr, sbuf, t.x0, t.y0, tid, NT);
     }
     __syncthreads();
     body(I, t, sbuf);
