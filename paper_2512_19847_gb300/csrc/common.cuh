@@ -128,15 +128,19 @@ struct BatchDev {
   unsigned* err;         // device error flags (bit 0: non-finite state, bit 1: a bounded wait expired)
 };
 
-// Work items of the Helmholtz right-hand side kernel (k_rhs): rhs_pairs row pairs
-// times RHS_WARPS segments of RHS_SEG columns, one segment per warp.
+// Work of the Helmholtz right-hand side kernel (k_rhs): a task is rhs_pairs row pairs
+// times a segment of RHS_SEG columns (one warp); the tasks of an instance, row group by
+// row group, are taken RHS_WARPS at a time as the kernel's work items.
 #ifndef APD_RHS_PY
 #define APD_RHS_PY 2
 #endif
-constexpr int RHS_WARPS = 4, RHS_SEG = 28, RHS_COLS = RHS_WARPS * RHS_SEG;
+constexpr int RHS_WARPS = 4, RHS_SEG = 28;
 __host__ __device__ constexpr int rhs_pairs(bool f32) { return f32 ? APD_RHS_PY : 1; }
+__host__ __device__ constexpr int rhs_tasks(int nx, int ny, bool f32) {
+  return (((ny + 1) / 2 + rhs_pairs(f32) - 1) / rhs_pairs(f32)) * ((nx + RHS_SEG - 1) / RHS_SEG);
+}
 __host__ __device__ constexpr int rhs_items(int nx, int ny, bool f32) {
-  return (((ny + 1) / 2 + rhs_pairs(f32) - 1) / rhs_pairs(f32)) * ((nx + RHS_COLS - 1) / RHS_COLS);
+  return (rhs_tasks(nx, ny, f32) + RHS_WARPS - 1) / RHS_WARPS;
 }
 
 // Instance owning work item `item`: the last k with start[k] <= item.

@@ -834,9 +834,9 @@ __global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_expl
 //   R_i = -kappa_i theta^n + sum_{j<i} a_ij/(dt a_ii^2) D_0.u^(j) + 1/(dt a_ii) D_0.u^n
 //         - sum_{j<=i} a_ij/a_ii D_0^2:B(v^(j)) - sum_{j<i} a_ij/a_ii D_Delta theta^(j),
 // with D_0^2:B(v^(i)) = -D_xx v1 + 2 D_xy v2 + D_yy v1 formed here from v^(i) and stored
-// for the later stages.  A work item (rhs_start, rhs_items) is rhs_pairs row pairs times
-// RHS_COLS columns of one instance; each warp takes a segment of RHS_SEG columns, its lanes
-// holding the columns x0 - 2 .. x0 + RHS_SEG + 1: it loads rows y0 - 2 .. y0 + NR + 1 of v1
+// for the later stages.  A work item (rhs_start, rhs_items) is RHS_WARPS consecutive tasks
+// of one instance, one per warp: a task is rhs_pairs row pairs times a segment of RHS_SEG
+// columns, the warp's lanes holding the columns x0 - 2 .. x0 + RHS_SEG + 1: it loads rows y0 - 2 .. y0 + NR + 1 of v1
 // and v2 at its column once for the item's NR rows, forms D_y v2 there, and takes the
 // x-neighbours of v1 and D_y v2 from the neighbouring lanes (shuffles): no staging, no
 // barrier but around the per-instance coefficient list and the theta sum.  The
@@ -902,12 +902,13 @@ __global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 :
     T* DBi = reinterpret_cast<T*>(I.DB[i]);
     T* Rp = reinterpret_cast<T*>(I.R);
     const int local = it - b.rhs_start[k_inst];
-    const int nxb = (nx + RHS_COLS - 1) / RHS_COLS;
-    const int g = local / nxb, xb = local - g * nxb;
+    const int nseg = (nx + RHS_SEG - 1) / RHS_SEG;
+    const int task = local * RHS_WARPS + warp;          // this warp's (row group, segment)
+    const int g = task / nseg, sg = task - g * nseg;
     const int y0 = NR * g, nrows = min(NR, ny - y0);
-    const int seg0 = xb * RHS_COLS + warp * RHS_SEG;   // first column of this warp's segment
+    const int seg0 = sg * RHS_SEG;                       // first column of this warp's segment
     double tsum = 0.0;
-    if (seg0 < nx) {   // warp-uniform: the segment starts inside the row
+    if (task < rhs_tasks(nx, ny, sizeof(T) == 4)) {   // warp-uniform: past the instance's last task
       const int xs = seg0 + lane - 2;                 // this lane's column, unwrapped
       int x = xs % nx;
       if (x < 0) x += nx;
