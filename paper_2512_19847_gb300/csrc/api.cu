@@ -334,9 +334,17 @@ ap_dvm_status flush(ap_dvm_handle* h) {
     d.tiles_y = (s.p.ny + TY - 1) / TY;
     const int pairs = (s.p.ny + 1) / 2;   // row pairs (the last one single when ny is odd)
     d.row_pairs = std::max(1, std::min(h->eblk >> d.lnx, pairs));
-    // power-of-two columns: a few adjacent columns per item (4 FP32 or 2 FP64: 32-byte row segments)
-    d.col_group = is_pow2(s.p.ny) ? std::min(h->f32 ? 4 : 2, std::max(1, h->eblk_cols >> d.lny))
-                                  : std::max(1, h->eblk >> d.lny);
+    // power-of-two columns: as many adjacent columns per item as the item's buffer holds
+    // (4 FP32 or 2 FP64 of 2048 cells: 32-byte row segments; more on shorter columns), up to
+    // the power of two that covers the nx/2 + 1 spectral columns
+    if (is_pow2(s.p.ny)) {
+      const int cap = std::max(1, h->eblk_cols >> d.lny), nh = s.p.nx / 2 + 1;
+      int g = 1;
+      while (g < cap && g < nh) g <<= 1;
+      d.col_group = g;
+    } else {
+      d.col_group = std::max(1, h->eblk >> d.lny);
+    }
     for (int par = 0; par < 2; ++par) {   // the instance as steps of either parity see it
       InstDev v = view(s, par);
       // tensor maps of the stage buffers for the current tile shape (TMA staging)
