@@ -844,12 +844,18 @@ __global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_expl
 // one unrolled, predicated loop, all their loads in flight together, before any store.
 // The first stage also sums theta^n over the item in a fixed order (th_part).
 constexpr int RHS_THREADS = 32 * RHS_WARPS;
+// Resident blocks per SM the kernel is compiled for: FP32 8 (64 registers; 10 spill),
+// FP64 4 (128 registers: 0.585 ms per step at 2048^2 against 0.605 with 5 blocks, which
+// spill, and 0.624 with no bound, which takes 136 and runs 3 blocks).
 #ifndef APD_RHS_MINB32
-#define APD_RHS_MINB32 8   // FP32: resident blocks per SM the kernel is compiled for (64 registers; 10 spill)
+#define APD_RHS_MINB32 8
+#endif
+#ifndef APD_RHS_MINB64
+#define APD_RHS_MINB64 4
 #endif
 
 template <typename T, int SCHEME>
-__global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 : 1) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign,
+__global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 : APD_RHS_MINB64) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign,
                                                     int first_stage) {
   constexpr int MAXT = 1 + 3 * (APD_MAXS - 1);
   constexpr int NR = 2 * rhs_pairs(sizeof(T) == 4);   // rows per item
