@@ -178,6 +178,22 @@ def test_fp32_form_ragged(nx, ny):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("nx,ny", [(8, 9), (9, 10), (27, 13), (16, 11), (50, 27)])
+def test_fp32_form_narrow_and_short_grids(nx, ny):
+    """FP32 form on grids narrower than one right-hand-side segment of 28 columns (lane
+    columns wrapping more than once) and with few, odd rows (the last item of two row pairs
+    ending past the last row), against the oracle on a resolved flow."""
+    u1, u2, pr = W.taylor_green(nx, ny)
+    X0 = O.equilibrium_state(u1, u2, pr)
+    dt = W.stable_dt(u1, u2, 2 * math.pi / nx, 0.05)
+    p, o = _pair(nx, ny, "WENO5_C4", "gsa2", 1e-4, 0.05, dt, mach=1e-3)
+    p.precision = api.FP32_DEV
+    got = run_gpu(p, X0, 5)
+    ref = O.run(X0, o, 5)
+    err = np.max(np.hypot(got[0] - ref[0], got[1] - ref[1])) / np.max(np.hypot(ref[0], ref[1]))
+    assert err <= 1e-5, err
+
+
 def test_batch_mixed_sizes_equal_alone():
     """One batch holding power-of-two and other sizes: each result equals the solve alone bit for bit."""
     tmpl = api.default_params(100, 100, eps=1e-2, dt=0.01, tableau=tableaux.gsa2())
