@@ -844,11 +844,12 @@ __global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_expl
 // one unrolled, predicated loop, all their loads in flight together, before any store.
 // The first stage also sums theta^n over the item in a fixed order (th_part).
 constexpr int RHS_THREADS = 32 * RHS_WARPS;
-// Resident blocks per SM the kernel is compiled for: FP32 8 (64 registers; 10 spill),
-// FP64 4 (128 registers: 0.585 ms per step at 2048^2 against 0.605 with 5 blocks, which
-// spill, and 0.624 with no bound, which takes 136 and runs 3 blocks).
+// Resident blocks per SM the kernel is compiled for: FP32 7 (72 registers: 0.146 ms per
+// step at 2048^2 against 0.151 with 8 blocks at 64; 10 spill; three row pairs per item at
+// 6 blocks 0.184), FP64 4 (128 registers: 0.585 ms per step against 0.605 with 5 blocks,
+// which spill, and 0.624 with no bound, which takes 136 and runs 3 blocks).
 #ifndef APD_RHS_MINB32
-#define APD_RHS_MINB32 8
+#define APD_RHS_MINB32 7
 #endif
 #ifndef APD_RHS_MINB64
 #define APD_RHS_MINB64 4
