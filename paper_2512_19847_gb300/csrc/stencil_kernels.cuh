@@ -836,10 +836,11 @@ __global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_expl
 // with D_0^2:B(v^(i)) = -D_xx v1 + 2 D_xy v2 + D_yy v1 formed here from v^(i) and stored
 // for the later stages.  A work item (rhs_start, rhs_items) is RHS_WARPS consecutive tasks
 // of one instance, one per warp: a task is rhs_pairs row pairs times a segment of RHS_SEG
-// columns, the warp's lanes holding the columns x0 - 2 .. x0 + RHS_SEG + 1: it loads rows y0 - 2 .. y0 + NR + 1 of v1
-// and v2 at its column once for the item's NR rows, forms D_y v2 there, and takes the
-// x-neighbours of v1 and D_y v2 from the neighbouring lanes (shuffles): no staging, no
-// barrier but around the per-instance coefficient list and the theta sum.  The
+// columns, the warp's lanes holding the columns x0 - 2 .. x0 + RHS_SEG + 1.  A lane loads
+// rows y0 - 2 .. y0 + NR + 1 of v1 and v2 at its column once for the task's NR rows, forms
+// D_y v2 there, and takes the x-neighbours of v1 and D_y v2 from the neighbouring lanes
+// (shuffles): no staging, no barrier but around the per-instance coefficient list and the
+// theta sum.  The
 // earlier-stage plane terms are summed as (coefficient, plane) pairs from that list in
 // one unrolled, predicated loop, all their loads in flight together, before any store.
 // The first stage also sums theta^n over the item in a fixed order (th_part).
@@ -856,8 +857,8 @@ constexpr int RHS_THREADS = 32 * RHS_WARPS;
 #endif
 
 template <typename T, int SCHEME>
-__global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 : APD_RHS_MINB64) k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign,
-                                                    int first_stage) {
+__global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 : APD_RHS_MINB64)
+    k_rhs(const BatchDev* __restrict__ bp, int i, double theta_sign, int first_stage) {
   constexpr int MAXT = 1 + 3 * (APD_MAXS - 1);
   constexpr int NR = 2 * rhs_pairs(sizeof(T) == 4);   // rows per item
   constexpr unsigned FULL = 0xffffffffu;
