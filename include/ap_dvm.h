@@ -291,6 +291,16 @@ void ap_dvm_destroy(ap_dvm_handle* h);
 ap_dvm_status ap_dvm_fma_peak(int precision, int iters, int reps, void* cuda_stream, double* tflops,
                               double* ms_per_launch);
 
+/* Self-check of the integer-pipe FP32 <-> FP64 conversions the FP32 forms use in place
+ * of the conversion instructions (the moment sums of the close and the FP64
+ * relaxations): for each of the n FP64 values at d_in (device), the narrowing to FP32
+ * (nearest, ties to even) and the widening of that FP32 value back to FP64 are compared
+ * with the instructions' results bit for bit (a NaN only as a NaN).  d_counts (device,
+ * 2 unsigned, caller-owned) receives the numbers of mismatching narrowings and
+ * widenings; it is zeroed first.  Asynchronous on cuda_stream.  Returns AP_DVM_ERR_ARG
+ * for null pointers or n < 0, AP_DVM_ERR_CUDA if a launch fails. */
+ap_dvm_status ap_dvm_check_conversions(const double* d_in, int n, unsigned* d_counts, void* cuda_stream);
+
 /* Fill *p with defaults: 2 pi periodic square, D2V6, rho0 = 1, mach = 1e-2,
  * tau = 0.05, the second-order GSA tableau of Sec. 4.1 (c = 2.25), WENO5+C4,
  * FP64, weno_eps = 1e-6; nx, ny, eps and dt are set from the arguments. */

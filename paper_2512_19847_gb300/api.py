@@ -112,6 +112,7 @@ def lib():
         "ap_dvm_default_params": (None, [P, i32, i32, f64, f64]),
         "ap_dvm_step_noalloc": (i32, [P, vp, i32, vp]),
         "ap_dvm_fma_peak": (i32, [i32, i32, i32, vp, ctypes.POINTER(f64), ctypes.POINTER(f64)]),
+        "ap_dvm_check_conversions": (i32, [vp, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -143,6 +144,19 @@ def fma_peak(precision: int = FP64, iters: int = 256, reps: int = 50, stream=Non
     if st != 0:
         raise ApDvmError(st, "ap_dvm_fma_peak failed")
     return tf.value, ms.value
+
+
+def check_conversions(x: torch.Tensor, stream=None) -> tuple[int, int]:
+    """ap_dvm_check_conversions on the FP64 values of the device tensor x: the numbers of
+    integer-pipe narrowings and widenings that differ from the conversion instructions."""
+    x = x.contiguous()
+    assert x.dtype == torch.float64 and x.is_cuda
+    counts = torch.zeros(2, dtype=torch.int32, device=x.device)
+    st = lib().ap_dvm_check_conversions(_ptr(x), int(x.numel()), _ptr(counts), _stream_ptr(stream))
+    if st != 0:
+        raise ApDvmError(st, "ap_dvm_check_conversions failed")
+    c = counts.cpu().tolist()
+    return c[0], c[1]
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:

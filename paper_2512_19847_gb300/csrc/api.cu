@@ -927,6 +927,13 @@ ap_dvm_status ap_dvm_check_wait_timeout(ap_dvm_handle* h, long long wait_ns) {
   return AP_DVM_OK;
 }
 
+ap_dvm_status ap_dvm_check_conversions(const double* d_in, int n, unsigned* d_counts, void* cuda_stream) {
+  if (!d_counts || n < 0 || (n > 0 && !d_in)) return AP_DVM_ERR_ARG;
+  return launch_check_conversions(d_in, n, d_counts, reinterpret_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
+             ? AP_DVM_OK
+             : AP_DVM_ERR_CUDA;
+}
+
 const char* ap_dvm_last_error(const ap_dvm_handle* h) { return h ? h->err : "null handle"; }
 
 void ap_dvm_destroy(ap_dvm_handle* h) {

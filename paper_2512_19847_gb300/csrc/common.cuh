@@ -214,10 +214,10 @@ __device__ __forceinline__ T d2_scale(T inv_h) { return SCHEME == LF1_C2 ? inv_h
 // IEEE 754 binary64 (binary32) bit pattern with integer operations and selects
 // only, for every class of input, with the instruction's result: exact
 // widening, narrowing rounded to nearest with ties to even (overflow to
-// infinity, subnormal results rounded likewise); a NaN stays a NaN.  The FP32
-// form's finish kernel, whose FP64 moment sums keep the FP64 pipe busy, uses
-// them; the stencil kernels, bound by latency rather than by that pipe, keep
-// the instructions (the integer form's extra instructions cost them more).
+// infinity, subnormal results rounded likewise); a NaN stays a NaN
+// (ap_dvm_check_conversions compares them with the instructions bit for bit).
+// The FP32 forms use them where their FP64 arithmetic meets FP32 data: the
+// moment sums of the close and the closed-form relaxations at eps <= 1e-4.
 __device__ __forceinline__ double widen_f32(float x) {
   const unsigned u = __float_as_uint(x), s = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
   // normal: exponent bias 127 -> 1023 (+896 in the exponent field), fraction 23 -> 52 bits
@@ -232,7 +232,8 @@ __device__ __forceinline__ double widen_f32(float x) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-__device__ __forceinline__ float narrow_f64_rn(double d) {
+// Every class of result: subnormal binary32 results and zero, overflow, infinity, NaN.
+static __device__ __noinline__ float narrow_f64_rn_any(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   const unsigned s = hi & 0x80000000u, ea = (hi >> 20) & 0x7ffu;
   // normal binary32 results (biased binary64 exponent 897 .. 1150): drop 29 fraction bits
@@ -252,6 +253,17 @@ __device__ __forceinline__ float narrow_f64_rn(double d) {
   if (ea == 0x7ffu)
     out = ((hi & 0xfffffu) | lo) ? (0x7fc00000u | ((hi & 0xfffffu) << 3) | (lo >> 29)) : 0x7f800000u;
   return __uint_as_float(out | s);
+}
+
+__device__ __forceinline__ float narrow_f64_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned ea = (hi >> 20) & 0x7ffu;
+  if (ea - 897u <= 1150u - 897u) {   // a normal binary32 result: drop 29 fraction bits, nearest, ties to even
+    unsigned r = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+    r += ((lo & 0x1fffffffu) + 0x0fffffffu + (r & 1u)) >> 29;   // (a carry into the exponent reaches infinity)
+    return __uint_as_float(r | (hi & 0x80000000u));
+  }
+  return narrow_f64_rn_any(d);
 }
 
 // Periodic image of index g on a line of n cells, for g >= -n (any g a tile or

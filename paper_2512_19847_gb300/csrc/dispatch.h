@@ -47,5 +47,7 @@ StencilSet stencil_f32_w5(int tile);
 MiscSet misc_set(int f32form, int tile);
 // One kernel whose bounded wait expires after limit_ns (sets the timeout bit of err).
 cudaError_t launch_wait_timeout(unsigned* err, unsigned long long limit_ns, cudaStream_t stream);
+// The integer-pipe FP32 <-> FP64 conversions against the instructions (ap_dvm_check_conversions).
+cudaError_t launch_check_conversions(const double* in, int n, unsigned* bad, cudaStream_t stream);
 
 }  // namespace apd

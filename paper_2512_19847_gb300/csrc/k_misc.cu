@@ -1,4 +1,6 @@
 // Instantiation unit of the FFT Helmholtz, state I/O and per-step finish kernels.
+#include <algorithm>
+
 #include "dispatch.h"
 #include "fft_kernels.cuh"
 #include "io_kernels.cuh"
@@ -22,6 +24,28 @@ __global__ void k_wait_timeout(unsigned* err, unsigned long long limit_ns) {
 
 cudaError_t launch_wait_timeout(unsigned* err, unsigned long long limit_ns, cudaStream_t stream) {
   k_wait_timeout<<<1, 32, 0, stream>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
+// The integer-pipe conversions against the instructions, bit for bit (NaN as NaN):
+// bad[0] counts mismatching narrowings of the inputs, bad[1] mismatching widenings
+// of the narrowed values.
+__global__ void k_check_conversions(const double* __restrict__ in, int n, unsigned* __restrict__ bad) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double d = in[k];
+    const float a = narrow_f64_rn(d), b = __double2float_rn(d);
+    const bool nb = b != b;
+    if (nb ? !(a != a) : __float_as_uint(a) != __float_as_uint(b)) atomicAdd(&bad[0], 1u);
+    const double w = widen_f32(b), v = (double)b;
+    const bool nv = v != v;
+    if (nv ? !(w != w) : __double_as_longlong(w) != __double_as_longlong(v)) atomicAdd(&bad[1], 1u);
+  }
+}
+
+cudaError_t launch_check_conversions(const double* in, int n, unsigned* bad, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  if (n > 0) k_check_conversions<<<std::min((n + 255) / 256, 4096), 256, 0, stream>>>(in, n, bad);
   return cudaGetLastError();
 }
 namespace {

@@ -662,10 +662,10 @@ __device__ __forceinline__ T* aligned_smem(unsigned char* raw) {
 
 // Widening of a transport value to the relaxation's arithmetic type R.  In the FP32
 // forms the closed-form relaxations run in FP64 (eps <= 1e-4): their FP32 inputs
-// are widened with integer operations (widen_f32, exact for every class of value)
-// rather than by the conversion instruction, which issues on the FP64 pipe, the
-// pipe those kernels' FP64 arithmetic already loads (APD_INT_WIDEN = 0 restores the
-// instruction).
+// are widened, and their results narrowed, with integer operations (widen_f32,
+// narrow_f64_rn: the instructions' results for every class of value) rather than by
+// the conversion instructions, which issue on the FP64 pipe, the pipe those kernels'
+// FP64 arithmetic already loads (APD_INT_WIDEN = 0 restores the instructions).
 #ifndef APD_INT_WIDEN
 #define APD_INT_WIDEN 1
 #endif
@@ -673,6 +673,12 @@ template <typename R, typename T>
 __device__ __forceinline__ R widen(T x) {
   if constexpr (APD_INT_WIDEN && std::is_same<R, double>::value && std::is_same<T, float>::value) return widen_f32(x);
   else return R(x);
+}
+// and the relaxation's result back to the transport type, rounded to nearest
+template <typename T, typename R>
+__device__ __forceinline__ T narrow(R x) {
+  if constexpr (APD_INT_WIDEN && std::is_same<R, double>::value && std::is_same<T, float>::value) return narrow_f64_rn(x);
+  else return T(x);
 }
 
 // ---------------------------------------------------------------------------
@@ -703,8 +709,8 @@ __device__ __forceinline__ void relax_v_cell(const BatchDev& b, const InstDev& I
       a2 = a2 + K.rv_v[i][jj] * widen<R>(x2);
     }
   }
-  r1 = T(a1);
-  r2 = T(a2);
+  r1 = narrow<T>(a1);
+  r2 = narrow<T>(a2);
 }
 
 // Resident blocks per SM the explicit and update kernels are compiled for: threads worth
@@ -1092,7 +1098,7 @@ __global__ void __launch_bounds__(TX* TY, stencil_min_blocks<T>(TX * TY)) k_upda
         aq = aq + K64.rq_d[i][jj] * dv;
         if (jj < i) aq = aq + K64.rv_v[i][jj] * widen<double>(reinterpret_cast<const T*>(I.Xs[jj])[o + 5 * pl]);
       }
-      qi = T(aq);
+      qi = narrow<T>(aq);
     } else {
       T aq = K.r_n[i] * Xn[o + 5 * pl];
       for (int jj = 1; jj <= i; ++jj) {
