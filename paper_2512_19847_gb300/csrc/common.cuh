@@ -218,7 +218,8 @@ __device__ __forceinline__ T d2_scale(T inv_h) { return SCHEME == LF1_C2 ? inv_h
 // (ap_dvm_check_conversions compares them with the instructions bit for bit).
 // The FP32 forms use them where their FP64 arithmetic meets FP32 data: the
 // moment sums of the close and the closed-form relaxations at eps <= 1e-4.
-__device__ __forceinline__ double widen_f32(float x) {
+// Every class of input: zero, subnormal, infinity, NaN as well.
+static __device__ __noinline__ double widen_f32_any(float x) {
   const unsigned u = __float_as_uint(x), s = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
   // normal: exponent bias 127 -> 1023 (+896 in the exponent field), fraction 23 -> 52 bits
   unsigned hi = s | (((u & 0x7fffffffu) >> 3) + (896u << 20)), lo = u << 29;
@@ -230,6 +231,13 @@ __device__ __forceinline__ double widen_f32(float x) {
   }
   if (e == 0xffu) hi = s | 0x7ff00000u | (m >> 3);   // infinity or NaN (lo as above)
   return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned u = __float_as_uint(x);
+  if (((u >> 23) & 0xffu) - 1u < 254u)   // a normal value: rebias the exponent, extend the fraction
+    return __hiloint2double((int)((u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20))), (int)(u << 29));
+  return widen_f32_any(x);
 }
 
 // Every class of result: subnormal binary32 results and zero, overflow, infinity, NaN.
