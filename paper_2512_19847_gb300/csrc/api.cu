@@ -11,8 +11,11 @@
 //   k_rhs(i)         the Helmholtz right-hand side of step 2
 //   k_fft_rows_fwd, k_fft_cols(i), k_fft_rows_inv(i)   step 2 (theta^(i)); the _bs kernels
 //                    of the same passes for axes whose length is not a power of two
-//   k_update(i)      steps 3 and 4 (u^(i), q^(i))
-// and finally k_finish (GSA: X^{n+1} = X^(s); FP32 form: repack populations).
+//   k_update(i)      steps 3 and 4 (u^(i), q^(i)); the last stage's update also closes
+//                    the step (GSA: X^{n+1} = X^(s); FP32 forms: pack the populations and
+//                    sum the next step's moments), written to the other state buffer
+// (k_finish closes the step instead only where no update of the last stage can: the
+// no-allocation entry point, whose state is single-buffered).
 #include <cuda_runtime.h>
 
 #include <algorithm>
