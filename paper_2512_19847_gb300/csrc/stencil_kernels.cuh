@@ -196,10 +196,13 @@ __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr
       const TileRef t = decode_tile<TX, TY>(b, it);
       const InstDev& I = b.inst[t.inst];
       if (I.tma) {
-        const bool ok = mbar_wait(&bars[0], phase & 1u);
+        const unsigned par = phase & 1u;
+        const bool ok = mbar_wait(&bars[0], par);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
+          // the copy did not complete: report, give it one more bounded wait, stop
           if (tid == 0) atomicOr(b.err, 2u);
+          mbar_wait(&bars[0], par);
           return;
         }
         if (tile_on_edge<G>(I, t.x0, t.y0)) stage_edges<T, G>(I, pr, stage0, t.x0, t.y0, tid, NT);
@@ -222,11 +225,14 @@ __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr
     const TileRef t = decode_tile<TX, TY>(b, it);
     const InstDev& I = b.inst[t.inst];
     if (I.tma) {
-      const bool ok = mbar_wait(&bars[cur], (phase >> cur) & 1u);
+      const unsigned par = (phase >> cur) & 1u;
+      const bool ok = mbar_wait(&bars[cur], par);
       phase ^= 1u << cur;
       if (__syncthreads_or(!ok)) {
-        // a copy did not complete: report, let the other buffer's copy land, stop
+        // a copy did not complete: report, give it and the other buffer's copy one more
+        // bounded wait each, stop
         if (tid == 0) atomicOr(b.err, 2u);
+        mbar_wait(&bars[cur], par);
         if (next_tma) mbar_wait(&bars[cur ^ 1], (phase >> (cur ^ 1)) & 1u);
         return;
       }
