@@ -510,6 +510,40 @@ def run_served(torch, n_requests=500, budget=120e9, load=0.8, v_ref=None, seed=7
     return out
 
 
+def run_size_sweep(torch, cells=2048 * 2048, steps=5, tile=2):
+    """Per-cell step cost of the FP32 deviation form in batches of equal total cells and
+    one grid size each (1 x 2048^2, 16 x 512^2, 64 x 256^2, 256 x 128^2, 1024 x 64^2;
+    Taylor-Green-like random divergence-free field, eps = 1e-4, Ma = 1e-2, tile 16x8):
+    per-kernel CUDA-event time per step divided by the cells, in ns."""
+    from paper_2512_19847_gb300 import api, tableaux, workloads as W
+    out = []
+    for n in (2048, 512, 256, 128, 64):
+        count = cells // (n * n)
+        t = api.default_params(n, n, eps=1e-4, dt=1e-3, tau=0.05, mach=1e-2, tableau=tableaux.gsa2(),
+                               precision=api.FP32_DEV)
+        b = api.Batch(t, capacity=count)
+        u1, u2, p = W.random_divfree(n, 7)
+        dt = W.stable_dt(u1, u2, 2 * math.pi / n, 0.05)
+        f = [torch.from_numpy(a).cuda() for a in (u1, u2, p)]
+        for k in range(count):
+            q = t.copy()
+            q.dt = dt
+            b.attach(k, q)
+            b.set_equilibrium(*f, slot=k)
+        b.set_tile(tile)
+        b.step(3)
+        torch.cuda.synchronize()
+        b.profile(True)
+        b.step(steps)
+        prof = b.profile_read()
+        b.profile(False)
+        per = {k: round(v[0] / steps * 1e6 / (n * n * count), 4) for k, v in prof.items()}
+        out.append({"n": n, "instances": count, "ns_per_cell": round(sum(per.values()), 4), "kernels_ns_per_cell": per})
+        del b
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_served_sweep(torch, v_ref, loads=(0.5, 0.7, 0.9), n_requests=500):
     """p50/p99 and Mcell-updates/s of the served form and of the per-solve path at
     several arrival rates (fractions of the batched form's sustained rate)."""
@@ -602,6 +636,8 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--fp64-peak", action="store_true", help="print only the FMA-peak legs (FP64 and FP32) and exit")
     ap.add_argument("--served-sweep", action="store_true", help="also sweep the served form's arrival rate")
+    ap.add_argument("--size-sweep", action="store_true",
+                    help="print only the per-cell step cost of equal-cell FP32 batches of one grid size each and exit")
     ap.add_argument("--tiles", default=None,
                     help="FP64,FP32 tile indices (autotune.TILES) instead of the autotuner, e.g. 5,2 for profiling "
                          "runs, whose perturbed timings would make the autotuner pick other shapes")
@@ -632,6 +668,11 @@ def main():
         legs = {"fp64": fma_peak_leg(local, api.FP64, 256), "fp32": fma_peak_leg(local, api.FP32_DEV, 16384)}
         if rank == 0:
             print(json.dumps({"fma_peak": legs}), flush=True)
+        return
+    if args.size_sweep:
+        sweep = run_size_sweep(torch)
+        if rank == 0:
+            print(json.dumps({"size_sweep": sweep}), flush=True)
         return
     fields, dt = workload(n, args.eps, args.mach, args.tau)
     peaks = load_peaks()
