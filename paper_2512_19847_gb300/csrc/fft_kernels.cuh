@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(cols_threads<T>(), sizeof(T) == 4 ? 1024 / APD
       if (kx == 0 && ky == 0) {
         v.x = T(s_mean); v.y = T(0);
       } else if (sizeof(T) == 8) {
-        const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
+        const double f = scale * rcp_newton(I.lamx[kx] + I.lamy[ky] - kap);
         v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
       } else {
         // FP32 form: the symbol in FP32 from the tables rounded once on the host
@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols_bs(con
         if (kx == 0 && ky == 0) {
           v.x = T(s_mean); v.y = T(0);
         } else {
-          const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
+          const double f = scale * rcp_newton(I.lamx[kx] + I.lamy[ky] - kap);
           v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
         }
         x[g * m + off + ky] = v;
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_fft_cols_bs(con
       } else if (kx == 0 && ky == 0) {
         v.x = T(s_mean); v.y = T(0);
       } else {
-        const double f = scale / (I.lamx[kx] + I.lamy[ky] - kap);
+        const double f = scale * rcp_newton(I.lamx[kx] + I.lamy[ky] - kap);
         v.x = T(double(v.x) * f); v.y = T(double(v.y) * f);
       }
       x[e] = v;

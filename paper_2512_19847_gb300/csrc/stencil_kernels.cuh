@@ -293,26 +293,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined by one
-// third-order step r <- r + r (e + e^2), e = 1 - d r (APD_RCP_NEWTON = 0, the default:
-// it triples the number of correct bits in three FMAs), or by APD_RCP_NEWTON
-// Newton-Raphson steps r <- r + r (1 - d r), each doubling them in two (one step is
-// too few for the FP64 parity of 1e-12; two cost one FMA more than the third-order step).
-#ifndef APD_RCP_NEWTON
-#define APD_RCP_NEWTON 0
-#endif
-__device__ __forceinline__ double rcp_newton(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  if (APD_RCP_NEWTON == 0) {
-    const double e = fma(-d, r, 1.0);
-    return fma(r, fma(e, e, e), r);
-  }
-#pragma unroll
-  for (int k = 0; k < APD_RCP_NEWTON; ++k) r = fma(r, fma(-d, r, 1.0), r);
-  return r;
-}
-
 // Interface flux from the left (g+) and right (g-) reconstructions.
 template <typename T>
 __device__ __forceinline__ T combine(T nl, T dl, T nr, T dr) {
