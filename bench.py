@@ -76,8 +76,9 @@ def step_bytes_per_cell(f32: bool) -> dict:
         # stage 2: read X^(2) (6), E^(1), v^n (4), write E, D0.u, D_Delta theta, D_LF.B(v) + D0 theta, v^(3) (8)
         "explicit": (5 + 5) + (10 + 8),
         # stage 2: read v^(2), theta^n, D0.u^n (4), write DB, R (2);
-        # stage 3: read v^(3), theta^n, D0.u^n, D0.u^(2), DB^(2), D_Delta theta^(2) (7), write 2
-        "rhs": (4 + 2) + (7 + 2),
+        # stage 3: read v^(3), theta^n, D0.u^n, D0.u^(2), DB^(2), D_Delta theta^(2) (7), write R
+        # (the last stage's DB is read by no later stage)
+        "rhs": (4 + 2) + (7 + 1),
         # each pass reads and writes one plane-equivalent (real plane or half spectrum), two solves
         "fft_rows_fwd": 4, "fft_cols": 4, "fft_rows_inv": 4,
         # stage 2: read theta, v, u^(1), u^n, q^n (8), write u, q, D0.v (4);

@@ -900,6 +900,7 @@ __global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 :
     const T* v2 = v1 + pl;
     const T* th = reinterpret_cast<const T*>(I.X) + 2 * pl;
     T* DBi = reinterpret_cast<T*>(I.DB[i]);
+    const bool keep_db = i < b.s;   // D_0^2:B(v^(i)) is read by the later stages only
     T* Rp = reinterpret_cast<T*>(I.R);
     const int local = it - b.rhs_start[k_inst];
     const int nseg = (nx + RHS_SEG - 1) / RHS_SEG;
@@ -956,7 +957,7 @@ __global__ void __launch_bounds__(RHS_THREADS, sizeof(T) == 4 ? APD_RHS_MINB32 :
         const T Bh = msx2 * sxx + sx1x2 * sxy + sy2 * syy;
         if (outc && h < nrows) {
           const size_t o = (size_t)(y0 + h) * nx + x;
-          DBi[o] = Bh;
+          if (keep_db) DBi[o] = Bh;
           Rp[o] = R[h] - cdb * Bh;
           tsum += double(thn[h]);
         }
