@@ -250,18 +250,20 @@ __device__ __forceinline__ void tile_loop(const BatchDev& b, const PlaneList& pr
 // right-biased reconstruction, which mirrors the left-biased one).  C holds
 // (13/3) (f_{m-1} - 2 f_m + f_{m+1})^2 + 4 eps_W per point: the Jiang-Shu
 // indicators and eps_W are both scaled by 4, which leaves the normalised
-// weights unchanged and makes (eps_W + beta_k) one FMA from C.  Returns
-// numerator and denominator of
+// weights unchanged and makes (eps_W + beta_k) one FMA from C.  FP64 (FP32 WENO5
+// runs in registers, w5_rec_f32).  Returns numerator and denominator of
 //   sum_k d_k p_k / s_k  /  sum_k d_k / s_k,   s_k = (eps_W + beta_k)^2,
-// multiplied through by s_0 s_1 s_2 (FP64) so that no division is needed here.
-template <typename T>
-__device__ __forceinline__ T frcp(T x) {
-  if (std::is_same<T, float>::value) return T(__frcp_rn(float(x)));
-  return T(1) / x;
-}
-
+// multiplied through by s_0 s_1 s_2 so that no division is needed here, and
+// written about the centred candidate, p_1 + w_0 (p_0 - p_1) + w_2 (p_2 - p_1): the
+// differences are third differences of the stencil, (f_{m-2} - 3 f_{m-1} + 3 f_m -
+// f_{m+1})/3 = (l_0 + l_1)/3 and (f_{m-1} - 3 f_m + 3 f_{m+1} - f_{m+2})/6 = (l_1 - l_2)/6
+// from the indicators' linear terms l_k, so no candidate but p_1 is formed.  With the
+// denominator taken 10 times (A + 6 B + 3 C) and the numerator 30 times, their ratio
+// is three times the reconstruction; that 3 joins 1/dx in the flux difference
+// (flux_scale).  24 FP64 operations against 29 for the three weighted candidates.
 template <typename T>
 __device__ __forceinline__ void w5_nd(const T* P, const T* C, int st, T& num, T& den) {
+  static_assert(std::is_same<T, double>::value, "FP64 reconstruction");
   const T a = P[-2 * st], b = P[-st], c = P[0], d = P[st], e = P[2 * st];
   const T l0 = a - T(4) * b + T(3) * c;
   const T l1 = b - d;
@@ -269,21 +271,12 @@ __device__ __forceinline__ void w5_nd(const T* P, const T* C, int st, T& num, T&
   const T e0 = C[-st] + l0 * l0;
   const T e1 = C[0] + l1 * l1;
   const T e2 = C[st] + l2 * l2;
-  // candidate polynomials times their linear weights (1/10, 6/10, 3/10)
-  const T q0 = a * T(1.0 / 30.0) - b * T(7.0 / 60.0) + c * T(11.0 / 60.0);
-  const T q1 = -b * T(0.1) + c * T(0.5) + d * T(0.2);
-  const T q2 = c * T(0.1) + d * T(0.25) - e * T(0.05);
-  if (std::is_same<T, double>::value) {
-    const T s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
-    const T A = s1 * s2, B = s0 * s2, Cc = s0 * s1;
-    num = A * q0 + B * q1 + Cc * q2;
-    den = T(0.1) * A + T(0.6) * B + T(0.3) * Cc;
-  } else {
-    // FP32: reciprocal weights (products of s_k could leave the float range)
-    const T r0 = frcp(e0 * e0), r1 = frcp(e1 * e1), r2 = frcp(e2 * e2);
-    num = r0 * q0 + r1 * q1 + r2 * q2;
-    den = T(0.1) * r0 + T(0.6) * r1 + T(0.3) * r2;
-  }
+  const T s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+  const T A = s1 * s2, B = s0 * s2, Cc = s0 * s1;     // 1 / s_k times s_0 s_1 s_2
+  den = fma(T(3), Cc, fma(T(6), B, A));               // 10 (d_0 A + d_1 B + d_2 C)
+  const T p1x3 = fma(T(2.5), c, fma(T(-0.5), b, d));  // 3 p_1
+  const T ta = l0 + l1, tb = T(1.5) * (l1 - l2);      // 3 (p_0 - p_1), 9 (p_2 - p_1)
+  num = fma(p1x3, den, fma(A, ta, Cc * tb));          // 30 (d_0 A p_0 + d_1 B p_1 + d_2 C p_2)
 }
 
 // FP32: approximate reciprocal (one MUFU operation, PTX rcp.approx.ftz.f32).
@@ -293,11 +286,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Interface flux from the left (g+) and right (g-) reconstructions.
-template <typename T>
-__device__ __forceinline__ T combine(T nl, T dl, T nr, T dr) {
-  if (std::is_same<T, double>::value) return (nl * dr + nr * dl) * rcp_newton(double(dl * dr));
-  return nl * frcp(dl) + nr * frcp(dr);
+// Interface flux from the left (g+) and right (g-) reconstructions (FP64).
+__device__ __forceinline__ double combine(double nl, double dl, double nr, double dr) {
+  return (nl * dr + nr * dl) * rcp_newton(dl * dr);
 }
 
 // Select a[i] for a small compile-time-sized array without local memory.
@@ -381,29 +372,31 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
     }
     return;
   }
-  // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W (x 4 for the doubled split)
-  const T ew4 = T(16) * ew;
-  for (int k = tid; k < 2 * NP * LS; k += NT) {
-    const int q = k / LS, r = k - q * LS;
-    int line, pt;
-    pt_line(r, line, pt);
-    if (pt == 0 || pt == LL - 1) continue;
-    const int pr = q >> 1, pm = q & 1;
-    const T* f = split + (4 * pr + pm) * LS + r;
-    const T cv = f[-PS] - T(2) * f[0] + f[PS];
-    split[(4 * pr + 2 + pm) * LS + r] = T(13.0 / 3.0) * cv * cv + ew4;
-  }
-  __syncthreads();
-  // 3. interface fluxes: left-biased reconstruction of g+ centred at m, right-biased of g- centred at m+1
-  for (int k = tid; k < NP * NL * NI; k += NT) {
-    const int pr = k / (NL * NI);
-    int line, m;
-    if_line(k - pr * (NL * NI), line, m);
-    const int base = sp_off(line, H - 1 + m);
-    T nl, dl, nr, dr;
-    w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, PS, nl, dl);
-    w5_nd<T>(split + (4 * pr + 1) * LS + base + PS, split + (4 * pr + 3) * LS + base + PS, -PS, nr, dr);
-    out[pr * NL * NI + out_off(line, m)] = combine<T>(nl, dl, nr, dr);
+  if constexpr (SCHEME == WENO5_C4) {
+    // 2. curvature part of the smoothness indicators, scaled by 4, plus 4 eps_W (x 4 for the doubled split)
+    const T ew4 = T(16) * ew;
+    for (int k = tid; k < 2 * NP * LS; k += NT) {
+      const int q = k / LS, r = k - q * LS;
+      int line, pt;
+      pt_line(r, line, pt);
+      if (pt == 0 || pt == LL - 1) continue;
+      const int pr = q >> 1, pm = q & 1;
+      const T* f = split + (4 * pr + pm) * LS + r;
+      const T cv = f[-PS] - T(2) * f[0] + f[PS];
+      split[(4 * pr + 2 + pm) * LS + r] = T(13.0 / 3.0) * cv * cv + ew4;
+    }
+    __syncthreads();
+    // 3. interface fluxes: left-biased reconstruction of g+ centred at m, right-biased of g- centred at m+1
+    for (int k = tid; k < NP * NL * NI; k += NT) {
+      const int pr = k / (NL * NI);
+      int line, m;
+      if_line(k - pr * (NL * NI), line, m);
+      const int base = sp_off(line, H - 1 + m);
+      T nl, dl, nr, dr;
+      w5_nd<T>(split + (4 * pr + 0) * LS + base, split + (4 * pr + 2) * LS + base, PS, nl, dl);
+      w5_nd<T>(split + (4 * pr + 1) * LS + base + PS, split + (4 * pr + 3) * LS + base + PS, -PS, nr, dr);
+      out[pr * NL * NI + out_off(line, m)] = combine(nl, dl, nr, dr);
+    }
   }
 }
 
@@ -419,20 +412,19 @@ __device__ __forceinline__ void axis_fluxes(const T* const* g, const T* const* U
 // immediate constants issues fewer instructions here than paired f32x2
 // arithmetic, whose operands and constants must first be packed.)
 
-// Scalar FP32 WENO5 reconstruction from register values (the arithmetic of
-// w5_nd with reciprocal weights); returns num / den.
+// Scalar FP32 WENO5 reconstruction from register values: the arithmetic of w5_nd
+// (about the centred candidate, three times the reconstruction) with reciprocal
+// weights r_k = 1 / s_k, as products of the s_k could leave the float range.
 __device__ __forceinline__ float w5_rec_f32(float a, float b, float c, float d, float e, float C0, float C1, float C2) {
   const float l0 = fmaf(3.f, c, fmaf(-4.f, b, a));
   const float l1 = b - d;
   const float l2 = fmaf(3.f, c, fmaf(-4.f, d, e));
   const float e0 = fmaf(l0, l0, C0), e1 = fmaf(l1, l1, C1), e2 = fmaf(l2, l2, C2);
   const float r0 = rcp_approx(e0 * e0), r1 = rcp_approx(e1 * e1), r2 = rcp_approx(e2 * e2);
-  // candidate polynomials times their linear weights (1/10, 6/10, 3/10)
-  const float q0 = fmaf(11.f / 60.f, c, fmaf(-7.f / 60.f, b, a * (1.f / 30.f)));
-  const float q1 = fmaf(0.2f, d, fmaf(0.5f, c, b * -0.1f));
-  const float q2 = fmaf(-0.05f, e, fmaf(0.25f, d, c * 0.1f));
-  const float num = fmaf(r2, q2, fmaf(r1, q1, r0 * q0));
-  const float den = fmaf(0.3f, r2, fmaf(0.6f, r1, 0.1f * r0));
+  const float den = fmaf(3.f, r2, fmaf(6.f, r1, r0));          // 10 sum_k d_k r_k
+  const float p1x3 = fmaf(2.5f, c, fmaf(-0.5f, b, d));          // 3 p_1
+  const float ta = l0 + l1, tb = 1.5f * (l1 - l2);              // 3 (p_0 - p_1), 9 (p_2 - p_1)
+  const float num = fmaf(p1x3, den, fmaf(r0, ta, r2 * tb));     // 30 sum_k d_k r_k p_k
   return num * rcp_approx(den);
 }
 
@@ -583,14 +575,14 @@ __device__ __forceinline__ void w5_fluxes_xy(const T* const* gx, const T* const*
       const int base = line * W + (H - 1 + m);
       w5_nd<T>(spx + (4 * pr + 0) * LSX + base, spx + (4 * pr + 2) * LSX + base, 1, nl, dl);
       w5_nd<T>(spx + (4 * pr + 1) * LSX + base + 1, spx + (4 * pr + 3) * LSX + base + 1, -1, nr, dr);
-      fx[pr * TY * NIX + line * NIX + m] = combine<T>(nl, dl, nr, dr);
+      fx[pr * TY * NIX + line * NIX + m] = combine(nl, dl, nr, dr);
     } else {
       const int kk = k - NP * TY * NIX;
       const int pr = kk / (TX * NIY), r = kk - pr * (TX * NIY), m = r / TX, line = r - m * TX;
       const int base = (H - 1 + m) * TX + line;
       w5_nd<T>(spy + (4 * pr + 0) * LSY + base, spy + (4 * pr + 2) * LSY + base, TX, nl, dl);
       w5_nd<T>(spy + (4 * pr + 1) * LSY + base + TX, spy + (4 * pr + 3) * LSY + base + TX, -TX, nr, dr);
-      fy[pr * TX * NIY + m * TX + line] = combine<T>(nl, dl, nr, dr);
+      fy[pr * TX * NIY + m * TX + line] = combine(nl, dl, nr, dr);
     }
   }
 }
@@ -716,10 +708,15 @@ __host__ __device__ constexpr int stencil_min_blocks(int threads) {
   return b > 0 ? b : 1;
 }
 
-// Factor of 1/h in the difference of interface fluxes: the WENO fluxes come out
-// doubled (the split without its 1/2), the LF1 flux of Sec. 3.2 does not.
+// Factor of 1/h in the difference of interface fluxes: the WENO3 fluxes come out
+// doubled (the split without its 1/2), the WENO5 ones six times (the reconstruction
+// three times as well); the LF1 flux of Sec. 3.2 comes out as it is.
 template <typename T, int SCHEME>
-__device__ __forceinline__ T flux_scale(T inv_h) { return SCHEME == LF1_C2 ? inv_h : T(0.5) * inv_h; }
+__device__ __forceinline__ T flux_scale(T inv_h) {
+  if (SCHEME == LF1_C2) return inv_h;
+  if (SCHEME == WENO5_C4) return inv_h * T(1.0 / 6.0);
+  return T(0.5) * inv_h;
+}
 
 // ---------------------------------------------------------------------------
 template <typename T, int SCHEME, int TX, int TY>
