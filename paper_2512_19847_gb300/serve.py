@@ -84,7 +84,8 @@ class Server:
         self.chunk = chunk
         self.free = list(range(capacity))[::-1]
         self.resident = {}             # slot -> [job, remaining steps, workspace bytes]
-        self.bytes = self.batch.workspace.numel()
+        self.base = self.batch.workspace.numel()
+        self.bytes = self.base
         self.inflight = []             # (job, host tensor, event)
 
     def _admit(self, job: Job, now: float) -> bool:
@@ -125,6 +126,12 @@ class Server:
         self.inflight = keep
 
     def run(self, jobs: list[Job]) -> ServeStats:
+        # admission is in arrival order: a request that cannot fit even alone would hold
+        # up every later one forever
+        for j in jobs:
+            if self.base + api.Batch.instance_bytes(j.params) > self.budget:
+                raise ValueError(f"request {j.rid}: its workspace does not fit the HBM budget "
+                                 f"of {self.budget:.0f} bytes even alone")
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
         queue = collections.deque()
         t0 = time.perf_counter()
