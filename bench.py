@@ -617,7 +617,15 @@ def config_dict(args):
     return {"workload": f"taylor_green_{args.n}x{args.n}_eps{args.eps:g}_Ma{args.mach:g}",
             "grid": [args.n, args.n], "eps": args.eps, "mach": args.mach, "tau": args.tau,
             "dt_rule": "min(0.4 dx/max|u|, 0.32 dx^2/(tau/4))",
-            "tableau": "GSA2 c=2.25", "space": "WENO5+C4", "l2": "inputs larger than L2 (FP64 state 201 MB, step working set ~1.7 GB)"}
+            "tableau": "GSA2 c=2.25", "space": "WENO5+C4", "l2": l2_note(args.n)}
+
+
+def l2_note(n: int) -> str:
+    """The timing rule's L2 statement for an n x n workload (129 MB of L2; the step's
+    working set scales with the cells, about 1.7 GB at 2048^2)."""
+    state, work = 48 * n * n / 1e6, 1.7 * n * n / 2048 ** 2
+    side = "larger" if state > 129 else "smaller"
+    return f"inputs {side} than L2 (FP64 state {state:.0f} MB, step working set ~{work:.2g} GB)"
 
 
 # ----------------------------------------------------------------- main

@@ -88,3 +88,24 @@ def test_fp32_error_measure():
     Y[0] += 1e-6 * np.max(np.hypot(X[0], X[1]))
     vel, _ = bench.fp32_errors(Y, X)
     assert vel == pytest.approx(1e-6, rel=1e-6)
+
+
+def test_l2_note_follows_the_size():
+    assert bench.l2_note(2048) == "inputs larger than L2 (FP64 state 201 MB, step working set ~1.7 GB)"
+    assert bench.l2_note(512).startswith("inputs smaller than L2")
+
+
+def test_reference_arm_line():
+    # the oracle on the host cores, small grid: the line the contract asks for, impl reference
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"), "--impl", "reference",
+                        "--n", "32", "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["grid"] == [32, 32] and "smaller than L2" in line["config"]["l2"]
